@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark: seconds per ChFSI pass on the FP64-at-scale workload, through the C ABI.
+
+Workload (synthetic stand-in for the paper's Mo/Al systems): periodic cube of side
+30 bohr, 24^3 cells, p = 6 GLL elements (343 nodes/cell, 144^3 = 2,985,984 DoFs),
+64 Gaussian wells (depth 3 Ha, width 0.8 bohr) on a jittered 4^3 lattice, 4
+projectors per atom (256, Gaussian radial width 1 bohr, cutoff 3 bohr, couplings
+U[0.5, 2] Ha); 512 states, block 128, Chebyshev degree 40.  A step is one pass:
+filter (4 blocks x 40 applications of H~), Cholesky-Gram-Schmidt, Rayleigh-Ritz,
+residuals, bounds update.
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own seeded
+replica (weak scaling; the pass has no cross-rank data path here).
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision fp64] [--workload scale|small]
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def workload(name, seed):
+    if name == "small":
+        return synth.small_wells(seed)
+    return synth.lattice_atoms(seed)
+
+
+def describe(wl):
+    return {"workload": wl.name, "L_bohr": wl.L, "cells": [wl.ncell] * 3, "degree": wl.degree,
+            "ndofs": wl.ndofs, "nstates": wl.nstates, "block": wl.block,
+            "cheb_degree": wl.cheb_degree, "atoms": int(wl.centres.shape[0]), "projectors": wl.nproj,
+            "seed": wl.seed, "l2": "inputs larger than L2 (cell matrices stream 13 GB per H~X)"}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ distributed
+def dist_init(gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as tdist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+    tdist.init_process_group(backend)
+    return rank, world, local, tdist
+
+
+def max_over_ranks(x, tdist, device):
+    if tdist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(tdist, device):
+    if tdist is None:
+        return
+    import torch
+    t = torch.zeros(1, device=device)
+    tdist.all_reduce(t)
+
+
+# ------------------------------------------------------------ CPU oracle
+def oracle_sample(wl, target_s=12.0):
+    """Oracle (FP64 numpy) on a bounded sample of the workload, scaled to one pass.
+
+    Sample: the cell matrices and the cell-level H~X of a subset of cells on one
+    block of `block` columns, plus the Gram product X^T X on a slice of rows; the
+    pass estimate is (applications per pass) x (per-cell time x N_c) + the three
+    M N^2 products (S, H^, rotations) at the measured Gram rate."""
+    import oracle
+    t0 = time.perf_counter()
+    m = oracle.PeriodicMesh(wl.L, wl.ncell, wl.degree)
+    h = oracle.Hamiltonian(m)
+    order = np.random.default_rng(wl.seed).permutation(m.ncells)
+    h.v_quad = np.zeros((m.ncells, h.nq))
+    setup = time.perf_counter() - t0
+    ncells_done, t_cells = 0, 0.0
+    tl = time.perf_counter()
+    while time.perf_counter() - tl < target_s * 0.85 and ncells_done < m.ncells:
+        c = int(order[ncells_done])
+        cx, cy, cz = m.cell_coords(c)
+        xq, _ = m.quad_rule(0)
+        nq1 = xq.size
+        qa = np.tile(np.arange(nq1), nq1 * nq1)
+        qb = np.tile(np.repeat(np.arange(nq1), nq1), nq1)
+        qc = np.repeat(np.arange(nq1), nq1 * nq1)
+        pts = np.stack([cc * m.h[d] + (xq[qi] + 1.0) * m.h[d] / 2.0
+                        for d, (cc, qi) in enumerate(((cx, qa), (cy, qb), (cz, qc)))], axis=1)
+        h.v_quad[c] = synth.gaussian_wells(pts, wl.centres, wl.depth, wl.width, wl.L)
+        Hc = h.cell_matrix(c)                              # set-up, outside the pass
+        rows = m.cell_map[c]
+        Xc = synth.random_rows(wl.seed, rows, wl.block)    # the cell's rows of the block
+        Y = np.zeros_like(Xc)
+        tb = time.perf_counter()
+        Yc = Hc @ Xc                                       # cell GEMM
+        np.add.at(Y, np.arange(len(rows)), Yc)             # assembly into the output rows
+        t_cells += time.perf_counter() - tb
+        ncells_done += 1
+    per_cell_apply = t_cells / max(ncells_done, 1)
+    apps = wl.cheb_degree * (wl.nstates // wl.block) + wl.nstates // wl.block
+    t_filter = per_cell_apply * m.ncells * apps
+    # Gram rate on a row slice (M N^2 flops class)
+    rows = min(m.ndofs, 200000)
+    Xs = synth.random_block(wl.seed + 1, rows, wl.nstates)
+    ta = time.perf_counter()
+    _ = Xs.T @ Xs
+    tg = time.perf_counter() - ta
+    gram_rate = rows * wl.nstates ** 2 * 2 / tg
+    t_dense = (m.ndofs * wl.nstates ** 2 * (1 + 1 + 1 + 2 + 2)) / gram_rate
+    return {"value": t_filter + t_dense, "unit": "s/pass", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"oracle cell-level H~X on {ncells_done} of {m.ncells} cells x {wl.block} columns "
+                       f"({t_cells:.1f} s, scaled x{m.ncells}/{ncells_done} x {apps} applications) + "
+                       f"X^T X on {rows} x {wl.nstates} rows ({tg:.1f} s, scaled to S, H^ and "
+                       f"3 rotations); setup {setup:.1f} s not counted")}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local, tdist):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_07820_gb300 as dg
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = workload(args.workload, args.seed + rank)
+    stream = torch.cuda.current_stream()
+    mesh = dg.dftfe_mesh_create(wl.L, wl.ncell, wl.degree)
+    ham = dg.dftfe_ham_create(mesh, stream.cuda_stream)
+    nxyz, qxyz = dg.dftfe_mesh_coords(mesh)
+    v = synth.gaussian_wells(qxyz.reshape(-1, 3), wl.centres, wl.depth, wl.width, wl.L)
+    dg.dftfe_ham_set_potential(ham, torch.from_numpy(v).to(dev))
+    if wl.nproj:
+        rowptr, node, chi = synth.projector_csr(nxyz, wl.centres, wl.proj_width, wl.proj_cutoff, wl.L)
+        dg.dftfe_ham_set_nonlocal(ham, wl.couplings, rowptr, node, chi)
+    del v, qxyz, nxyz
+    M, N = wl.ndofs, wl.nstates
+    X = torch.empty((M, N), dtype=torch.float64, device=dev)
+    dg.dftfe_random_uniform(X, wl.seed)
+    bounds = dg.dftfe_spectrum_bounds(ham, 20, wl.seed + 1000, N)
+    ev = torch.empty(N, dtype=torch.float64, device=dev)
+    rs = torch.empty(N, dtype=torch.float64, device=dev)
+    prec = dg.DFTFE_FP64
+
+    for _ in range(args.warmup):
+        dg.dftfe_chfsi_pass(ham, X, wl.block, wl.cheb_degree, bounds, ev, rs, prec)
+    torch.cuda.synchronize()
+
+    dg.dftfe_profile_enable(ham, True)
+    clk = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                       if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local)
+    barrier(tdist, dev)
+    torch.cuda.synchronize()
+    clk.start()
+    l0 = dg.dftfe_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        dg.dftfe_chfsi_pass(ham, X, wl.block, wl.cheb_degree, bounds, ev, rs, prec)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(tdist, dev)
+    launches = dg.dftfe_launch_count() - l0
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, tdist, dev)
+    cell_ms, cell_n = dg.dftfe_profile_query(ham, "cell_gemm_fp64")
+    dg.dftfe_profile_enable(ham, False)
+    sec_per_pass = ms / 1e3 / args.steps
+
+    nc = (wl.degree + 1) ** 3
+    Nc = wl.ncell ** 3
+    apps_cols = N * wl.cheb_degree + N            # filter + Rayleigh-Ritz H~X columns per pass
+    cell_flops = 2.0 * Nc * nc * nc * apps_cols * args.steps
+    filter_flops = 2.0 * Nc * nc * nc * N * wl.cheb_degree
+    achieved = cell_flops / (cell_ms / 1e3) / 1e12 if cell_ms > 0 else None
+    filt_tflops = filter_flops / (sec_per_pass) / 1e12
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.empty((M, N), dtype=torch.float64, pin_memory=True)
+        Xh.copy_(X)
+        evh = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        rsh = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        ne = max(1, min(args.steps, 2))
+        torch.cuda.synchronize()
+        barrier(tdist, dev)
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            X.copy_(Xh, non_blocking=True)
+            dg.dftfe_chfsi_pass(ham, X, wl.block, wl.cheb_degree, bounds, ev, rs, prec)
+            evh.copy_(ev, non_blocking=True)
+            rsh.copy_(rs, non_blocking=True)
+            torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / ne
+        te = max_over_ranks(te, tdist, dev)
+        e2e = {"value": te, "unit": "s/pass", "h2d_bytes_per_step": M * N * 8,
+               "d2h_bytes_per_step": 2 * N * 8, "steps": ne}
+
+    out = {
+        "metric": "ChFSI pass seconds (FP64) with filter TFLOP/s vs peak",
+        "value": sec_per_pass, "unit": "s/pass", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "precision": "fp64",
+        "config": describe(wl) | {"parallelism": f"replicas{world}"},
+        "filter_tflops": filt_tflops,
+        "dofs_x_vectors_per_s": M * N * wl.cheb_degree / (sec_per_pass),
+        "roofline": {"kernel": "k_cell_fp64_wide (gather + dense cell GEMM + scatter-add)",
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                     "traffic": None, "launches": cell_n,
+                     "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2.07 GHz (nominal 1.25 TF/s)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "bounds": {"a": bounds.a, "b": bounds.b, "a0": bounds.a0},
+        "max_resid": float(rs.max().item()),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = oracle_sample(wl, args.cpu_seconds)
+        except Exception as exc:  # the baseline must not hide the measurement
+            out["cpu_baseline"] = {"error": repr(exc)}
+    dg.dftfe_ham_destroy(ham)
+    dg.dftfe_mesh_destroy(mesh)
+    return out
+
+
+def run_reference(args, rank, world):
+    wl = workload(args.workload, args.seed)
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(wl, args.cpu_seconds)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            last = r
+    v = statistics.mean(vals)
+    return {"impl": "reference", "metric": "ChFSI pass seconds (FP64) with filter TFLOP/s vs peak",
+            "value": v, "unit": "s/pass", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": describe(wl) | {"parallelism": "cpu"},
+            "cpu_baseline": last | {"value": v},
+            "e2e": {"value": v, "unit": "s/pass", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "small"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    rank, world, local, tdist = dist_init(args.gpus)
+    out = run_ours(args, rank, world, local, tdist)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if tdist is not None:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * dftfe_gb300.h -- C ABI of a GB300 (sm_103a) implementation of one
+ * Chebyshev-filtered subspace iteration (ChFSI) pass for the spectral
+ * finite-element Kohn-Sham eigenproblem of DFT-FE 1.0 (Das, Motamarri,
+ * Subramanian, Rogers, Gavini, Comput. Phys. Commun.).
+ *
+ * Problem (Sec. 2.3): the generalised eigenproblem H u = eps M u with C0
+ * Lagrange elements on Gauss-Lobatto-Legendre (GLL) nodes (Eq. fem), lumped
+ * diagonal M by GLL quadrature, is solved in the Loewdin form
+ * H~ = M^-1/2 H M^-1/2 (Eq. hep).  H = H^loc + H^nl at the Gamma point
+ * (Eq. discreteHam without the GGA and k terms; Eq. nonlocalHamDiscrete).
+ * The pass (Sec. 3.1-3.2): Chebyshev filter (Eq. chebyfilter), then
+ * Cholesky-Gram-Schmidt and Rayleigh-Ritz (the orthonormalise-first reading of
+ * Alg. 2), then residuals.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns dftfe_status; nothing throws or aborts across the ABI.
+ *    On error, dftfe_last_error() returns a thread-local message.
+ *  - Wavefunction blocks X are DoF-major (Sec. 4.3: all values of one DoF are
+ *    contiguous): element (i, j) of an M x ncol block is X[i*ld + j], ld >= ncol,
+ *    FP64, in DEVICE memory owned by the caller.
+ *  - Handles own their device state and workspace; workspace is allocated on
+ *    first use and freed by *_destroy.  A handle is not thread-safe; distinct
+ *    handles are independent.  All device work of a ham is enqueued on the
+ *    stream given to dftfe_ham_create and is asynchronous, except calls that
+ *    return host scalars (they synchronise that stream and say so).
+ *  - On DFTFE_ERR_ARG, outputs are untouched.
+ *  - Numbering (the paper is silent; this library's contract): global node
+ *    (ix, iy, iz) -> ix + gx*(iy + gy*iz), gx = ncell[0]*degree; cell
+ *    (cx, cy, cz) -> cx + nx*(cy + ny*cz); cell-local node (a, b, c) ->
+ *    a + (p+1)*(b + (p+1)*c); quadrature points in the same order, x fastest.
+ *  - Periodic cubes/cuboids only, >= 2 cells per axis.
+ */
+#ifndef DFTFE_GB300_H
+#define DFTFE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DFTFE_OK = 0,
+  DFTFE_ERR_ARG = 1,      /* invalid argument; outputs untouched */
+  DFTFE_ERR_OOM = 2,      /* device allocation failed */
+  DFTFE_ERR_CUDA = 3,     /* a CUDA runtime call or launch failed */
+  DFTFE_ERR_NOT_SPD = 4,  /* overlap matrix S not positive definite (X untouched) */
+  DFTFE_ERR_NOCONV = 5,   /* dense eigensolver did not converge */
+  DFTFE_ERR_TIMEOUT = 6,  /* a bounded device-side wait gave up */
+  DFTFE_ERR_STATE = 7     /* call out of order (e.g. no potential set) */
+} dftfe_status;
+
+typedef enum {
+  DFTFE_FP64 = 0,          /* everything in FP64 */
+  DFTFE_MIXED_BF16X3 = 1   /* filter cell GEMMs as 3-term BF16 splits with FP32
+                              accumulation on the tensor cores (tcgen05); CholGS,
+                              Rayleigh-Ritz and residuals in FP64 */
+} dftfe_precision;
+
+typedef struct dftfe_mesh_s* dftfe_mesh; /* opaque, library-owned */
+typedef struct dftfe_ham_s* dftfe_ham;   /* opaque, library-owned */
+
+/* Mesh description.  L: box lengths (bohr).  ncell: cells per axis (>= 2).
+ * degree: FE degree p (1..8).  periodic: must be {1,1,1}.
+ * vquad: rule for the local-potential term of Eq. quadLocal (the paper does not
+ *   fix n_q): 0 = Gauss-Legendre with nq1d points per axis (dense V^c),
+ *   1 = GLL collocated on the nodes (V^c diagonal).
+ * nq1d: Gauss points per axis for vquad = 0 (0 means degree + 1, max 12). */
+typedef struct {
+  double L[3];
+  int ncell[3];
+  int degree;
+  int periodic[3];
+  int vquad;
+  int nq1d;
+} dftfe_mesh_desc;
+
+/* Spectrum bounds for the filter (Eq. chebyfilter: Hbar = c1 H~ + c2 maps the
+ * unwanted interval [a, b] to [-1, 1]).  a0: estimate of the lowest wanted
+ * eigenvalue, used by the scaled recurrence (Zhou-Saad); NaN selects the
+ * unscaled three-term recurrence T_{k+1} = 2 x T_k - T_{k-1}. */
+typedef struct {
+  double a, b, a0;
+} dftfe_bounds;
+
+/* ---------------------------------------------------------------- mesh (host) */
+
+/* Create the mesh description and its 1D GLL / Gauss rules (Sec. 2.3, Eq. fem;
+ * lumped M in the text after Eq. hep).  Host-only; no device memory. */
+dftfe_status dftfe_mesh_create(const dftfe_mesh_desc* desc, dftfe_mesh* out);
+
+/* Sizes: ndofs M = prod(ncell*degree), ncells, nodes_per_cell (p+1)^3,
+ * quad_per_cell (nq1d^3 for vquad 0, (p+1)^3 for vquad 1).  Any pointer may be NULL. */
+dftfe_status dftfe_mesh_info(dftfe_mesh mesh, int64_t* ndofs, int64_t* ncells,
+                             int* nodes_per_cell, int* quad_per_cell);
+
+/* Coordinates in HOST memory: node_xyz (M x 3) and, if non-NULL, quad_xyz
+ * (ncells x quad_per_cell x 3) of the potential quadrature points, both in the
+ * numbering above (used by callers to evaluate V and projectors).  Either may be NULL. */
+dftfe_status dftfe_mesh_coords(dftfe_mesh mesh, double* node_xyz, double* quad_xyz);
+
+dftfe_status dftfe_mesh_destroy(dftfe_mesh mesh);
+
+/* ---------------------------------------------------------------- Hamiltonian */
+
+/* Build the device operator state on the current CUDA device: cell -> global
+ * map, lumped mass M (a1), the shared GLL stiffness, the packed product table
+ * P of Eq. gemmLoc, and storage for the N_c dense cell matrices.  stream: a
+ * cudaStream_t (NULL = legacy default stream) on which every later call of this
+ * ham runs.  The mesh must outlive the ham. */
+dftfe_status dftfe_ham_create(dftfe_mesh mesh, void* stream, dftfe_ham* out);
+
+/* Set the local potential (a2; Sec. 4.2, Eq. quadLocal / Eq. gemmLoc):
+ * v_quad is DEVICE memory, ncells x quad_per_cell FP64 values V(x_q).  Forms
+ * V^c for all cells with one packed-symmetric GEMM K = P V, adds the stiffness
+ * K^c = 1/2 int grad N . grad N, and stores H~^c = D_c^-1/2 (K^c + V^c) D_c^-1/2.
+ * Asynchronous; v_quad may be freed once the stream reaches this point. */
+dftfe_status dftfe_ham_set_potential(dftfe_ham ham, const double* v_quad);
+
+/* Set the nonlocal projector term (a3; Eq. nonlocalHamDiscrete, Alg. 4):
+ * nproj projectors in CSR by projector, all in HOST memory: rowptr (nproj+1),
+ * node (rowptr[nproj] global node indices), chi (projector values chi_a(x_j) at
+ * those nodes), h (nproj couplings, Ha).  With GLL collocation C_ja = M_jj chi_a(x_j),
+ * so the library stores C~ = M^1/2 chi and applies H~_nl = C~ diag(h) C~^T.
+ * nproj = 0 removes the term.  Copies the inputs; synchronises the stream. */
+dftfe_status dftfe_ham_set_nonlocal(dftfe_ham ham, int nproj, const double* h,
+                                    const int64_t* rowptr, const int64_t* node,
+                                    const double* chi);
+
+dftfe_status dftfe_ham_destroy(dftfe_ham ham);
+
+/* Copy device state out for inspection: mass (M doubles), cell_map
+ * (ncells x nodes_per_cell int32), cell matrices of cells [c0, c0+count)
+ * (count x n_c x n_c doubles).  All outputs DEVICE memory; any may be NULL. */
+dftfe_status dftfe_ham_export(dftfe_ham ham, double* mass, int32_t* cell_map,
+                              int64_t c0, int64_t count, double* cell_mats);
+
+/* Y = H~ X for an M x ncol block (a4 + a5; Eq. celldgemm and Alg. 4): gather to
+ * cells, dense per-cell product, colour-ordered scatter-add, plus C~ h C~^T X.
+ * X and Y in DEVICE memory, must not overlap. */
+dftfe_status dftfe_ham_apply(dftfe_ham ham, const double* X, int64_t ldx,
+                             double* Y, int64_t ldy, int ncol, dftfe_precision prec);
+
+/* --------------------------------------------------------------- ChFSI steps */
+
+/* Counter-based SplitMix64 uniforms in [-1/2, 1/2) (Steele, Lea, Flood 2014):
+ * out[i] = u(seed, offset + i) with u(s, k) = (mix(s + (k+1)*0x9E3779B97F4A7C15)
+ * >> 11) * 2^-53 - 1/2.  out is DEVICE memory (n doubles); runs on `stream`.
+ * For an M x ncol block with ld = ncol, element (i, j) uses k = i*ncol + j. */
+dftfe_status dftfe_random_uniform(double* out, int64_t n, uint64_t seed,
+                                  int64_t offset, void* stream);
+
+/* k-step Lanczos with full reorthogonalisation on H~ (a7; the paper only says
+ * the degree follows the upper bound of H~, Sec. 3.1).  v0: DEVICE start vector
+ * (M doubles) or NULL to use dftfe_random_uniform(seed, offset 0).  Writes to
+ * HOST out3 = {theta_min, theta_max, b}, b = theta_max + |beta_k| |s_k| (a
+ * Ritz-residual upper bound).  Synchronises the stream. */
+dftfe_status dftfe_lanczos(dftfe_ham ham, int k, const double* v0, uint64_t seed,
+                           double* out3);
+
+/* First-pass bounds from dftfe_lanczos: a0 = theta_min, b as above,
+ * a = theta_min + (b - theta_min) * max(4 nstates / M, 0.05).  Host out. */
+dftfe_status dftfe_spectrum_bounds(dftfe_ham ham, int k, uint64_t seed, int nstates,
+                                   dftfe_bounds* out);
+
+/* Chebyshev filter in place on ncol columns (a4-a6; Eq. chebyfilter): degree m
+ * applications of H~ with the scaled (a0 finite) or unscaled (a0 = NaN)
+ * three-term recurrence; X <- p_m(H~) X.  The caller filters a block of B_f
+ * columns per call (Sec. 4.3 blocking).  Requires b > a, and a0 < a when scaled. */
+dftfe_status dftfe_chebyshev_filter(dftfe_ham ham, double* X, int64_t ld, int ncol,
+                                    int degree, const dftfe_bounds* bounds,
+                                    dftfe_precision prec);
+
+/* Cholesky-Gram-Schmidt in place (a8, a9; Alg. 2 steps 1a, 2a, 3b):
+ * S = X^T X (lower triangle), S = L L^T, X <- X L^-T.  DFTFE_ERR_NOT_SPD when a
+ * Cholesky pivot is not above 1e-14 times its diagonal entry of S (numerically
+ * singular overlap); X is then untouched.  Synchronises the stream (reads the factorisation status). */
+dftfe_status dftfe_cholgs(dftfe_ham ham, double* X, int64_t ld, int ncol,
+                          dftfe_precision prec);
+
+/* Rayleigh-Ritz on orthonormal X (a10-a12; Alg. 2 steps 1b, 2b-c, 3a):
+ * W = H~ X, H^ = X^T W (lower triangle, symmetric), H^ = Q Theta Q^T with
+ * Theta ascending and each column of Q signed so its largest-|.| entry is
+ * positive, X <- X Q.  evals: DEVICE, ncol doubles.  HX: DEVICE M x ncol (ldhx)
+ * receiving W Q = H~ X_new, or NULL (the library then uses its own workspace).
+ * Synchronises the stream. */
+dftfe_status dftfe_rayleigh_ritz(dftfe_ham ham, double* X, int64_t ld, int ncol,
+                                 double* evals, double* HX, int64_t ldhx,
+                                 dftfe_precision prec);
+
+/* Residual norms (a13): kind 0 -> ||W_i - theta_i X_i||_2 in the Loewdin basis
+ * (X orthonormal); kind 1 -> ||H psi - theta M psi|| / ||psi|| with
+ * psi = M^-1/2 x (the generalised form).  X, HX (ld), evals, resid: DEVICE. */
+dftfe_status dftfe_residuals(dftfe_ham ham, const double* X, const double* HX,
+                             int64_t ld, int ncol, const double* evals,
+                             double* resid, int kind);
+
+/* One ChFSI pass (Sec. 3.1-3.2): filter each block of `block` columns with the
+ * same bounds, CholGS on all ncol columns, Rayleigh-Ritz, Loewdin residuals,
+ * then the bounds update a <- theta_ncol, a0 <- theta_1 (b kept; a0 stays NaN
+ * for the unscaled filter).  evals, resid: DEVICE (ncol each).  inout: HOST.
+ * Synchronises the stream. */
+dftfe_status dftfe_chfsi_pass(dftfe_ham ham, double* X, int64_t ld, int ncol,
+                              int block, int degree, dftfe_bounds* inout,
+                              double* evals, double* resid, dftfe_precision prec);
+
+/* ------------------------------------------------------------ instrumentation */
+
+/* Per-kernel timing with CUDA events recorded on the ham's stream around every
+ * launch of the named kernel family ("cell_gemm_fp64", "cell_gemm_mixed",
+ * "gram", "rotate", ...).  enable != 0 starts recording (and clears totals). */
+dftfe_status dftfe_profile_enable(dftfe_ham ham, int enable);
+/* Total milliseconds and number of timed launches of a kernel family since the
+ * last enable.  Synchronises the stream. */
+dftfe_status dftfe_profile_query(dftfe_ham ham, const char* kernel, double* total_ms,
+                                 int64_t* launches);
+
+/* Number of kernels this library has launched in this process (all handles). */
+int64_t dftfe_launch_count(void);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* dftfe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFTFE_GB300_H */

@@ -53,8 +53,9 @@ class Hamiltonian:
         self._Hc = None
 
     def cell_V(self, c):
+        """V^c_jk = sum_q (w_q detJ V(x_q)) N_j(x_q) N_k(x_q), as Nq^T diag(w detJ V) Nq."""
         wv = self.Wq * self.mesh.detJ * self.v_quad[c]
-        return np.einsum("qj,q,qk->jk", self.Nq, wv, self.Nq)
+        return (self.Nq.T * wv[None, :]) @ self.Nq
 
     def cell_matrix(self, c):
         d = 1.0 / np.sqrt(self.mesh.mass[self.mesh.cell_map[c]])
@@ -64,7 +65,7 @@ class Hamiltonian:
         if self._Hc is None:
             m = self.mesh
             wv = self.Wq[None, :] * m.detJ * self.v_quad
-            V = np.einsum("qj,cq,qk->cjk", self.Nq, wv, self.Nq)
+            V = np.matmul(self.Nq.T[None, :, :] * wv[:, None, :], self.Nq[None, :, :])
             d = 1.0 / np.sqrt(m.mass[m.cell_map])
             self._Hc = d[:, :, None] * (self.K[None] + V) * d[:, None, :]
         return self._Hc

@@ -1,0 +1,260 @@
+"""Python binding of libdftfe_gb300 (argument marshalling only).
+
+Every function has the name of the C entry point it calls (include/dftfe_gb300.h);
+all computation runs in the library's CUDA kernels.  Device arrays are torch
+tensors (FP64, CUDA, row-major with unit column stride; a column slice of a wider
+block is fine and its row stride is passed as the leading dimension).  Host arrays
+are numpy.  A non-zero status raises DftfeError with the library's message.
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2203_07820_gb300._build``); importing without it raises.
+"""
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdftfe_gb300.so")
+
+DFTFE_FP64 = 0
+DFTFE_MIXED_BF16X3 = 1
+
+STATUS = {0: "DFTFE_OK", 1: "DFTFE_ERR_ARG", 2: "DFTFE_ERR_OOM", 3: "DFTFE_ERR_CUDA",
+          4: "DFTFE_ERR_NOT_SPD", 5: "DFTFE_ERR_NOCONV", 6: "DFTFE_ERR_TIMEOUT",
+          7: "DFTFE_ERR_STATE"}
+
+
+class DftfeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("L", C.c_double * 3), ("ncell", C.c_int * 3), ("degree", C.c_int),
+                ("periodic", C.c_int * 3), ("vquad", C.c_int), ("nq1d", C.c_int)]
+
+
+class Bounds(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("a0", C.c_double)]
+
+    def __repr__(self):
+        return f"Bounds(a={self.a!r}, b={self.b!r}, a0={self.a0!r})"
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                      "(there is no CPU fallback)")
+_lib = C.CDLL(LIB_PATH)
+
+_vp, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+_SIGS = {
+    "dftfe_mesh_create": [C.POINTER(MeshDesc), C.POINTER(_vp)],
+    "dftfe_mesh_info": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_int), C.POINTER(_int)],
+    "dftfe_mesh_coords": [_vp, _vp, _vp],
+    "dftfe_mesh_destroy": [_vp],
+    "dftfe_ham_create": [_vp, _vp, C.POINTER(_vp)],
+    "dftfe_ham_set_potential": [_vp, _vp],
+    "dftfe_ham_set_nonlocal": [_vp, _int, _vp, _vp, _vp, _vp],
+    "dftfe_ham_destroy": [_vp],
+    "dftfe_ham_export": [_vp, _vp, _vp, _i64, _i64, _vp],
+    "dftfe_ham_apply": [_vp, _vp, _i64, _vp, _i64, _int, _int],
+    "dftfe_random_uniform": [_vp, _i64, C.c_uint64, _i64, _vp],
+    "dftfe_lanczos": [_vp, _int, _vp, C.c_uint64, _vp],
+    "dftfe_spectrum_bounds": [_vp, _int, C.c_uint64, _int, C.POINTER(Bounds)],
+    "dftfe_chebyshev_filter": [_vp, _vp, _i64, _int, _int, C.POINTER(Bounds), _int],
+    "dftfe_cholgs": [_vp, _vp, _i64, _int, _int],
+    "dftfe_rayleigh_ritz": [_vp, _vp, _i64, _int, _vp, _vp, _i64, _int],
+    "dftfe_residuals": [_vp, _vp, _vp, _i64, _int, _vp, _vp, _int],
+    "dftfe_chfsi_pass": [_vp, _vp, _i64, _int, _int, _int, C.POINTER(Bounds), _vp, _vp, _int],
+    "dftfe_profile_enable": [_vp, _int],
+    "dftfe_profile_query": [_vp, C.c_char_p, C.POINTER(_dbl), C.POINTER(_i64)],
+}
+for _name, _args in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.dftfe_launch_count.argtypes = []
+_lib.dftfe_launch_count.restype = C.c_int64
+_lib.dftfe_last_error.argtypes = []
+_lib.dftfe_last_error.restype = C.c_char_p
+
+
+def _check(rc):
+    if rc != 0:
+        raise DftfeError(rc, _lib.dftfe_last_error().decode())
+
+
+def _dev(t, name="array"):
+    """Pointer and leading dimension of a CUDA FP64 tensor with unit column stride."""
+    if t is None:
+        return None, 0
+    if not t.is_cuda or t.dtype.itemsize != 8 or not t.dtype.is_floating_point:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if t.dim() == 1:
+        return _vp(t.data_ptr()), 1
+    if t.dim() != 2 or (t.stride(1) != 1 and t.shape[1] > 1):
+        raise ValueError(f"{name} must be 2-D with unit column stride")
+    return _vp(t.data_ptr()), t.stride(0)
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(_vp)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return _vp(torch.cuda.current_stream().cuda_stream)
+    return _vp(int(stream))
+
+
+def lib():
+    """The loaded ctypes library (for tests that call the ABI directly)."""
+    return _lib
+
+
+# ------------------------------------------------------------------ mesh
+def dftfe_mesh_create(L, ncell, degree, vquad=0, nq1d=0):
+    L = np.broadcast_to(np.asarray(L, np.float64), (3,))
+    n = np.broadcast_to(np.asarray(ncell, np.int64), (3,))
+    d = MeshDesc((C.c_double * 3)(*L), (C.c_int * 3)(*[int(x) for x in n]), int(degree),
+                 (C.c_int * 3)(1, 1, 1), int(vquad), int(nq1d))
+    out = _vp()
+    _check(_lib.dftfe_mesh_create(C.byref(d), C.byref(out)))
+    return out
+
+
+def dftfe_mesh_info(mesh):
+    nd, ncl, npc, nqp = _i64(), _i64(), _int(), _int()
+    _check(_lib.dftfe_mesh_info(mesh, C.byref(nd), C.byref(ncl), C.byref(npc), C.byref(nqp)))
+    return nd.value, ncl.value, npc.value, nqp.value
+
+
+def dftfe_mesh_coords(mesh, nodes=True, quad=True):
+    nd, ncl, npc, nqp = dftfe_mesh_info(mesh)
+    node_xyz = np.empty((nd, 3)) if nodes else None
+    quad_xyz = np.empty((ncl, nqp, 3)) if quad else None
+    _check(_lib.dftfe_mesh_coords(mesh, None if node_xyz is None else node_xyz.ctypes.data_as(_vp),
+                                  None if quad_xyz is None else quad_xyz.ctypes.data_as(_vp)))
+    return node_xyz, quad_xyz
+
+
+def dftfe_mesh_destroy(mesh):
+    _check(_lib.dftfe_mesh_destroy(mesh))
+
+
+# ------------------------------------------------------------ Hamiltonian
+def dftfe_ham_create(mesh, stream=None):
+    out = _vp()
+    _check(_lib.dftfe_ham_create(mesh, _stream(stream), C.byref(out)))
+    return out
+
+
+def dftfe_ham_set_potential(ham, v_quad):
+    p, _ = _dev(v_quad.reshape(-1), "v_quad")
+    _check(_lib.dftfe_ham_set_potential(ham, p))
+
+
+def dftfe_ham_set_nonlocal(ham, h, rowptr, node, chi):
+    h, ph = _host(h, np.float64)
+    rowptr, pr = _host(rowptr, np.int64)
+    node, pn = _host(node, np.int64)
+    chi, pc = _host(chi, np.float64)
+    _check(_lib.dftfe_ham_set_nonlocal(ham, int(h.size), ph, pr, pn, pc))
+
+
+def dftfe_ham_destroy(ham):
+    _check(_lib.dftfe_ham_destroy(ham))
+
+
+def dftfe_ham_export(ham, mass=None, cell_map=None, c0=0, cell_mats=None):
+    pm = None if mass is None else _vp(mass.data_ptr())
+    pc = None if cell_map is None else _vp(cell_map.data_ptr())
+    count = 0 if cell_mats is None else cell_mats.shape[0]
+    pmat = None if cell_mats is None else _vp(cell_mats.data_ptr())
+    _check(_lib.dftfe_ham_export(ham, pm, pc, int(c0), int(count), pmat))
+
+
+def dftfe_ham_apply(ham, X, Y, prec=DFTFE_FP64):
+    px, ldx = _dev(X, "X")
+    py, ldy = _dev(Y, "Y")
+    ncol = 1 if X.dim() == 1 else X.shape[1]
+    _check(_lib.dftfe_ham_apply(ham, px, ldx, py, ldy, ncol, prec))
+
+
+# ------------------------------------------------------------ ChFSI steps
+def dftfe_random_uniform(out, seed, offset=0, stream=None):
+    _check(_lib.dftfe_random_uniform(_vp(out.data_ptr()), out.numel(), C.c_uint64(seed), int(offset),
+                                     _stream(stream)))
+
+
+def dftfe_lanczos(ham, k, v0=None, seed=0):
+    out = (C.c_double * 3)()
+    pv = None if v0 is None else _vp(v0.data_ptr())
+    _check(_lib.dftfe_lanczos(ham, int(k), pv, C.c_uint64(seed), C.cast(out, _vp)))
+    return out[0], out[1], out[2]
+
+
+def dftfe_spectrum_bounds(ham, k, seed, nstates):
+    b = Bounds()
+    _check(_lib.dftfe_spectrum_bounds(ham, int(k), C.c_uint64(seed), int(nstates), C.byref(b)))
+    return b
+
+
+def make_bounds(a, b, a0=math.nan):
+    return Bounds(float(a), float(b), float(a0))
+
+
+def dftfe_chebyshev_filter(ham, X, degree, bounds, prec=DFTFE_FP64):
+    px, ld = _dev(X, "X")
+    _check(_lib.dftfe_chebyshev_filter(ham, px, ld, X.shape[1], int(degree), C.byref(bounds), prec))
+
+
+def dftfe_cholgs(ham, X, prec=DFTFE_FP64):
+    px, ld = _dev(X, "X")
+    _check(_lib.dftfe_cholgs(ham, px, ld, X.shape[1], prec))
+
+
+def dftfe_rayleigh_ritz(ham, X, evals, HX=None, prec=DFTFE_FP64):
+    px, ld = _dev(X, "X")
+    ph, ldh = _dev(HX, "HX")
+    _check(_lib.dftfe_rayleigh_ritz(ham, px, ld, X.shape[1], _vp(evals.data_ptr()), ph, ldh, prec))
+
+
+def dftfe_residuals(ham, X, HX, evals, resid, kind=0):
+    px, ld = _dev(X, "X")
+    ph, ldh = _dev(HX, "HX")
+    if ldh != ld:
+        raise ValueError("X and HX must share the leading dimension")
+    _check(_lib.dftfe_residuals(ham, px, ph, ld, X.shape[1], _vp(evals.data_ptr()),
+                                _vp(resid.data_ptr()), int(kind)))
+
+
+def dftfe_chfsi_pass(ham, X, block, degree, bounds, evals, resid, prec=DFTFE_FP64):
+    px, ld = _dev(X, "X")
+    _check(_lib.dftfe_chfsi_pass(ham, px, ld, X.shape[1], int(block), int(degree), C.byref(bounds),
+                                 _vp(evals.data_ptr()), _vp(resid.data_ptr()), prec))
+    return bounds
+
+
+# -------------------------------------------------------- instrumentation
+def dftfe_profile_enable(ham, enable=True):
+    _check(_lib.dftfe_profile_enable(ham, 1 if enable else 0))
+
+
+def dftfe_profile_query(ham, kernel):
+    ms, n = _dbl(), _i64()
+    _check(_lib.dftfe_profile_query(ham, kernel.encode(), C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def dftfe_launch_count():
+    return _lib.dftfe_launch_count()
+
+
+def dftfe_last_error():
+    return _lib.dftfe_last_error().decode()

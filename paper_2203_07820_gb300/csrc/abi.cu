@@ -1,0 +1,195 @@
+// Orchestration of the pass steps behind the C ABI: Lanczos bounds (a7),
+// Cholesky-Gram-Schmidt (a8, a9), Rayleigh-Ritz (a10-a12), residuals (a13), the pass
+// (Sec. 3.1-3.2 with Alg. 2 read as orthonormalise-first), random numbers, profiling.
+#include "internal.h"
+
+#include <cmath>
+
+namespace dftfe {
+
+static int read_status(dftfe_ham h, int* d_status) {
+  int st = 0;
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
+static void cholgs_impl(dftfe_ham h, double* X, int64_t ld, int ncol) {
+  auto* m = h->mesh;
+  const int N = ncol;
+  double* S = (double*)ws_get(h, "S", sizeof(double) * (size_t)N * N);
+  double* Z = (double*)ws_get(h, "Zinv", sizeof(double) * (size_t)N * N);
+  int* st = (int*)ws_get(h, "status", sizeof(int) * 4);
+  const int nsplit = gram_nsplit(h, m->M, N);
+  double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N * N);
+  gram_lower(h, X, ld, X, ld, m->M, N, S, part, nsplit);
+  potrf(h->stream, S, N, st);
+  const int s = read_status(h, st);
+  if (s == DFTFE_ERR_NOT_SPD) throw Error(DFTFE_ERR_NOT_SPD, "overlap matrix is not positive definite");
+  trtri_lower_to_upper_t(h->stream, S, Z, N);
+  rotate_inplace(h, X, ld, m->M, N, Z, true);
+}
+
+static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals, double* W, int64_t ldw) {
+  auto* m = h->mesh;
+  const int N = ncol;
+  apply_combo(h, X, ld, nullptr, 0, W, ldw, N, 1.0, 0.0, 0.0);
+  double* Hh = (double*)ws_get(h, "Hhat", sizeof(double) * (size_t)N * N);
+  double* Q = (double*)ws_get(h, "Q", sizeof(double) * (size_t)N * N);
+  int* st = (int*)ws_get(h, "status", sizeof(int) * 4);
+  const int nsplit = gram_nsplit(h, m->M, N);
+  double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N * N);
+  gram_lower(h, X, ld, W, ldw, m->M, N, Hh, part, nsplit);
+  syevd(h, Hh, N, evals, Q, st);
+  const int s = read_status(h, st);
+  if (s == DFTFE_ERR_NOCONV) throw Error(DFTFE_ERR_NOCONV, "subspace eigensolver did not converge");
+  rotate_inplace(h, X, ld, m->M, N, Q, false);
+  rotate_inplace(h, W, ldw, m->M, N, Q, false);
+}
+
+}  // namespace dftfe
+
+using namespace dftfe;
+
+extern "C" dftfe_status dftfe_random_uniform(double* out, int64_t n, uint64_t seed, int64_t offset,
+                                             void* stream) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(n >= 0 && offset >= 0, "negative size");
+  DFTFE_REQUIRE(out || n == 0, "null output");
+  random_uniform((cudaStream_t)stream, out, n, seed, offset);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && out3, "null argument");
+  DFTFE_REQUIRE(k >= 1 && k <= 200, "k must be in 1..200");
+  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  lanczos(h, k, v0, seed, out3);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_spectrum_bounds(dftfe_ham h, int k, uint64_t seed, int nstates,
+                                              dftfe_bounds* out) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && out, "null argument");
+  DFTFE_REQUIRE(k >= 1 && k <= 200 && nstates >= 1, "bad k / nstates");
+  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  double r[3];
+  lanczos(h, k, nullptr, seed, r);
+  const double frac = std::max(4.0 * nstates / (double)h->mesh->M, 0.05);
+  out->a0 = r[0];
+  out->b = r[2];
+  out->a = r[0] + (r[2] - r[0]) * frac;
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_cholgs(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_precision prec) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && X, "null argument");
+  DFTFE_REQUIRE(ncol >= 1 && ncol <= 2048 && ld >= ncol, "bad ncol / ld");
+  DFTFE_REQUIRE(ncol <= h->mesh->M, "more columns than DoFs");
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3, "unknown precision");
+  cholgs_impl(h, X, ld, ncol);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_rayleigh_ritz(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals,
+                                            double* HX, int64_t ldhx, dftfe_precision prec) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && X && evals, "null argument");
+  DFTFE_REQUIRE(ncol >= 1 && ncol <= 2048 && ld >= ncol, "bad ncol / ld");
+  DFTFE_REQUIRE(!HX || ldhx >= ncol, "bad ldhx");
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3, "unknown precision");
+  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  double* W = HX;
+  int64_t ldw = ldhx;
+  if (!W) {
+    W = (double*)ws_get(h, "W", sizeof(double) * (size_t)h->mesh->M * ncol);
+    ldw = ncol;
+  }
+  rr_impl(h, X, ld, ncol, evals, W, ldw);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_residuals(dftfe_ham h, const double* X, const double* HX, int64_t ld, int ncol,
+                                        const double* evals, double* resid, int kind) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && X && HX && evals && resid, "null argument");
+  DFTFE_REQUIRE(ncol >= 1 && ld >= ncol, "bad ncol / ld");
+  DFTFE_REQUIRE(kind == 0 || kind == 1, "kind must be 0 or 1");
+  residual_norms(h, X, ld, HX, ld, h->mesh->M, ncol, evals, resid, kind);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_chfsi_pass(dftfe_ham h, double* X, int64_t ld, int ncol, int block, int degree,
+                                         dftfe_bounds* inout, double* evals, double* resid,
+                                         dftfe_precision prec) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && X && inout && evals && resid, "null argument");
+  DFTFE_REQUIRE(ncol >= 1 && ncol <= 2048 && ld >= ncol && block >= 1 && degree >= 0, "bad sizes");
+  DFTFE_REQUIRE(ncol <= h->mesh->M, "more columns than DoFs");
+  DFTFE_REQUIRE(inout->b > inout->a, "need b > a");
+  DFTFE_REQUIRE(std::isnan(inout->a0) || inout->a0 < inout->a, "need a0 < a for the scaled filter");
+  DFTFE_REQUIRE(prec == DFTFE_FP64, "dftfe_chfsi_pass: precision not built");
+  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  auto* m = h->mesh;
+  {
+    ProfScope ps(h, "pass_filter");
+    for (int j0 = 0; j0 < ncol; j0 += block) {
+      const int nb = std::min(block, ncol - j0);
+      chebyshev_filter(h, X + j0, ld, nb, degree, *inout);
+    }
+  }
+  {
+    ProfScope ps(h, "pass_cholgs");
+    cholgs_impl(h, X, ld, ncol);
+  }
+  double* W = (double*)ws_get(h, "W", sizeof(double) * (size_t)m->M * ncol);
+  {
+    ProfScope ps(h, "pass_rr");
+    rr_impl(h, X, ld, ncol, evals, W, ncol);
+  }
+  residual_norms(h, X, ld, W, ncol, m->M, ncol, evals, resid, 0);
+  double ends[2];
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[0], evals, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[1], evals + ncol - 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  inout->a = ends[1];
+  if (!std::isnan(inout->a0)) inout->a0 = ends[0];
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_profile_enable(dftfe_ham h, int enable) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h, "null ham");
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  for (auto& kv : h->timers) {
+    kv.second.used = 0;
+    kv.second.launches = 0;
+    kv.second.total_ms = 0;
+  }
+  h->profiling = enable != 0;
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_profile_query(dftfe_ham h, const char* kernel, double* total_ms,
+                                            int64_t* launches) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && kernel && total_ms && launches, "null argument");
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  auto it = h->timers.find(kernel);
+  double ms = 0.0;
+  int64_t n = 0;
+  if (it != h->timers.end()) {
+    for (size_t i = 0; i < it->second.used; ++i) {
+      float t = 0.f;
+      DFTFE_CHECK_CUDA(cudaEventElapsedTime(&t, it->second.events[i].first, it->second.events[i].second));
+      ms += t;
+    }
+    n = it->second.launches;
+  }
+  *total_ms = ms;
+  *launches = n;
+  ABI_END
+}

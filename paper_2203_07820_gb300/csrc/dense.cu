@@ -1,0 +1,740 @@
+// Dense FP64 kernels of Cholesky-Gram-Schmidt and Rayleigh-Ritz (a8-a13), the Lanczos
+// bound (a7) and the counter-based random numbers.
+//
+//  gram_lower   C = A^T B, lower triangle (Alg. 2 steps 1a/1b; only the lower triangle
+//               is formed, as in Sec. 4.4), split over the long M dimension with a
+//               fixed-order second-stage sum (deterministic).
+//  potrf        S = L L^T, left-looking, one CTA (Alg. 2 step 2a).
+//  trtri        Z = L^-T, one thread per column of L^-1 (forward substitution).
+//  rotate       X <- X Z in place, row panels staged in shared memory (steps 3a/3b).
+//  syevd        H^ = Q Theta Q^T: Householder tridiagonalisation, accumulation of Q,
+//               implicit-shift QL on the tridiagonal (Bowdler, Martin, Reinsch,
+//               Wilkinson, Numer. Math. 11, 1968) with the rotations replayed on Q,
+//               then ascending sort and the sign convention (step 2b-c).
+//  residuals    ||W_i - theta_i X_i|| or the generalised form (a13).
+#include "internal.h"
+
+#include <cmath>
+#include <vector>
+
+namespace dftfe {
+
+static unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ----------------------------------------------------------- block reduction
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
+    red[NT / 32] = t;
+  }
+  __syncthreads();
+  return red[NT / 32];
+}
+
+// ------------------------------------------------------------------ Gram
+constexpr int GT = 64, GK = 16;
+__global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ A, int64_t lda,
+                                                      const double* __restrict__ B, int64_t ldb,
+                                                      int64_t M, int N, int64_t rows_per_split,
+                                                      const int32_t* __restrict__ tiles,
+                                                      double* __restrict__ part) {
+  __shared__ double As[GK][GT];
+  __shared__ double Bs[GK][GT];
+  const int ti = tiles[2 * blockIdx.x], tj = tiles[2 * blockIdx.x + 1];
+  const int i0 = ti * GT, j0 = tj * GT;
+  const int64_t m0 = (int64_t)blockIdx.y * rows_per_split;
+  const int64_t m1 = min(M, m0 + rows_per_split);
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int64_t mm = m0; mm < m1; mm += GK) {
+    for (int e = threadIdx.x; e < GK * GT; e += 256) {
+      const int kk = e / GT, c = e % GT;
+      const int64_t row = mm + kk;
+      const bool rok = row < m1;
+      As[kk][c] = (rok && i0 + c < N) ? A[row * lda + i0 + c] : 0.0;
+      Bs[kk][c] = (rok && j0 + c < N) ? B[row * ldb + j0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.y * N * N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gi = i0 + ty + 16 * i;
+    if (gi >= N) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gj = j0 + tx + 16 * j;
+      if (gj < N) out[(int64_t)gi * N + gj] = acc[i][j];
+    }
+  }
+}
+
+// C[i][j] = C[j][i] = sum_s part[s][i][j] for i >= j (fixed order over s).
+__global__ void k_gram_reduce(const double* __restrict__ part, int nsplit, int N, double* __restrict__ C) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * N) return;
+  const int i = (int)(t / N), j = (int)(t % N);
+  if (i < j) return;
+  double s = 0.0;
+  for (int k = 0; k < nsplit; ++k) s += part[(int64_t)k * N * N + t];
+  C[(int64_t)i * N + j] = s;
+  C[(int64_t)j * N + i] = s;
+}
+
+int gram_nsplit(dftfe_ham h, int64_t M, int N) {
+  const int T = (N + GT - 1) / GT;
+  const int ntiles = T * (T + 1) / 2;
+  int64_t want = (4LL * h->sm_count + ntiles - 1) / ntiles;
+  int64_t maxs = std::max<int64_t>(1, M / 256);
+  return (int)std::max<int64_t>(1, std::min(want, maxs));
+}
+
+void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M,
+                int N, double* C, double* part, int nsplit) {
+  const int T = (N + GT - 1) / GT;
+  const int ntiles = T * (T + 1) / 2;
+  std::vector<int32_t> tl;
+  tl.reserve(2 * ntiles);
+  for (int i = 0; i < T; ++i)
+    for (int j = 0; j <= i; ++j) {
+      tl.push_back(i);
+      tl.push_back(j);
+    }
+  int32_t* d_tiles = (int32_t*)ws_get(h, "gram_tiles", sizeof(int32_t) * tl.size());
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(d_tiles, tl.data(), sizeof(int32_t) * tl.size(),
+                                   cudaMemcpyHostToDevice, h->stream));
+  const int64_t rows = (M + nsplit - 1) / nsplit;
+  {
+    ProfScope ps(h, "gram");
+    DFTFE_LAUNCH(k_gram_partial, dim3(ntiles, nsplit), 256, 0, h->stream, A, lda, B, ldb, M, N,
+                 rows, d_tiles, part);
+  }
+  DFTFE_LAUNCH(k_gram_reduce, nblk((int64_t)N * N), 256, 0, h->stream, part, nsplit, N, C);
+}
+
+// ---------------------------------------------------------------- Cholesky
+// Left-looking Cholesky of the lower triangle of A (N x N, row-major) in place; the
+// strict upper triangle is zeroed.  status = DFTFE_ERR_NOT_SPD when a pivot is not
+// larger than 1e-14 times its original diagonal entry (S numerically singular).
+__global__ void __launch_bounds__(1024) k_potrf(double* A, int N, int* status) {
+  __shared__ double diag, dorig;
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < N; ++j) {
+    if (threadIdx.x == 0) dorig = A[(int64_t)j * N + j];
+    __syncthreads();
+    for (int i = j + threadIdx.x; i < N; i += blockDim.x) {
+      double s = A[(int64_t)i * N + j];
+      const double* Li = A + (int64_t)i * N;
+      const double* Lj = A + (int64_t)j * N;
+      for (int k = 0; k < j; ++k) s -= Li[k] * Lj[k];
+      A[(int64_t)i * N + j] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double d = A[(int64_t)j * N + j];
+      if (!(d > 1e-14 * dorig) || !(dorig > 0.0) || !isfinite(d)) bad = 1;
+      else {
+        diag = sqrt(d);
+        A[(int64_t)j * N + j] = diag;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    for (int i = j + 1 + threadIdx.x; i < N; i += blockDim.x) A[(int64_t)i * N + j] /= diag;
+    __syncthreads();
+  }
+  if (!bad)
+    for (int64_t t = threadIdx.x; t < (int64_t)N * N; t += blockDim.x) {
+      const int i = (int)(t / N), j = (int)(t % N);
+      if (j > i) A[t] = 0.0;
+    }
+  if (threadIdx.x == 0) *status = bad ? (int)DFTFE_ERR_NOT_SPD : 0;
+}
+
+void potrf(cudaStream_t s, double* A, int N, int* d_status) {
+  DFTFE_LAUNCH(k_potrf, 1, 1024, 0, s, A, N, d_status);
+}
+
+// Z = L^-T: thread j solves L y = e_j by forward substitution and stores y as row j of Z.
+__global__ void k_trtri(const double* __restrict__ L, double* __restrict__ Z, int N) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  double* y = Z + (int64_t)j * N;
+  for (int i = 0; i < j; ++i) y[i] = 0.0;
+  for (int i = j; i < N; ++i) {
+    double s = (i == j) ? 1.0 : 0.0;
+    const double* Li = L + (int64_t)i * N;
+    for (int k = j; k < i; ++k) s -= Li[k] * y[k];
+    y[i] = s / Li[i];
+  }
+}
+
+void trtri_lower_to_upper_t(cudaStream_t s, const double* L, double* Z, int N) {
+  DFTFE_LAUNCH(k_trtri, nblk(N, 128), 128, 0, s, L, Z, N);
+}
+
+// ------------------------------------------------------------------ rotate
+// X[r0:r0+R, :] <- X[r0:r0+R, :] Z, in place.  Thread t owns columns t + 256 c.
+template <int R, int CPT>
+__global__ void __launch_bounds__(256) k_rotate(double* __restrict__ X, int64_t ld, int64_t M, int N,
+                                                const double* __restrict__ Z, int upper) {
+  extern __shared__ double xs[];  // R x N
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int rows = (int)min((int64_t)R, M - r0);
+  for (int t = threadIdx.x; t < R * N; t += 256) {
+    const int r = t / N, k = t % N;
+    xs[t] = r < rows ? X[(r0 + r) * ld + k] : 0.0;
+  }
+  __syncthreads();
+  double acc[R][CPT];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[r][c] = 0.0;
+  int jmax = -1;
+#pragma unroll
+  for (int c = 0; c < CPT; ++c)
+    if (threadIdx.x + 256 * c < N) jmax = threadIdx.x + 256 * c;
+  const int kend = upper ? jmax + 1 : (jmax >= 0 ? N : 0);
+  for (int k = 0; k < kend; ++k) {
+    double z[CPT];
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int j = threadIdx.x + 256 * c;
+      z[c] = j < N ? __ldg(Z + (int64_t)k * N + j) : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double xv = xs[r * N + k];
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) acc[r][c] = fma(xv, z[c], acc[r][c]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (r >= rows) break;
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const int j = threadIdx.x + 256 * c;
+      if (j < N) X[(r0 + r) * ld + j] = acc[r][c];
+    }
+  }
+}
+
+template <int R, int CPT>
+static void launch_rotate(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {
+  const size_t sh = (size_t)R * N * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_rotate<R, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024));
+    attr = true;
+  }
+  const unsigned grid = (unsigned)((M + R - 1) / R);
+  ProfScope ps(h, "rotate");
+  DFTFE_LAUNCH((k_rotate<R, CPT>), grid, 256, sh, h->stream, X, ld, M, N, Z, upper ? 1 : 0);
+}
+
+void rotate_inplace(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {
+  if (M == 0 || N == 0) return;
+  if (N <= 256) launch_rotate<32, 1>(h, X, ld, M, N, Z, upper);
+  else if (N <= 512) launch_rotate<32, 2>(h, X, ld, M, N, Z, upper);
+  else if (N <= 1024) launch_rotate<16, 4>(h, X, ld, M, N, Z, upper);
+  else if (N <= 2048) launch_rotate<8, 8>(h, X, ld, M, N, Z, upper);
+  else throw Error(DFTFE_ERR_ARG, "more than 2048 states are not supported");
+}
+
+// -------------------------------------------------------------- eigensolver
+// Householder step k on the symmetric A (N x N, full storage): x = A[k][k+1..N-1],
+// H_k = I - tau v v^T with v_0 = 1 maps x to beta e_1 (LAPACK dlarfg convention).
+// Each CTA rebuilds v in shared memory and computes p = tau A22 v for its rows.
+__global__ void __launch_bounds__(256) k_hh_matvec(const double* __restrict__ A, int N, int k,
+                                                   double* __restrict__ V, double* __restrict__ tau,
+                                                   double* __restrict__ d, double* __restrict__ e,
+                                                   double* __restrict__ p) {
+  extern __shared__ double sv[];  // n
+  __shared__ double red[9];
+  const int n = N - k - 1;
+  const double* xr = A + (int64_t)k * N + k + 1;
+  double part = 0.0;
+  for (int i = 1 + threadIdx.x; i < n; i += 256) part += xr[i] * xr[i];
+  const double xn2 = block_sum<256>(part, red);
+  const double x0 = xr[0];
+  double beta, t, scal;
+  if (xn2 == 0.0) {
+    beta = x0; t = 0.0; scal = 0.0;
+  } else {
+    beta = -copysign(sqrt(x0 * x0 + xn2), x0);
+    t = (beta - x0) / beta;
+    scal = 1.0 / (x0 - beta);
+  }
+  for (int i = threadIdx.x; i < n; i += 256) sv[i] = (i == 0) ? 1.0 : xr[i] * scal;
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < n; i += 256) V[(int64_t)k * N + i] = sv[i];
+    if (threadIdx.x == 0) {
+      tau[k] = t;
+      d[k] = A[(int64_t)k * N + k];
+      e[k] = beta;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
+    const double* row = A + (int64_t)(k + 1 + i) * N + k + 1;
+    double s = 0.0;
+    for (int j = lane; j < n; j += 32) s = fma(row[j], sv[j], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) p[i] = t * s;
+  }
+}
+
+// A22 -= v w^T + w v^T with w = p - (tau/2)(p.v) v.
+__global__ void __launch_bounds__(256) k_hh_update(double* __restrict__ A, int N, int k,
+                                                   const double* __restrict__ V,
+                                                   const double* __restrict__ tau,
+                                                   const double* __restrict__ p) {
+  __shared__ double red[9];
+  const int n = N - k - 1;
+  const double* v = V + (int64_t)k * N;
+  double part = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) part += p[i] * v[i];
+  const double pv = block_sum<256>(part, red);
+  const double a2 = -0.5 * tau[k] * pv;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const double vi = v[i], wi = p[i] + a2 * vi;
+    double* row = A + (int64_t)(k + 1 + i) * N + k + 1;
+    for (int j = threadIdx.x; j < n; j += 256) {
+      const double wj = p[j] + a2 * v[j];
+      row[j] -= vi * wj + wi * v[j];
+    }
+  }
+}
+
+__global__ void k_hh_tail(const double* A, int N, double* d, double* e) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (N >= 2) {
+    d[N - 2] = A[(int64_t)(N - 2) * N + N - 2];
+    e[N - 2] = A[(int64_t)(N - 1) * N + N - 2];
+  }
+  d[N - 1] = A[(int64_t)(N - 1) * N + N - 1];
+  e[N - 1] = 0.0;
+}
+
+__global__ void k_identity(double* Q, int N) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < (int64_t)N * N) Q[t] = (t / N == t % N) ? 1.0 : 0.0;
+}
+
+// Q <- H_k Q on rows/cols k+1..N-1; thread = column (owns it entirely).
+__global__ void k_formq(double* __restrict__ Q, int N, int k, const double* __restrict__ V,
+                        const double* __restrict__ tau) {
+  const int n = N - k - 1;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double* v = V + (int64_t)k * N;
+  const double t = tau[k];
+  double* col = Q + (int64_t)(k + 1) * N + k + 1 + j;
+  double w = 0.0;
+  for (int i = 0; i < n; ++i) w = fma(v[i], col[(int64_t)i * N], w);
+  w *= t;
+  for (int i = 0; i < n; ++i) col[(int64_t)i * N] -= v[i] * w;
+}
+
+// Implicit QL with Wilkinson shifts on (d, e); rotations are replayed on the rows of Z
+// this CTA holds in shared memory.  Every CTA runs the same scalar recurrence (lane 0),
+// so all agree on d; CTA 0 writes it back.
+__global__ void __launch_bounds__(32) k_tql(double* __restrict__ dg, double* __restrict__ eg,
+                                            double* __restrict__ Z, int N, int R, int* status) {
+  extern __shared__ double sm[];
+  double* d = sm;                 // N
+  double* e = d + N;              // N
+  double* cs = e + N;             // N
+  double* sn = cs + N;            // N
+  double* zr = sn + N;            // R x (N+1)
+  __shared__ int nrot, base, fail;
+  const int r0 = blockIdx.x * R;
+  const int myrow = r0 + threadIdx.x;
+  const bool have = threadIdx.x < R && myrow < N;
+  for (int i = threadIdx.x; i < N; i += 32) {
+    d[i] = dg[i];
+    e[i] = (i < N - 1) ? eg[i] : 0.0;
+  }
+  for (int r = 0; r < R; ++r)
+    if (r0 + r < N)
+      for (int j = threadIdx.x; j < N; j += 32) zr[r * (N + 1) + j] = Z[(int64_t)(r0 + r) * N + j];
+  if (threadIdx.x == 0) fail = 0;
+  __syncwarp();
+  const double eps = 2.220446049250313e-16;
+  for (int l = 0; l < N; ++l) {
+    int iter = 0;
+    while (true) {
+      // lane 0 performs one QL sweep (or detects convergence) and records the rotations
+      if (threadIdx.x == 0) {
+        nrot = 0;
+        int m = l;
+        for (; m < N - 1; ++m) {
+          const double dd = fabs(d[m]) + fabs(d[m + 1]);
+          if (fabs(e[m]) <= eps * dd) break;
+        }
+        if (m == l) {
+          nrot = -1;
+        } else if (iter >= 60) {
+          nrot = -1;
+          fail = 1;
+        } else {
+          ++iter;
+          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+          double r = hypot(g, 1.0);
+          g = d[m] - d[l] + e[l] / (g + copysign(r, g));
+          double s = 1.0, c = 1.0, p = 0.0;
+          int i = m - 1;
+          bool early = false;
+          for (; i >= l; --i) {
+            const double f = s * e[i], b = c * e[i];
+            r = hypot(f, g);
+            e[i + 1] = r;
+            if (r == 0.0) {
+              d[i + 1] -= p;
+              e[m] = 0.0;
+              early = true;
+              break;
+            }
+            s = f / r;
+            c = g / r;
+            g = d[i + 1] - p;
+            r = (d[i] - g) * s + 2.0 * c * b;
+            p = s * r;
+            d[i + 1] = g + p;
+            g = c * r - b;
+            cs[nrot] = c;
+            sn[nrot] = s;
+            ++nrot;
+          }
+          base = m - 1;  // rotation t acts on columns (base - t, base - t + 1)
+          if (!early) {
+            d[l] -= p;
+            e[l] = g;
+            e[m] = 0.0;
+          }
+        }
+      }
+      __syncwarp();
+      const int nr = nrot;
+      if (nr < 0) break;
+      if (have) {
+        double* z = zr + threadIdx.x * (N + 1);
+        const int b0 = base;
+        for (int t = 0; t < nr; ++t) {
+          const int i = b0 - t;
+          const double f = z[i + 1];
+          z[i + 1] = sn[t] * z[i] + cs[t] * f;
+          z[i] = cs[t] * z[i] - sn[t] * f;
+        }
+      }
+      __syncwarp();
+    }
+    if (fail) break;
+  }
+  __syncwarp();
+  if (have)
+    for (int j = 0; j < N; ++j) Z[(int64_t)myrow * N + j] = zr[threadIdx.x * (N + 1) + j];
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < N; i += 32) dg[i] = d[i];
+    if (threadIdx.x == 0) *status = fail ? (int)DFTFE_ERR_NOCONV : 0;
+  }
+}
+
+void tridiag_ql(cudaStream_t s, double* d, double* e, double* Z, int N, int* d_status) {
+  int R = (int)std::min<int64_t>(32, std::max<int64_t>(1, 131072 / ((int64_t)(N + 1) * 8)));
+  size_t sh = (size_t)(4 * N + R * (N + 1)) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_tql, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+    attr = true;
+  }
+  if (sh > 220 * 1024) throw Error(DFTFE_ERR_ARG, "dense eigensolver: N too large");
+  DFTFE_LAUNCH(k_tql, (unsigned)((N + R - 1) / R), 32, sh, s, d, e, Z, N, R, d_status);
+}
+
+// ascending order (ties by index) and the sign convention: the largest-|.| entry of each
+// eigenvector (first one on ties) is made positive.
+__global__ void k_rank(const double* d, int N, int* perm, double* evals) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double di = d[i];
+  int r = 0;
+  for (int j = 0; j < N; ++j) r += (d[j] < di) || (d[j] == di && j < i);
+  perm[r] = i;
+  evals[r] = di;
+}
+
+__global__ void __launch_bounds__(256) k_sign_copy(const double* __restrict__ Z, const int* perm, int N,
+                                                   double* __restrict__ Q) {
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  const int c = blockIdx.x;
+  const int src = perm[c];
+  double best = -1.0;
+  int bidx = N;
+  for (int r = threadIdx.x; r < N; r += 256) {
+    const double a = fabs(Z[(int64_t)r * N + src]);
+    if (a > best || (a == best && r < bidx)) { best = a; bidx = r; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double o = bv[threadIdx.x + s];
+      const int oi = bi[threadIdx.x + s];
+      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = o;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const double sgn = Z[(int64_t)bi[0] * N + src] < 0.0 ? -1.0 : 1.0;
+  for (int r = threadIdx.x; r < N; r += 256) Q[(int64_t)r * N + c] = sgn * Z[(int64_t)r * N + src];
+}
+
+void syevd(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_status) {
+  cudaStream_t s = h->stream;
+  ProfScope ps(h, "syevd");
+  double* V = (double*)ws_get(h, "eig_V", sizeof(double) * (size_t)N * N);
+  double* Z = (double*)ws_get(h, "eig_Z", sizeof(double) * (size_t)N * N);
+  double* vec = (double*)ws_get(h, "eig_vec", sizeof(double) * 4 * (size_t)N + 64);
+  double* tau = vec, *d = vec + N, *e = vec + 2 * N, *p = vec + 3 * N;
+  int* perm = (int*)ws_get(h, "eig_perm", sizeof(int) * (size_t)N);
+  const int grid = std::max(1, std::min(h->sm_count * 2, (N + 7) / 8));
+  for (int k = 0; k + 2 < N; ++k) {
+    const int n = N - k - 1;
+    DFTFE_LAUNCH(k_hh_matvec, grid, 256, sizeof(double) * n, s, A, N, k, V, tau, d, e, p);
+    DFTFE_LAUNCH(k_hh_update, std::min(n, h->sm_count * 4), 256, 0, s, A, N, k, V, tau, p);
+  }
+  DFTFE_LAUNCH(k_hh_tail, 1, 32, 0, s, A, N, d, e);
+  DFTFE_LAUNCH(k_identity, nblk((int64_t)N * N), 256, 0, s, Z, N);
+  for (int k = N - 3; k >= 0; --k) {
+    const int n = N - k - 1;
+    DFTFE_LAUNCH(k_formq, nblk(n, 128), 128, 0, s, Z, N, k, V, tau);
+  }
+  tridiag_ql(s, d, e, Z, N, d_status);
+  DFTFE_LAUNCH(k_rank, nblk(N, 128), 128, 0, s, d, N, perm, evals);
+  DFTFE_LAUNCH(k_sign_copy, N, 256, 0, s, Z, perm, N, Q);
+}
+
+// ----------------------------------------------------------------- residuals
+__global__ void k_resid_partial(const double* __restrict__ X, int64_t ldx, const double* __restrict__ W,
+                                int64_t ldw, int64_t M, int ncol, const double* __restrict__ evals,
+                                const double* __restrict__ mass, int kind, int64_t rows,
+                                double* __restrict__ part) {
+  const int64_t i0 = (int64_t)blockIdx.x * rows;
+  const int64_t i1 = min(M, i0 + rows);
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    const double th = evals[c];
+    double num = 0.0, den = 0.0;
+    for (int64_t i = i0; i < i1; ++i) {
+      const double x = X[i * ldx + c];
+      const double r = W[i * ldw + c] - th * x;
+      if (kind == 0) num = fma(r, r, num);
+      else {
+        const double m = mass[i];
+        num = fma(m * r, r, num);
+        den = fma(x / m, x, den);
+      }
+    }
+    part[((int64_t)blockIdx.x * ncol + c) * 2] = num;
+    part[((int64_t)blockIdx.x * ncol + c) * 2 + 1] = den;
+  }
+}
+
+__global__ void k_resid_final(const double* __restrict__ part, int nchunk, int ncol, int kind,
+                              double* __restrict__ resid) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  double num = 0.0, den = 0.0;
+  for (int k = 0; k < nchunk; ++k) {
+    num += part[((int64_t)k * ncol + c) * 2];
+    den += part[((int64_t)k * ncol + c) * 2 + 1];
+  }
+  resid[c] = kind == 0 ? sqrt(num) : sqrt(num) / sqrt(den);
+}
+
+void residual_norms(dftfe_ham h, const double* X, int64_t ldx, const double* W, int64_t ldw, int64_t M,
+                     int ncol, const double* evals, double* resid, int kind) {
+  if (ncol <= 0) return;
+  const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(h->sm_count * 4, M / 64));
+  const int64_t rows = (M + nchunk - 1) / nchunk;
+  double* part = (double*)ws_get(h, "resid_part", sizeof(double) * 2 * (size_t)nchunk * ncol);
+  DFTFE_LAUNCH(k_resid_partial, nchunk, 256, 0, h->stream, X, ldx, W, ldw, M, ncol, evals, h->d_mass,
+               kind, rows, part);
+  DFTFE_LAUNCH(k_resid_final, nblk(ncol, 128), 128, 0, h->stream, part, nchunk, ncol, kind, resid);
+}
+
+// --------------------------------------------------------- random numbers
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_random(double* out, int64_t n, uint64_t seed, int64_t offset) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const uint64_t idx = (uint64_t)(offset + t);
+  const uint64_t z = splitmix_mix(seed + (idx + 1ULL) * 0x9E3779B97F4A7C15ULL);
+  out[t] = (double)(z >> 11) * 0x1.0p-53 - 0.5;
+}
+
+void random_uniform(cudaStream_t s, double* out, int64_t n, uint64_t seed, int64_t offset) {
+  if (n <= 0) return;
+  DFTFE_LAUNCH(k_random, nblk(n), 256, 0, s, out, n, seed, offset);
+}
+
+// ------------------------------------------------------------------ Lanczos
+constexpr int LZ_G = 512;
+// part[v*G + b] = partial dot of V[v] (stride M) with w over block b's rows.
+__global__ void __launch_bounds__(256) k_multidot_partial(const double* __restrict__ Vm, int nv,
+                                                          const double* __restrict__ w, int64_t M,
+                                                          double* __restrict__ part) {
+  __shared__ double red[9];
+  const int64_t rows = (M + gridDim.x - 1) / gridDim.x;
+  const int64_t i0 = blockIdx.x * rows, i1 = min(M, i0 + rows);
+  for (int v = 0; v < nv; ++v) {
+    const double* x = Vm + (int64_t)v * M;
+    double s = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += 256) s = fma(x[i], w[i], s);
+    s = block_sum<256>(s, red);
+    if (threadIdx.x == 0) part[v * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// out[v] = sum_b part[v*G + b] (fixed order); mode 1 stores sqrt.
+__global__ void k_multidot_final(const double* part, int nv, int G, double* out, int mode) {
+  const int v = threadIdx.x;
+  if (v >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < G; ++b) s += part[v * G + b];
+  out[v] = mode == 1 ? sqrt(s) : s;
+}
+
+// w = (w - a v) - b u   (a = *pa, b = *pb or 0)
+__global__ void k_lz_three_term(double* w, const double* v, const double* u, const double* pa,
+                                const double* pb, int64_t M) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double x = w[i] - pa[0] * v[i];
+  if (u) x = x - pb[0] * u[i];
+  w[i] = x;
+}
+
+// w -= sum_v hcoef[v] V[v]
+__global__ void k_lz_reorth(double* w, const double* Vm, int nv, const double* hcoef, int64_t M) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double s = 0.0;
+  for (int v = 0; v < nv; ++v) s = fma(hcoef[v], Vm[(int64_t)v * M + i], s);
+  w[i] -= s;
+}
+
+// out = w / *pn (0 if the norm is 0)
+__global__ void k_lz_scale(double* out, const double* w, const double* pn, int64_t M) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const double n = pn[0];
+  out[i] = n > 0.0 ? w[i] / n : 0.0;
+}
+
+__global__ void k_lz_tridiag(const double* alpha, const double* beta, int k, double* d, double* e, double* Z) {
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    d[i] = alpha[i];
+    e[i] = i < k - 1 ? beta[i] : 0.0;
+  }
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) Z[t] = (t / k == t % k) ? 1.0 : 0.0;
+}
+
+__global__ void k_lz_bound(const double* d, const double* Z, const double* beta, int k, double* out3) {
+  if (threadIdx.x != 0) return;
+  int imin = 0, imax = 0;
+  for (int i = 1; i < k; ++i) {
+    if (d[i] < d[imin]) imin = i;
+    if (d[i] > d[imax]) imax = i;
+  }
+  out3[0] = d[imin];
+  out3[1] = d[imax];
+  out3[2] = d[imax] + fabs(beta[k - 1]) * fabs(Z[(int64_t)(k - 1) * k + imax]);
+}
+
+void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3) {
+  auto* m = h->mesh;
+  const int64_t M = m->M;
+  cudaStream_t s = h->stream;
+  double* Vm = (double*)ws_get(h, "lz_V", sizeof(double) * (size_t)(k + 1) * M);
+  double* w = (double*)ws_get(h, "lz_w", sizeof(double) * (size_t)M);
+  double* sc = (double*)ws_get(h, "lz_scal", sizeof(double) * (size_t)(4 * k + 8 + k * k + 2 * k));
+  double* part = (double*)ws_get(h, "lz_part", sizeof(double) * (size_t)(k + 1) * LZ_G);
+  int* st = (int*)ws_get(h, "lz_status", sizeof(int));
+  double* alpha = sc;
+  double* beta = sc + k;
+  double* hco = sc + 2 * k;        // k + 1
+  double* nrm = sc + 3 * k + 1;    // 1
+  double* d = sc + 3 * k + 2;      // k
+  double* e = d + k;               // k
+  double* Z = e + k;               // k*k
+  double* d_out = Z + k * k;       // 3
+  if (v0) DFTFE_CHECK_CUDA(cudaMemcpyAsync(w, v0, sizeof(double) * M, cudaMemcpyDeviceToDevice, s));
+  else random_uniform(s, w, M, seed, 0);
+  DFTFE_LAUNCH(k_multidot_partial, LZ_G, 256, 0, s, w, 1, w, M, part);
+  DFTFE_LAUNCH(k_multidot_final, 1, 32, 0, s, part, 1, LZ_G, nrm, 1);
+  DFTFE_LAUNCH(k_lz_scale, nblk(M), 256, 0, s, Vm, w, nrm, M);
+  for (int j = 0; j < k; ++j) {
+    double* vj = Vm + (int64_t)j * M;
+    apply_combo(h, vj, 1, nullptr, 0, w, 1, 1, 1.0, 0.0, 0.0);
+    DFTFE_LAUNCH(k_multidot_partial, LZ_G, 256, 0, s, vj, 1, w, M, part);
+    DFTFE_LAUNCH(k_multidot_final, 1, 32, 0, s, part, 1, LZ_G, alpha + j, 0);
+    DFTFE_LAUNCH(k_lz_three_term, nblk(M), 256, 0, s, w, vj, j > 0 ? vj - M : nullptr, alpha + j,
+                 j > 0 ? beta + j - 1 : alpha + j, M);
+    for (int rep = 0; rep < 2; ++rep) {
+      DFTFE_LAUNCH(k_multidot_partial, LZ_G, 256, 0, s, Vm, j + 1, w, M, part);
+      DFTFE_LAUNCH(k_multidot_final, 1, 256, 0, s, part, j + 1, LZ_G, hco, 0);
+      DFTFE_LAUNCH(k_lz_reorth, nblk(M), 256, 0, s, w, Vm, j + 1, hco, M);
+    }
+    DFTFE_LAUNCH(k_multidot_partial, LZ_G, 256, 0, s, w, 1, w, M, part);
+    DFTFE_LAUNCH(k_multidot_final, 1, 32, 0, s, part, 1, LZ_G, beta + j, 1);
+    DFTFE_LAUNCH(k_lz_scale, nblk(M), 256, 0, s, Vm + (int64_t)(j + 1) * M, w, beta + j, M);
+  }
+  DFTFE_LAUNCH(k_lz_tridiag, 1, 256, 0, s, alpha, beta, k, d, e, Z);
+  tridiag_ql(s, d, e, Z, k, st);
+  DFTFE_LAUNCH(k_lz_bound, 1, 32, 0, s, d, Z, beta, k, d_out);
+  int hst = 0;
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(out3, d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&hst, st, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (hst) throw Error(DFTFE_ERR_NOCONV, "Lanczos tridiagonal eigensolve did not converge");
+}
+
+}  // namespace dftfe

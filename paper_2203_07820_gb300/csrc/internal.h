@@ -1,0 +1,193 @@
+// Internal declarations shared by the translation units of libdftfe_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+#include <map>
+#include <stdexcept>
+#include <atomic>
+
+#include "../../include/dftfe_gb300.h"
+
+namespace dftfe {
+
+// ------------------------------------------------------------------ errors
+struct Error : std::runtime_error {
+  dftfe_status code;
+  Error(dftfe_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+void set_error(const std::string& msg);
+void clear_error();
+const char* last_error();
+
+#define DFTFE_CHECK_CUDA(call)                                                        \
+  do {                                                                                \
+    cudaError_t e__ = (call);                                                         \
+    if (e__ != cudaSuccess)                                                           \
+      throw ::dftfe::Error(e__ == cudaErrorMemoryAllocation ? DFTFE_ERR_OOM : DFTFE_ERR_CUDA, \
+                           std::string(#call) + ": " + cudaGetErrorString(e__));      \
+  } while (0)
+
+#define DFTFE_REQUIRE(cond, msg)                                     \
+  do {                                                               \
+    if (!(cond)) throw ::dftfe::Error(DFTFE_ERR_ARG, (msg));         \
+  } while (0)
+
+// Every kernel launch goes through this macro: it counts the launch and checks
+// the launch status.
+extern std::atomic<int64_t> g_launches;
+#define DFTFE_LAUNCH(kernel, grid, block, smem, stream, ...)                     \
+  do {                                                                           \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                  \
+    ::dftfe::g_launches.fetch_add(1, std::memory_order_relaxed);                 \
+    DFTFE_CHECK_CUDA(cudaGetLastError());                                        \
+  } while (0)
+
+// ---------------------------------------------------------------- basis (host)
+struct Rule1D {
+  std::vector<double> x, w;
+};
+Rule1D gll_rule(int p);                         // p+1 GLL points
+Rule1D gauss_rule(int n);                       // n Gauss-Legendre points
+std::vector<double> barycentric_weights(const std::vector<double>& x);
+// T[q*n + j] = l_j(pts[q]) for the Lagrange basis of nodes x (n = x.size()).
+std::vector<double> lagrange_at(const std::vector<double>& x, const std::vector<double>& pts);
+// D[i*n + j] = l_j'(x_i) at the nodes themselves.
+std::vector<double> derivative_matrix(const std::vector<double>& x);
+
+// ------------------------------------------------------------------- handles
+}  // namespace dftfe
+
+struct dftfe_mesh_s {
+  double L[3];
+  int n[3];
+  int p, vquad, nq1d;
+  int n1;        // p+1
+  int nc;        // nodes per cell (p+1)^3
+  int nq;        // quadrature points per cell
+  int nq1;       // 1D quadrature points
+  int64_t g[3];  // nodes per axis
+  int64_t M;     // DoFs
+  int64_t Nc;    // cells
+  double h[3];
+  double detJ;
+  dftfe::Rule1D gll, quad;
+  std::vector<double> D;      // n1 x n1 derivative matrix at GLL nodes
+  std::vector<double> Lq;     // nq1 x n1: l_a at the potential quadrature points
+  std::vector<double> m1[3];  // 1D lumped mass per axis
+};
+
+namespace dftfe {
+
+// A grow-only device buffer.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  void* get(size_t need);
+  void release();
+};
+
+struct KernelTimer {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+  size_t used = 0;
+  double total_ms = 0;
+  int64_t launches = 0;
+};
+
+}  // namespace dftfe
+
+struct dftfe_ham_s {
+  dftfe_mesh mesh = nullptr;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  // a1: mesh data on the device
+  int32_t* d_map = nullptr;        // Nc x nc
+  double* d_mass = nullptr;        // M
+  double* d_minvsqrt = nullptr;    // M
+  // colouring (cells grouped by colour; no two cells of one colour share a node)
+  int ncolours = 0;
+  std::vector<int64_t> colour_off; // ncolours + 1
+  int32_t* d_colour_cells = nullptr;
+  // a2: cell matrices
+  double* d_K = nullptr;           // nc x nc shared stiffness
+  double* d_P = nullptr;           // Msym x nq packed basis products (Eq. gemmLoc)
+  int32_t* d_pairs = nullptr;      // Msym x 2 (j <= k)
+  double* d_wq = nullptr;          // nq quadrature weights * detJ
+  double* d_Hc = nullptr;          // Nc x nc x nc FP64
+  bool has_potential = false;
+  // a3: nonlocal (CSR by projector and by node)
+  int nproj = 0;
+  double* d_h = nullptr;
+  int64_t* d_prow = nullptr;  int32_t* d_pnode = nullptr;  double* d_pval = nullptr;
+  int64_t nsup = 0;
+  int32_t* d_snode = nullptr; int64_t* d_srow = nullptr;
+  int32_t* d_sproj = nullptr; double* d_sval = nullptr;
+  // workspace
+  std::map<std::string, dftfe::DevBuf> ws;
+  // profiling
+  bool profiling = false;
+  std::map<std::string, dftfe::KernelTimer> timers;
+};
+
+namespace dftfe {
+
+void* ws_get(dftfe_ham h, const char* name, size_t bytes);
+
+// Records an event pair around a kernel-family launch when profiling is on.
+struct ProfScope {
+  dftfe_ham h;
+  KernelTimer* t = nullptr;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(dftfe_ham h, const char* name);
+  ~ProfScope();
+};
+
+// ------------------------------------------------------------ device kernels
+// hx.cu
+void apply_combo(dftfe_ham h, const double* X, int64_t ldx, const double* Xprev, int64_t ldp,
+                 double* Z, int64_t ldz, int ncol, double alpha, double s1, double s2);
+void chebyshev_filter(dftfe_ham h, double* X, int64_t ld, int ncol, int degree,
+                      const dftfe_bounds& b);
+void copy_block(cudaStream_t s, const double* src, int64_t lds, double* dst, int64_t ldd,
+                int64_t rows, int ncol);
+
+// dense.cu
+void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb,
+                int64_t M, int N, double* C, double* part, int nsplit);
+int gram_nsplit(dftfe_ham h, int64_t M, int N);
+void potrf(cudaStream_t s, double* A, int N, int* d_status);
+void trtri_lower_to_upper_t(cudaStream_t s, const double* L, double* Z, int N);
+void rotate_inplace(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z,
+                    bool upper);
+void syevd(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_status);
+void tridiag_ql(cudaStream_t s, double* d, double* e, double* Z, int N, int* d_status);
+void residual_norms(dftfe_ham h, const double* X, int64_t ldx, const double* W, int64_t ldw,
+                    int64_t M, int ncol, const double* evals, double* resid, int kind);
+void random_uniform(cudaStream_t s, double* out, int64_t n, uint64_t seed, int64_t offset);
+void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3);
+
+}  // namespace dftfe
+
+// Wraps the body of every extern "C" entry point: exceptions become status codes.
+#define ABI_BEGIN \
+  try {         \
+    ::dftfe::clear_error();
+#define ABI_END                                     \
+  return DFTFE_OK;                                  \
+  }                                                 \
+  catch (const ::dftfe::Error& e) {                 \
+    ::dftfe::set_error(e.what());                   \
+    return e.code;                                  \
+  }                                                 \
+  catch (const std::bad_alloc&) {                   \
+    ::dftfe::set_error("host allocation failed");   \
+    return DFTFE_ERR_OOM;                           \
+  }                                                 \
+  catch (const std::exception& e) {                 \
+    ::dftfe::set_error(e.what());                   \
+    return DFTFE_ERR_CUDA;                          \
+  }

@@ -58,6 +58,16 @@ def random_block(seed, nrow, ncol):
     return out
 
 
+def random_rows(seed, rows, ncol):
+    """Rows `rows` of the block random_block(seed, nrow, ncol), without forming the rest."""
+    rows = np.asarray(rows, dtype=np.uint64)
+    idx = (rows[:, None] * np.uint64(ncol) + np.arange(ncol, dtype=np.uint64)[None, :]).ravel()
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & MASK) + (idx + np.uint64(1)) * np.uint64(GAMMA)
+    z = _mix_u64(z)
+    return ((z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53) - 0.5).reshape(len(rows), ncol)
+
+
 class Stream:
     """Sequential SplitMix64 stream; uniform() returns values in [0, 1)."""
 
@@ -149,7 +159,8 @@ def gaussian_wells(points, centres, depth, width, L):
     pts = np.asarray(points, dtype=np.float64)
     v = np.zeros(pts.shape[0])
     rcut = 8.0 * width
-    k = int(math.ceil((rcut + 0.5 * L) / L))
+    # after the minimum-image wrap every other image is at least L/2 away
+    k = 0 if rcut <= 0.5 * L else int(math.ceil((rcut + 0.5 * L) / L))
     shifts = [(i, j, l) for i in range(-k, k + 1) for j in range(-k, k + 1) for l in range(-k, k + 1)]
     for R in centres:
         d0 = _wrap(pts - R, L)

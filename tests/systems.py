@@ -1,0 +1,48 @@
+"""Seeded test systems built twice from the same synth inputs: once in the oracle,
+once through the C ABI (each side evaluates the model functions at its own mesh
+points)."""
+import math
+import numpy as np
+
+import oracle
+import synth
+
+
+def oracle_system(L, n, p, centres, depth, width, vquad=0, proj=None):
+    m = oracle.PeriodicMesh(L, n, p)
+    h = oracle.Hamiltonian(m, vquad=vquad)
+    Lb = np.broadcast_to(np.asarray(L, float), (3,))
+    h.set_potential(synth.gaussian_wells(m.quad_xyz(vquad).reshape(-1, 3), centres, depth, width, Lb[0]))
+    if proj is not None:
+        cent, w, rc, hcoup = proj
+        rowptr, node, chi = synth.projector_csr(m.node_xyz(), cent, w, rc, Lb[0])
+        h.set_nonlocal(hcoup, rowptr, node, chi)
+    return m, h
+
+
+def gpu_system(L, n, p, centres, depth, width, vquad=0, proj=None):
+    import torch
+    import paper_2203_07820_gb300 as dg
+    mesh = dg.dftfe_mesh_create(L, n, p, vquad=vquad)
+    ham = dg.dftfe_ham_create(mesh)
+    nxyz, qxyz = dg.dftfe_mesh_coords(mesh)
+    Lb = np.broadcast_to(np.asarray(L, float), (3,))
+    v = synth.gaussian_wells(qxyz.reshape(-1, 3), centres, depth, width, Lb[0])
+    dg.dftfe_ham_set_potential(ham, torch.from_numpy(v).cuda())
+    if proj is not None:
+        cent, w, rc, hcoup = proj
+        rowptr, node, chi = synth.projector_csr(nxyz, cent, w, rc, Lb[0])
+        dg.dftfe_ham_set_nonlocal(ham, hcoup, rowptr, node, chi)
+    torch.cuda.synchronize()
+    return mesh, ham
+
+
+def small_case(seed=0, n=(4, 3, 2), p=4, L=8.0, nl=True, vquad=0):
+    """A cube with a non-uniform cell count (odd axis -> 3 colours) and projectors."""
+    s = synth.Stream(seed)
+    cent = np.array([[L * s.uniform() for _ in range(3)] for _ in range(3)])
+    proj = None
+    if nl:
+        hc = np.array([0.5 + 1.5 * s.uniform() for _ in range(4 * len(cent))])
+        proj = (cent, 1.0, 2.5, hc)
+    return dict(L=L, n=n, p=p, centres=cent, depth=2.0, width=1.0, vquad=vquad, proj=proj)

@@ -1,0 +1,239 @@
+"""GPU parity: every step of the pass through the C ABI against the FP64 oracle on the
+same seeded inputs (element by element), at sizes that span several tiles, a ragged
+column tail, an odd cell count (3-colour axis) and p = 6 (343 nodes per cell)."""
+import math
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from systems import oracle_system, gpu_system, small_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_APPLY = 1e-12     # relative to max |Y|: FP64, different summation order
+TOL_EPS = 1e-9        # Ha, FP64 path (spec tolerance)
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_07820_gb300 as dg
+    return dg
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = {
+    "p4_432_nl": small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True),
+    "p6_223_nl": small_case(1, n=(2, 2, 3), p=6, L=7.0, nl=True),
+    "p3_333_gll": small_case(2, n=(3, 3, 3), p=3, L=6.0, nl=False, vquad=1),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def pair(request, dg):
+    c = CASES[request.param]
+    om, oh = oracle_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    yield om, oh, mesh, ham
+    dg.dftfe_ham_destroy(ham)
+    dg.dftfe_mesh_destroy(mesh)
+
+
+def test_a1_map_and_mass(dg, pair):
+    om, oh, mesh, ham = pair
+    mass = torch.empty(om.ndofs, dtype=torch.float64, device="cuda")
+    cmap = torch.empty((om.ncells, om.nodes_per_cell), dtype=torch.int32, device="cuda")
+    dg.dftfe_ham_export(ham, mass=mass, cell_map=cmap)
+    torch.cuda.synchronize()
+    assert np.array_equal(cmap.cpu().numpy(), om.cell_map)                   # bit-exact indices
+    assert _rel(mass.cpu().numpy(), om.mass) < 1e-14
+
+
+def test_a2_cell_matrices(dg, pair):
+    om, oh, mesh, ham = pair
+    cells = [0, om.ncells // 2, om.ncells - 1]
+    nc = om.nodes_per_cell
+    for c in cells:
+        out = torch.empty((1, nc, nc), dtype=torch.float64, device="cuda")
+        dg.dftfe_ham_export(ham, c0=c, cell_mats=out)
+        torch.cuda.synchronize()
+        ref = oh.cell_matrix(c)
+        assert _rel(out[0].cpu().numpy(), ref) < 1e-13
+
+
+@pytest.mark.parametrize("ncol", [1, 3, 4, 5, 32, 37, 70])
+def test_a4_a5_apply(dg, pair, ncol):
+    om, oh, mesh, ham = pair
+    X0 = synth.random_block(100 + ncol, om.ndofs, ncol)
+    X = torch.from_numpy(X0).cuda()
+    Y = torch.full_like(X, float("nan"))
+    dg.dftfe_ham_apply(ham, X, Y)
+    ref = oh.apply(X0)
+    assert _rel(Y.cpu().numpy(), ref) < TOL_APPLY
+
+
+def test_apply_strided_columns(dg, pair):
+    """A column slice of a wider block: the row stride is the leading dimension."""
+    om, oh, mesh, ham = pair
+    X0 = synth.random_block(7, om.ndofs, 48)
+    X = torch.from_numpy(X0).cuda()
+    Y = torch.zeros((om.ndofs, 64), dtype=torch.float64, device="cuda")
+    dg.dftfe_ham_apply(ham, X[:, 5:40], Y[:, 10:45])
+    ref = oh.apply(X0[:, 5:40])
+    y = Y.cpu().numpy()
+    assert _rel(y[:, 10:45], ref) < TOL_APPLY
+    assert np.all(y[:, :10] == 0) and np.all(y[:, 45:] == 0)
+
+
+def test_apply_is_deterministic(dg, pair):
+    om, oh, mesh, ham = pair
+    X = torch.from_numpy(synth.random_block(8, om.ndofs, 33)).cuda()
+    Y1, Y2 = torch.empty_like(X), torch.empty_like(X)
+    dg.dftfe_ham_apply(ham, X, Y1)
+    dg.dftfe_ham_apply(ham, X, Y2)
+    assert torch.equal(Y1, Y2)
+
+
+@pytest.mark.parametrize("scaled", [True, False])
+@pytest.mark.parametrize("ncol,degree", [(6, 1), (37, 9), (16, 14)])
+def test_a6_chebyshev_filter(dg, pair, scaled, ncol, degree):
+    om, oh, mesh, ham = pair
+    lam_lo, lam_hi, b = oracle.lanczos_bounds(oh.apply, synth.counter_uniform(5, om.ndofs), 20)
+    a = lam_lo + 0.1 * (b - lam_lo)
+    bd = oracle.Bounds(a, b, lam_lo if scaled else math.nan)
+    X0 = synth.random_block(11, om.ndofs, ncol)
+    X = torch.from_numpy(X0).cuda()
+    dg.dftfe_chebyshev_filter(ham, X, degree, dg.make_bounds(bd.a, bd.b, bd.a0))
+    ref = oracle.chebyshev_filter(oh.apply, X0, degree, bd)
+    assert _rel(X.cpu().numpy(), ref) < 1e-10
+
+
+def test_a7_lanczos(dg, pair):
+    om, oh, mesh, ham = pair
+    v0 = synth.counter_uniform(21, om.ndofs)
+    ref = oracle.lanczos_bounds(oh.apply, v0, 20)
+    got = dg.dftfe_lanczos(ham, 20, torch.from_numpy(v0).cuda())
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-10)
+    # seeded start vector drawn on the device equals the oracle's counter stream
+    got2 = dg.dftfe_lanczos(ham, 20, None, 21)
+    assert np.allclose(got2, ref, rtol=1e-10, atol=1e-10)
+
+
+def test_a8_a9_cholgs(dg, pair):
+    om, oh, mesh, ham = pair
+    N = 24
+    X0 = synth.random_block(12, om.ndofs, N) @ np.diag(np.linspace(1.0, 50.0, N))
+    X = torch.from_numpy(X0).cuda()
+    dg.dftfe_cholgs(ham, X)
+    ref, _, _ = oracle.cholgs(X0)
+    x = X.cpu().numpy()
+    assert _rel(x, ref) < 1e-11
+    assert np.abs(x.T @ x - np.eye(N)).max() < 1e-12
+
+
+def test_cholgs_not_spd_leaves_x_untouched(dg, pair):
+    om, oh, mesh, ham = pair
+    X0 = synth.random_block(13, om.ndofs, 6)
+    X0[:, 4] = X0[:, 1]
+    X = torch.from_numpy(X0).cuda()
+    with pytest.raises(dg.DftfeError) as e:
+        dg.dftfe_cholgs(ham, X)
+    assert e.value.code == 4
+    assert np.array_equal(X.cpu().numpy(), X0)
+
+
+def _cluster_projectors_match(theta, A, B, tol):
+    """Compare column blocks through their projectors on clusters of close eigenvalues."""
+    i = 0
+    N = len(theta)
+    while i < N:
+        j = i + 1
+        while j < N and theta[j] - theta[j - 1] < 1e-6:
+            j += 1
+        Pa = A[:, i:j] @ A[:, i:j].T if A.shape[0] <= 4000 else None
+        if Pa is not None:
+            Pb = B[:, i:j] @ B[:, i:j].T
+            assert np.abs(Pa - Pb).max() < tol
+        i = j
+
+
+def test_a10_a12_rayleigh_ritz(dg, pair):
+    om, oh, mesh, ham = pair
+    N = 20
+    Xo, _, _ = oracle.cholgs(synth.random_block(14, om.ndofs, N))
+    X = torch.from_numpy(Xo.copy()).cuda()
+    ev = torch.empty(N, dtype=torch.float64, device="cuda")
+    HX = torch.empty_like(X)
+    dg.dftfe_rayleigh_ritz(ham, X, ev, HX)
+    Xr, Wr, theta, _ = oracle.rayleigh_ritz(oh.apply, Xo)
+    assert np.abs(ev.cpu().numpy() - theta).max() < 1e-11
+    x, w = X.cpu().numpy(), HX.cpu().numpy()
+    # distinct eigenvalues: columns agree after the sign convention
+    gaps = np.minimum(np.r_[np.inf, np.diff(theta)], np.r_[np.diff(theta), np.inf])
+    ok = gaps > 1e-4
+    assert _rel(x[:, ok], Xr[:, ok]) < 1e-8
+    assert _rel(w[:, ok], Wr[:, ok]) < 1e-8
+    _cluster_projectors_match(theta, x, Xr, 1e-8)
+    assert np.abs(x.T @ x - np.eye(N)).max() < 1e-12
+
+
+def test_a13_residuals(dg, pair):
+    om, oh, mesh, ham = pair
+    N = 10
+    Xo, _, _ = oracle.cholgs(synth.random_block(15, om.ndofs, N))
+    Xr, Wr, theta, _ = oracle.rayleigh_ritz(oh.apply, Xo)
+    X = torch.from_numpy(Xr).cuda()
+    W = torch.from_numpy(Wr).cuda()
+    ev = torch.from_numpy(theta).cuda()
+    r = torch.empty(N, dtype=torch.float64, device="cuda")
+    rl, rg = oracle.residuals(Xr, Wr, theta, om.mass)
+    dg.dftfe_residuals(ham, X, W, ev, r, 0)
+    assert _rel(r.cpu().numpy(), rl) < 1e-12
+    dg.dftfe_residuals(ham, X, W, ev, r, 1)
+    assert _rel(r.cpu().numpy(), rg) < 1e-12
+
+
+def test_random_uniform_matches_synth(dg):
+    out = torch.empty(100003, dtype=torch.float64, device="cuda")
+    dg.dftfe_random_uniform(out, 987654321, 17)
+    ref = synth.counter_uniform(987654321, 100003, 17)
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("scaled", [True, False])
+def test_pass_sequence_small(dg, pair, scaled):
+    om, oh, mesh, ham = pair
+    N, B, deg = 14, 5, 8
+    X0 = synth.random_block(16, om.ndofs, N)
+    tmin, tmax, b = oracle.lanczos_bounds(oh.apply, synth.counter_uniform(17, om.ndofs), 20)
+    bd = oracle.first_pass_bounds(tmin, b, N, om.ndofs)
+    if not scaled:
+        bd.a0 = math.nan
+    gb = dg.make_bounds(bd.a, bd.b, bd.a0)
+    X = torch.from_numpy(X0).cuda()
+    ev = torch.empty(N, dtype=torch.float64, device="cuda")
+    rs = torch.empty(N, dtype=torch.float64, device="cuda")
+    Xo = X0
+    for _ in range(3):
+        Xo, Wo, theta, r, bd = oracle.chfsi_pass(oh, Xo, B, deg, bd)
+        dg.dftfe_chfsi_pass(ham, X, B, deg, gb, ev, rs)
+        assert np.abs(ev.cpu().numpy() - theta).max() < TOL_EPS
+        assert np.allclose(rs.cpu().numpy(), r, rtol=1e-6, atol=1e-10)
+        assert abs(gb.a - bd.a) < TOL_EPS and (math.isnan(gb.a0) == math.isnan(bd.a0))
+
+
+def test_bad_bounds_rejected(dg, pair):
+    om, oh, mesh, ham = pair
+    X = torch.zeros((om.ndofs, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(dg.DftfeError):
+        dg.dftfe_chebyshev_filter(ham, X, 3, dg.make_bounds(5.0, 1.0))
+    with pytest.raises(dg.DftfeError):
+        dg.dftfe_chebyshev_filter(ham, X, 3, dg.make_bounds(1.0, 5.0, 2.0))
