@@ -38,6 +38,10 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 def workload(name, seed):
     if name == "small":
         return synth.small_wells(seed)
+    if name == "profile":
+        # per-cell shape of the scale workload (p = 6, 1.25 bohr cells, block 128) on a
+        # 10 bohr box: 512 cells, 110,592 DoFs, cell matrices 0.48 GB (> L2)
+        return synth.lattice_atoms(seed, ncell=8, L=10.0, nside=1, nstates=128, block=128, passes=1)
     return synth.lattice_atoms(seed)
 
 
@@ -45,7 +49,9 @@ def describe(wl):
     return {"workload": wl.name, "L_bohr": wl.L, "cells": [wl.ncell] * 3, "degree": wl.degree,
             "ndofs": wl.ndofs, "nstates": wl.nstates, "block": wl.block,
             "cheb_degree": wl.cheb_degree, "atoms": int(wl.centres.shape[0]), "projectors": wl.nproj,
-            "seed": wl.seed, "l2": "inputs larger than L2 (cell matrices stream 13 GB per H~X)"}
+            "seed": wl.seed,
+            "l2": f"inputs larger than L2 (cell matrices {wl.ncell ** 3 * (wl.degree + 1) ** 6 * 8 / 1e9:.2f} GB"
+                  " streamed per H~X)"}
 
 
 # ----------------------------------------------------------------- clocks
@@ -327,7 +333,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "small"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "small", "profile"])
     ap.add_argument("--precision", default="fp64", choices=["fp64"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

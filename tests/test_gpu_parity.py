@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_APPLY = 1e-12     # relative to max |Y|: FP64, different summation order
-TOL_EPS = 1e-9        # Ha, FP64 path (spec tolerance)
+TOL_EPS = 1e-9        # Ha, FP64 path: |d eps| <= 1e-9 Ha
 
 
 @pytest.fixture(scope="module")
