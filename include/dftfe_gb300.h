@@ -205,6 +205,24 @@ dftfe_status dftfe_chfsi_pass(dftfe_ham ham, double* X, int64_t ld, int ncol,
                               int block, int degree, dftfe_bounds* inout,
                               double* evals, double* resid, dftfe_precision prec);
 
+/* Allocation-free Cholesky-Gram-Schmidt (the paper has no counterpart; this is an
+ * interface for callers that cannot allocate device memory at the call site, e.g.
+ * inside a fixed memory pool or a framework step that forbids cudaMalloc).  Same
+ * result as dftfe_cholgs (S = X^T X, S = L L^T, X <- X L^-T) on an M x ncol FP64
+ * block X (DEVICE, ld), without a ham and without allocating: all scratch lives in
+ * one static device array of about 20 MiB that every GPU loading this library holds
+ * until exit.  ncol above DFTFE_NOALLOC_MAX_COLS returns DFTFE_ERR_ARG.
+ * Work runs on `stream` (a cudaStream_t, NULL = legacy default) and the call
+ * synchronises it (it reads the factorisation status).  The first call on each
+ * device resolves the scratch address and fills a small table (a synchronous
+ * copy), so make that first call before any stream capture.  Every call shares the
+ * one scratch array and reuses whatever the last call left there (each call
+ * overwrites all scratch it reads); calls that overlap on the GPU (other streams,
+ * other threads) race on it and must be serialised by the caller.
+ * DFTFE_ERR_NOT_SPD leaves X untouched. */
+#define DFTFE_NOALLOC_MAX_COLS 512
+dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, int ncol, void* stream);
+
 /* ------------------------------------------------------------ instrumentation */
 
 /* Per-kernel timing with CUDA events recorded on the ham's stream around every

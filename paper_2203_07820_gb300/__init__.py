@@ -69,6 +69,7 @@ _SIGS = {
     "dftfe_rayleigh_ritz": [_vp, _vp, _i64, _int, _vp, _vp, _i64, _int],
     "dftfe_residuals": [_vp, _vp, _vp, _i64, _int, _vp, _vp, _int],
     "dftfe_chfsi_pass": [_vp, _vp, _i64, _int, _int, _int, C.POINTER(Bounds), _vp, _vp, _int],
+    "dftfe_cholgs_noalloc": [_vp, _i64, _i64, _int, _vp],
     "dftfe_profile_enable": [_vp, _int],
     "dftfe_profile_query": [_vp, C.c_char_p, C.POINTER(_dbl), C.POINTER(_i64)],
 }
@@ -239,6 +240,12 @@ def dftfe_chfsi_pass(ham, X, block, degree, bounds, evals, resid, prec=DFTFE_FP6
     _check(_lib.dftfe_chfsi_pass(ham, px, ld, X.shape[1], int(block), int(degree), C.byref(bounds),
                                  _vp(evals.data_ptr()), _vp(resid.data_ptr()), prec))
     return bounds
+
+
+def dftfe_cholgs_noalloc(X, stream=None):
+    """Allocation-free CholGS of X (M x ncol, ncol <= 512) on `stream` (no handle needed)."""
+    px, ld = _dev(X, "X")
+    _check(_lib.dftfe_cholgs_noalloc(px, ld, X.shape[0], X.shape[1], _stream(stream)))
 
 
 # -------------------------------------------------------- instrumentation

@@ -738,3 +738,36 @@ void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3) 
 }
 
 }  // namespace dftfe
+
+// ------------------------------------------------ stream-only launchers
+// Launch the kernels above with caller-provided scratch and a plain stream (no handle,
+// no workspace).  Used by the allocation-free CholGS entry point.
+namespace dftfe {
+
+void gram_partial_launch(cudaStream_t s, const double* A, int64_t lda, const double* B, int64_t ldb,
+                         int64_t M, int N, int nsplit, const int32_t* tiles, int ntiles, double* part) {
+  const int64_t rows = (M + nsplit - 1) / nsplit;
+  DFTFE_LAUNCH(k_gram_partial, dim3(ntiles, nsplit), 256, 0, s, A, lda, B, ldb, M, N, rows, tiles, part);
+}
+
+void gram_reduce_launch(cudaStream_t s, const double* part, int nsplit, int N, double* C) {
+  DFTFE_LAUNCH(k_gram_reduce, nblk((int64_t)N * N), 256, 0, s, part, nsplit, N, C);
+}
+
+template <int R, int CPT>
+static void rotate_launch_t(cudaStream_t s, double* X, int64_t ld, int64_t M, int N, const double* Z,
+                            bool upper) {
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_rotate<R, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+  const size_t sh = (size_t)R * N * sizeof(double);
+  DFTFE_LAUNCH((k_rotate<R, CPT>), (unsigned)((M + R - 1) / R), 256, sh, s, X, ld, M, N, Z, upper ? 1 : 0);
+}
+
+void rotate_launch(cudaStream_t s, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {
+  if (M == 0 || N == 0) return;
+  if (N <= 256) rotate_launch_t<32, 1>(s, X, ld, M, N, Z, upper);
+  else if (N <= 512) rotate_launch_t<32, 2>(s, X, ld, M, N, Z, upper);
+  else throw Error(DFTFE_ERR_ARG, "rotate_launch: at most 512 columns");
+}
+
+}  // namespace dftfe
