@@ -220,7 +220,8 @@ def run_ours(args, rank, world, local, tdist):
     bounds = dg.dftfe_spectrum_bounds(ham, 20, wl.seed + 1000, N)
     ev = torch.empty(N, dtype=torch.float64, device=dev)
     rs = torch.empty(N, dtype=torch.float64, device=dev)
-    prec = dg.DFTFE_FP64
+    prec = {"fp64": dg.DFTFE_FP64, "tf32x3": dg.DFTFE_MIXED_TF32X3,
+            "bf16x3": dg.DFTFE_MIXED_BF16X3}[args.precision]
 
     for _ in range(args.warmup):
         dg.dftfe_chfsi_pass(ham, X, wl.block, wl.cheb_degree, bounds, ev, rs, prec)
@@ -334,7 +335,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=["scale", "small", "profile"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")

@@ -53,9 +53,11 @@ typedef enum {
 
 typedef enum {
   DFTFE_FP64 = 0,          /* everything in FP64 */
-  DFTFE_MIXED_BF16X3 = 1   /* filter cell GEMMs as 3-term BF16 splits with FP32
-                              accumulation on the tensor cores (tcgen05); CholGS,
-                              Rayleigh-Ritz and residuals in FP64 */
+  DFTFE_MIXED_BF16X3 = 1,  /* filter: cell products as 3-term BF16 splits (hi*hi + hi*lo +
+                              lo*hi) on the tensor cores (tcgen05), FP32 accumulation, FP32
+                              vectors; CholGS, Rayleigh-Ritz and residuals in FP64 */
+  DFTFE_MIXED_TF32X3 = 2   /* as above with 3-term TF32 splits (about 2^-21 relative per
+                              product instead of 2^-16) */
 } dftfe_precision;
 
 typedef struct dftfe_mesh_s* dftfe_mesh; /* opaque, library-owned */
@@ -138,7 +140,9 @@ dftfe_status dftfe_ham_export(dftfe_ham ham, double* mass, int32_t* cell_map,
 
 /* Y = H~ X for an M x ncol block (a4 + a5; Eq. celldgemm and Alg. 4): gather to
  * cells, dense per-cell product, colour-ordered scatter-add, plus C~ h C~^T X.
- * X and Y in DEVICE memory, must not overlap. */
+ * X and Y in DEVICE memory, must not overlap.  prec selects the FP64 cell kernel or
+ * the split-precision tensor-core kernel (FP32 inside, converted at both ends;
+ * at most 512 nodes per cell, i.e. p <= 7). */
 dftfe_status dftfe_ham_apply(dftfe_ham ham, const double* X, int64_t ldx,
                              double* Y, int64_t ldy, int ncol, dftfe_precision prec);
 

@@ -89,7 +89,7 @@ extern "C" dftfe_status dftfe_cholgs(dftfe_ham h, double* X, int64_t ld, int nco
   DFTFE_REQUIRE(h && X, "null argument");
   DFTFE_REQUIRE(ncol >= 1 && ncol <= 2048 && ld >= ncol, "bad ncol / ld");
   DFTFE_REQUIRE(ncol <= h->mesh->M, "more columns than DoFs");
-  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3, "unknown precision");
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3, "unknown precision");
   cholgs_impl(h, X, ld, ncol);
   ABI_END
 }
@@ -100,7 +100,7 @@ extern "C" dftfe_status dftfe_rayleigh_ritz(dftfe_ham h, double* X, int64_t ld, 
   DFTFE_REQUIRE(h && X && evals, "null argument");
   DFTFE_REQUIRE(ncol >= 1 && ncol <= 2048 && ld >= ncol, "bad ncol / ld");
   DFTFE_REQUIRE(!HX || ldhx >= ncol, "bad ldhx");
-  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3, "unknown precision");
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3, "unknown precision");
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   double* W = HX;
   int64_t ldw = ldhx;
@@ -131,14 +131,16 @@ extern "C" dftfe_status dftfe_chfsi_pass(dftfe_ham h, double* X, int64_t ld, int
   DFTFE_REQUIRE(ncol <= h->mesh->M, "more columns than DoFs");
   DFTFE_REQUIRE(inout->b > inout->a, "need b > a");
   DFTFE_REQUIRE(std::isnan(inout->a0) || inout->a0 < inout->a, "need a0 < a for the scaled filter");
-  DFTFE_REQUIRE(prec == DFTFE_FP64, "dftfe_chfsi_pass: precision not built");
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
+                "unknown precision");
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   auto* m = h->mesh;
   {
     ProfScope ps(h, "pass_filter");
     for (int j0 = 0; j0 < ncol; j0 += block) {
       const int nb = std::min(block, ncol - j0);
-      chebyshev_filter(h, X + j0, ld, nb, degree, *inout);
+      if (prec == DFTFE_FP64) chebyshev_filter(h, X + j0, ld, nb, degree, *inout);
+      else chebyshev_filter_mixed(h, X + j0, ld, nb, degree, *inout, prec == DFTFE_MIXED_TF32X3);
     }
   }
   {

@@ -290,8 +290,11 @@ extern "C" dftfe_status dftfe_ham_apply(dftfe_ham h, const double* X, int64_t ld
   ABI_BEGIN
   DFTFE_REQUIRE(h && X && Y, "null argument");
   DFTFE_REQUIRE(ncol >= 0 && ldx >= ncol && ldy >= ncol, "bad ncol / leading dimension");
-  DFTFE_REQUIRE(prec == DFTFE_FP64, "dftfe_ham_apply: only DFTFE_FP64");
-  apply_combo(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
+                "unknown precision");
+  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (prec == DFTFE_FP64) apply_combo(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
+  else apply_mixed(h, X, ldx, Y, ldy, ncol, prec == DFTFE_MIXED_TF32X3);
   ABI_END
 }
 
@@ -302,9 +305,10 @@ extern "C" dftfe_status dftfe_chebyshev_filter(dftfe_ham h, double* X, int64_t l
   DFTFE_REQUIRE(ncol >= 0 && ld >= ncol && degree >= 0, "bad ncol / ld / degree");
   DFTFE_REQUIRE(bounds->b > bounds->a, "need b > a");
   DFTFE_REQUIRE(std::isnan(bounds->a0) || bounds->a0 < bounds->a, "need a0 < a for the scaled filter");
-  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3, "unknown precision");
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
+                "unknown precision");
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   if (prec == DFTFE_FP64) chebyshev_filter(h, X, ld, ncol, degree, *bounds);
-  else throw Error(DFTFE_ERR_ARG, "mixed precision filter not built");
+  else chebyshev_filter_mixed(h, X, ld, ncol, degree, *bounds, prec == DFTFE_MIXED_TF32X3);
   ABI_END
 }

@@ -1,0 +1,569 @@
+// Mixed-precision H~X for the Chebyshev filter: the dense cell products
+// Y^c = H~^c X^c (Sec. 4.3, Eq. celldgemm) as 3-term split products on the fifth-generation
+// tensor cores (tcgen05), FP32 accumulation in tensor memory, FP32 vectors.
+//
+//   H~^c = H_hi + H_lo, X^c = X_hi + X_lo  (each term TF32 or BF16, rounded to nearest)
+//   Y^c ~= H_hi X_hi + H_hi X_lo + H_lo X_hi
+//
+// Operand layout: K-major, 128-byte swizzle (rows of 128 bytes, 8-row atoms of 1024 bytes,
+// 16-byte chunks XOR-ed with the row index mod 8).  The split cell matrices are laid out in
+// HBM in exactly this tile order at set-up, so the kernel streams them with plain bulk
+// copies (cp.async.bulk) into shared memory.  The cell's columns of X are gathered by four
+// producer warps, split, and written transposed (K-major) into the B tiles.
+//
+// One CTA per SM walks the cells of one colour (no two share a node).  Warp roles:
+//   warp 0      A producer (bulk copies of the split cell-matrix tiles, 4-stage ring)
+//   warp 1      TMEM owner and MMA issuer (one elected lane)
+//   warps 2-5   B producers (gather + split of X^c, 2-stage ring)
+//   warps 6-9   epilogue (tcgen05.ld of the accumulators, scatter-add alpha*Y into Z)
+// Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its
+// own copies and MMAs (bounded), frees its tensor memory and returns.
+#include "internal.h"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+namespace dftfe {
+
+namespace mx {
+
+constexpr int kThreads = 320;
+constexpr int kStagesA = 4, kStagesB = 2;
+constexpr int kTile = 16384;                       // one 128-row x 128-byte operand tile
+constexpr int kStageBytes = 2 * kTile;             // hi + lo
+constexpr int kMaxMTiles = 4;                      // 4 x 128 accumulator columns = 512 TMEM columns
+constexpr long kSpinLimit = 40000000L;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of (row, byte) in a K-major 128-byte-swizzled tile
+__host__ __device__ __forceinline__ uint32_t sw128(uint32_t row, uint32_t b) {
+  return (row >> 3) * 1024u + (row & 7u) * 128u + ((((b >> 4) ^ (row & 7u)) & 7u) << 4) + (b & 15u);
+}
+
+// shared-memory matrix descriptor: start, LBO 16 B (unused for swizzled K-major),
+// SBO 1024 B (between 8-row atoms), version 1, layout SWIZZLE_128B
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// instruction descriptor: D = F32, A/B format (BF16 = 1 under kind::f16, TF32 = 2 under
+// kind::tf32), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int M, int N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+struct Shared {
+  uint64_t a_full[kStagesA], a_empty[kStagesA];
+  uint64_t b_full[kStagesB], b_empty[kStagesB];
+  uint64_t acc_full, acc_empty, drain;
+  uint32_t tmem;
+  int abort;
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count));
+}
+
+// bounded wait on a phase parity; false on time-out or abort
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* err) {
+  const uint32_t addr = smem_u32(b);
+  for (long it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}"
+                 : "=r"(done) : "r"(addr), "r"(parity) : "memory");
+    if (done) return true;
+    if (*abort) return false;
+  }
+  *abort = 1;
+  atomicExch(err, (int)DFTFE_ERR_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(smem_u32(b)) : "memory");
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  constexpr uint32_t id = idesc(TF32 ? 2u : 1u, 128, 128);
+  if (TF32)
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ uint32_t tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// split x into two terms of the operand type, packed as the 16-byte chunk layout needs
+template <bool TF32> struct Split;
+template <> struct Split<true> {
+  static constexpr int G = 4;  // elements per 16-byte chunk
+  __device__ static void run(const float* v, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      h[i] = tf32_rn(v[i]);
+      l[i] = tf32_rn(v[i] - __uint_as_float(h[i]));
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+};
+template <> struct Split<false> {
+  static constexpr int G = 8;
+  __device__ static void run(const float* v, uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __nv_bfloat16 a = __float2bfloat16_rn(v[2 * i]), b = __float2bfloat16_rn(v[2 * i + 1]);
+      __nv_bfloat16 c = __float2bfloat16_rn(v[2 * i] - __bfloat162float(a));
+      __nv_bfloat16 d = __float2bfloat16_rn(v[2 * i + 1] - __bfloat162float(b));
+      h[i] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+      l[i] = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+};
+
+}  // namespace mx
+
+// Set-up: split the FP64 cell matrices into the tile order the kernel streams:
+// A[cell][kc][mt][hi|lo][16 KB tile]; tile row r <-> matrix row mt*128 + r, tile byte b <->
+// column kc*KC + b/esize; zero outside nc x nc.
+template <bool TF32>
+__global__ void k_split_cells(const double* __restrict__ Hc, uint8_t* __restrict__ A, int64_t Nc, int nc,
+                              int nkc, int nmt) {
+  constexpr int ES = TF32 ? 4 : 2, KC = 128 / ES;
+  const int64_t per_cell = (int64_t)nkc * nmt * 128 * KC;   // elements (each yields hi and lo)
+  const int64_t total = Nc * per_cell;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cell = t / per_cell;
+    int64_t rem = t - cell * per_cell;
+    const int e = (int)(rem % KC);
+    rem /= KC;
+    const int r = (int)(rem % 128);
+    rem /= 128;
+    const int mt = (int)(rem % nmt);
+    const int kc = (int)(rem / nmt);
+    const int m = mt * 128 + r, k = kc * KC + e;
+    const double h = (m < nc && k < nc) ? Hc[(cell * nc + m) * (int64_t)nc + k] : 0.0;
+    uint8_t* tile = A + (((cell * nkc + kc) * nmt + mt) * 2) * (int64_t)mx::kTile;
+    const uint32_t off = mx::sw128((uint32_t)r, (uint32_t)(e * ES));
+    if (TF32) {
+      const uint32_t hi = mx::tf32_rn(__double2float_rn(h));
+      const uint32_t lo = mx::tf32_rn(__double2float_rn(h - (double)__uint_as_float(hi)));
+      *reinterpret_cast<uint32_t*>(tile + off) = hi;
+      *reinterpret_cast<uint32_t*>(tile + mx::kTile + off) = lo;
+    } else {
+      const __nv_bfloat16 hi = __double2bfloat16(h);
+      const __nv_bfloat16 lo = __double2bfloat16(h - (double)__bfloat162float(hi));
+      *reinterpret_cast<__nv_bfloat16*>(tile + off) = hi;
+      *reinterpret_cast<__nv_bfloat16*>(tile + mx::kTile + off) = lo;
+    }
+  }
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
+    const uint8_t* __restrict__ A, const int32_t* __restrict__ map, const int32_t* __restrict__ cells,
+    int ncells, int nc, int nkc, int nmt, const float* __restrict__ X, int64_t ldx,
+    float* __restrict__ Z, int64_t ldz, int col0, int ncol, float alpha, int* err) {
+  using namespace mx;
+  constexpr int ES = TF32 ? 4 : 2, KC = 128 / ES, G = Split<TF32>::G;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;                                    // kStagesA x (hi 16K | lo 16K)
+  uint8_t* sB = base + kStagesA * kStageBytes;           // kStagesB x (hi 16K | lo 16K)
+  Shared* sh = (Shared*)(sB + kStagesB * kStageBytes);
+  volatile int* abort = &sh->abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStagesA; ++s) { mbar_init(&sh->a_full[s], 1); mbar_init(&sh->a_empty[s], 1); }
+    for (int s = 0; s < kStagesB; ++s) { mbar_init(&sh->b_full[s], 128); mbar_init(&sh->b_empty[s], 1); }
+    mbar_init(&sh->acc_full, 1);
+    mbar_init(&sh->acc_empty, 128);
+    mbar_init(&sh->drain, 1);
+    sh->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&sh->tmem)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh->tmem;
+  const int my_cells = ncells > (int)blockIdx.x ? (ncells - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ A producer
+    if (lane == 0) {
+      uint32_t ta = 0;
+      for (int i = 0; i < my_cells && !*abort; ++i) {
+        const int64_t cell = cells[blockIdx.x + (int64_t)i * gridDim.x];
+        for (int kc = 0; kc < nkc && !*abort; ++kc)
+          for (int mt = 0; mt < nmt; ++mt, ++ta) {
+            const int s = ta % kStagesA;
+            if (!mbar_wait(&sh->a_empty[s], ((ta / kStagesA) & 1) ^ 1, abort, err)) break;
+            const uint32_t full = smem_u32(&sh->a_full[s]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(kStageBytes) : "memory");
+            const uint8_t* src = A + (((cell * nkc + kc) * nmt + mt) * 2) * (int64_t)kTile;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_u32(sA + s * kStageBytes)), "l"(src), "r"(kStageBytes), "r"(full) : "memory");
+          }
+      }
+      // drain: every issued copy has landed before the CTA may exit
+      for (uint32_t t = (ta > (uint32_t)kStagesA ? ta - kStagesA : 0); t < ta; ++t) {
+        volatile int no_abort = 0;
+        mbar_wait(&sh->a_full[t % kStagesA], (t / kStagesA) & 1, &no_abort, err);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t ta = 0, tb = 0;
+      for (int i = 0; i < my_cells && !*abort; ++i) {
+        if (!mbar_wait(&sh->acc_empty, (i & 1) ^ 1, abort, err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kc = 0; kc < nkc && !*abort; ++kc, ++tb) {
+          const int sb = tb % kStagesB;
+          if (!mbar_wait(&sh->b_full[sb], (tb / kStagesB) & 1, abort, err)) break;
+          const uint32_t bhi = smem_u32(sB + sb * kStageBytes), blo = bhi + kTile;
+          for (int mt = 0; mt < nmt; ++mt, ++ta) {
+            const int sa = ta % kStagesA;
+            if (!mbar_wait(&sh->a_full[sa], (ta / kStagesA) & 1, abort, err)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ahi = smem_u32(sA + sa * kStageBytes), alo = ahi + kTile;
+            const uint32_t d = tmem + (uint32_t)(mt * 128);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint32_t o = ks * 32;
+              mma<TF32>(d, sdesc(ahi + o), sdesc(bhi + o), (kc > 0 || ks > 0) ? 1u : 0u);
+              mma<TF32>(d, sdesc(ahi + o), sdesc(blo + o), 1u);
+              mma<TF32>(d, sdesc(alo + o), sdesc(bhi + o), 1u);
+            }
+            tc_commit(&sh->a_empty[sa]);
+          }
+          tc_commit(&sh->b_empty[sb]);
+        }
+        tc_commit(&sh->acc_full);
+      }
+      // drain: all issued MMAs complete before tensor memory is released
+      tc_commit(&sh->drain);
+      volatile int no_abort = 0;
+      mbar_wait(&sh->drain, 0, &no_abort, err);
+    }
+  } else if (warp < 6) {
+    // ------------------------------------------------------------ B producers
+    const int n = threadIdx.x - 64;              // column within the tile, 0..127
+    const int col = col0 + n;
+    const bool colok = col < ncol;
+    uint32_t tb = 0;
+    for (int i = 0; i < my_cells && !*abort; ++i) {
+      const int64_t cell = cells[blockIdx.x + (int64_t)i * gridDim.x];
+      const int32_t* cm = map + cell * nc;
+      for (int kc = 0; kc < nkc; ++kc, ++tb) {
+        const int sb = tb % kStagesB;
+        if (!mbar_wait(&sh->b_empty[sb], ((tb / kStagesB) & 1) ^ 1, abort, err)) break;
+        uint8_t* bhi = sB + sb * kStageBytes;
+        uint8_t* blo = bhi + kTile;
+#pragma unroll 2
+        for (int g = 0; g < KC / G; ++g) {
+          float v[G];
+#pragma unroll
+          for (int j = 0; j < G; ++j) {
+            const int k = kc * KC + g * G + j;
+            v[j] = (colok && k < nc) ? X[(int64_t)cm[k] * ldx + col] : 0.0f;
+          }
+          uint4 hi, lo;
+          Split<TF32>::run(v, hi, lo);
+          const uint32_t off = sw128((uint32_t)n, (uint32_t)(g * 16));
+          *reinterpret_cast<uint4*>(bhi + off) = hi;
+          *reinterpret_cast<uint4*>(blo + off) = lo;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&sh->b_full[sb]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;                       // TMEM lane quadrant of this warp
+    for (int i = 0; i < my_cells; ++i) {
+      if (!mbar_wait(&sh->acc_full, i & 1, abort, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t cell = cells[blockIdx.x + (int64_t)i * gridDim.x];
+      for (int mt = 0; mt < nmt; ++mt) {
+        const int row = mt * 128 + q * 32 + lane;
+        const int64_t g = row < nc ? (int64_t)map[cell * nc + row] : -1;
+        for (int cb = 0; cb < 4; ++cb) {
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128 + cb * 32);
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                       : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (g >= 0) {
+            float* z = Z + g * ldz + col0 + cb * 32;
+            const int cbase = col0 + cb * 32;
+            if (cbase + 32 <= ncol) {
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                float4 o = *reinterpret_cast<float4*>(z + j);
+                o.x = fmaf(alpha, __uint_as_float(r[j]), o.x);
+                o.y = fmaf(alpha, __uint_as_float(r[j + 1]), o.y);
+                o.z = fmaf(alpha, __uint_as_float(r[j + 2]), o.z);
+                o.w = fmaf(alpha, __uint_as_float(r[j + 3]), o.w);
+                *reinterpret_cast<float4*>(z + j) = o;
+              }
+            } else {
+              for (int j = 0; j < 32; ++j)
+                if (cbase + j < ncol) z[j] = fmaf(alpha, __uint_as_float(r[j]), z[j]);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&sh->acc_empty);
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
+// ------------------------------------------------------------ FP32 helpers
+__global__ void k_axpby_init32(float* __restrict__ Z, int64_t ldz, const float* __restrict__ X, int64_t ldx,
+                               const float* __restrict__ Xp, int64_t ldp, int64_t M, int ncol, float s1, float s2) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= M * ncol) return;
+  const int64_t i = t / ncol;
+  const int j = (int)(t - i * ncol);
+  float v = 0.0f;
+  if (s1 != 0.0f) v = s1 * X[i * ldx + j];
+  if (Xp) v = fmaf(s2, Xp[i * ldp + j], v);
+  Z[i * ldz + j] = v;
+}
+
+__global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy,
+                         int64_t M, int ncol) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= M * ncol) return;
+  const int64_t i = t / ncol;
+  const int j = (int)(t - i * ncol);
+  Y[i * ldy + j] = __double2float_rn(X[i * ldx + j]);
+}
+
+__global__ void k_to_f64(const float* __restrict__ Y, int64_t ldy, double* __restrict__ X, int64_t ldx,
+                         int64_t M, int ncol) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= M * ncol) return;
+  const int64_t i = t / ncol;
+  const int j = (int)(t - i * ncol);
+  X[i * ldx + j] = (double)Y[i * ldy + j];
+}
+
+__global__ void __launch_bounds__(256) k_nl_coef32(const float* __restrict__ X, int64_t ldx, int ncol,
+                                                   const int64_t* __restrict__ prow, const int32_t* __restrict__ pnode,
+                                                   const double* __restrict__ pval, const double* __restrict__ hcoup,
+                                                   float* __restrict__ P) {
+  __shared__ float red[8][32];
+  const int a = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.y * 32 + lane;
+  float s = 0.0f;
+  if (col < ncol)
+    for (int64_t e = prow[a] + warp; e < prow[a + 1]; e += 8)
+      s = fmaf((float)pval[e], X[(int64_t)pnode[e] * ldx + col], s);
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && col < ncol) {
+    float t = 0.0f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    P[(int64_t)a * ncol + col] = (float)hcoup[a] * t;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_nl_add32(float* __restrict__ Z, int64_t ldz, int ncol,
+                                                  const int32_t* __restrict__ snode, const int64_t* __restrict__ srow,
+                                                  const int32_t* __restrict__ sproj, const double* __restrict__ sval,
+                                                  const float* __restrict__ P, int64_t nsup, float alpha) {
+  const int lane = threadIdx.x & 31;
+  const int64_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int col = blockIdx.y * 32 + lane;
+  if (s >= nsup || col >= ncol) return;
+  float acc = 0.0f;
+  for (int64_t t = srow[s]; t < srow[s + 1]; ++t) acc = fmaf((float)sval[t], P[(int64_t)sproj[t] * ncol + col], acc);
+  Z[(int64_t)snode[s] * ldz + col] += alpha * acc;
+}
+
+static unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+static size_t mixed_smem() {
+  return 1024 + (size_t)mx::kStagesA * mx::kStageBytes + (size_t)mx::kStagesB * mx::kStageBytes + sizeof(mx::Shared);
+}
+
+// build (once per potential and precision) the split cell-matrix tiles
+static uint8_t* mixed_tiles(dftfe_ham h, bool tf32, int* nkc_out, int* nmt_out) {
+  auto* m = h->mesh;
+  const int es = tf32 ? 4 : 2, kc = 128 / es;
+  const int nkc = (m->nc + kc - 1) / kc, nmt = (m->nc + 127) / 128;
+  *nkc_out = nkc;
+  *nmt_out = nmt;
+  if (nmt > mx::kMaxMTiles) throw Error(DFTFE_ERR_ARG, "mixed precision supports at most 512 nodes per cell (p <= 7)");
+  const int fmt = tf32 ? 1 : 0;
+  const char* name = tf32 ? "mixed_tiles_tf32" : "mixed_tiles_bf16";
+  const size_t bytes = (size_t)m->Nc * nkc * nmt * 2 * mx::kTile;
+  uint8_t* A = (uint8_t*)ws_get(h, name, bytes);
+  if (h->mixed_version[fmt] != h->potential_version) {
+    const int grid = h->sm_count * 16;
+    if (tf32)
+      DFTFE_LAUNCH(k_split_cells<true>, grid, 256, 0, h->stream, h->d_Hc, A, m->Nc, m->nc, nkc, nmt);
+    else
+      DFTFE_LAUNCH(k_split_cells<false>, grid, 256, 0, h->stream, h->d_Hc, A, m->Nc, m->nc, nkc, nmt);
+    h->mixed_version[fmt] = h->potential_version;
+  }
+  return A;
+}
+
+// Z = alpha H~ X + s1 X + s2 Xp on FP32 blocks (ld multiple of 4), mixed cell products
+static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc, int nmt, const float* X, int64_t ldx,
+                              const float* Xp, int64_t ldp, float* Z, int64_t ldz, int ncol, float alpha, float s1,
+                              float s2, int* err) {
+  auto* m = h->mesh;
+  DFTFE_LAUNCH(k_axpby_init32, nblk(m->M * ncol), 256, 0, h->stream, Z, ldz, X, ldx, Xp, ldp, m->M, ncol, s1, s2);
+  if (h->nproj > 0) {
+    float* P = (float*)ws_get(h, "nl_coef32", sizeof(float) * h->nproj * (size_t)ncol);
+    dim3 g1((unsigned)h->nproj, (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_nl_coef32, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval, h->d_h, P);
+    dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_nl_add32, g2, 256, 0, h->stream, Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj, h->d_sval, P,
+                 h->nsup, alpha);
+  }
+  const size_t sh = mixed_smem();
+  for (int c = 0; c < h->ncolours; ++c) {
+    const int64_t n = h->colour_off[c + 1] - h->colour_off[c];
+    if (n == 0) continue;
+    const int32_t* cells = h->d_colour_cells + h->colour_off[c];
+    const unsigned grid = (unsigned)std::min<int64_t>(n, h->sm_count);
+    for (int col0 = 0; col0 < ncol; col0 += 128) {
+      ProfScope ps(h, tf32 ? "cell_gemm_tf32x3" : "cell_gemm_bf16x3");
+      if (tf32)
+        DFTFE_LAUNCH(k_cell_mixed<true>, grid, mx::kThreads, sh, h->stream, A, h->d_map, cells, (int)n, m->nc, nkc,
+                     nmt, X, ldx, Z, ldz, col0, ncol, alpha, err);
+      else
+        DFTFE_LAUNCH(k_cell_mixed<false>, grid, mx::kThreads, sh, h->stream, A, h->d_map, cells, (int)n, m->nc, nkc,
+                     nmt, X, ldx, Z, ldz, col0, ncol, alpha, err);
+    }
+  }
+}
+
+static bool g_mixed_attr = false;
+
+// Eq. chebyfilter with FP32 vectors and split-precision cell products; the caller's FP64
+// block is converted in and out.
+void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int degree, const dftfe_bounds& b,
+                            bool tf32) {
+  if (degree <= 0 || ncol <= 0) return;
+  auto* m = h->mesh;
+  if (!g_mixed_attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
+    g_mixed_attr = true;
+  }
+  int nkc, nmt;
+  const uint8_t* A = mixed_tiles(h, tf32, &nkc, &nmt);
+  const int64_t ld32 = (ncol + 31) / 32 * 32;
+  float* buf[3];
+  buf[0] = (float*)ws_get(h, "mx_v0", sizeof(float) * m->M * (size_t)ld32);
+  buf[1] = (float*)ws_get(h, "mx_v1", sizeof(float) * m->M * (size_t)ld32);
+  buf[2] = (float*)ws_get(h, "mx_v2", sizeof(float) * m->M * (size_t)ld32);
+  int* err = (int*)ws_get(h, "mx_err", sizeof(int));
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  DFTFE_LAUNCH(k_to_f32, nblk(m->M * ncol), 256, 0, h->stream, X, ld, buf[0], ld32, m->M, ncol);
+  const double e = (b.b - b.a) / 2.0, c = (b.b + b.a) / 2.0;
+  const bool scaled = !std::isnan(b.a0);
+  double sigma = scaled ? e / (b.a0 - c) : 0.0;
+  const double sigma1 = sigma, gamma = scaled ? 2.0 / sigma1 : 0.0;
+  int cur = 0, prev = -1;
+  for (int k = 1; k <= degree; ++k) {
+    int out = 0;
+    while (out == cur || out == prev) ++out;
+    double alpha, s1, s2 = 0.0;
+    if (k == 1) {
+      alpha = scaled ? sigma1 / e : 1.0 / e;
+      s1 = -c * alpha;
+    } else if (scaled) {
+      const double sigma2 = 1.0 / (gamma - sigma);
+      alpha = 2.0 * sigma2 / e;
+      s1 = -c * alpha;
+      s2 = -sigma * sigma2;
+      sigma = sigma2;
+    } else {
+      alpha = 2.0 / e;
+      s1 = -c * alpha;
+      s2 = -1.0;
+    }
+    apply_combo_mixed(h, tf32, A, nkc, nmt, buf[cur], ld32, prev >= 0 ? buf[prev] : nullptr, ld32, buf[out], ld32,
+                      ncol, (float)alpha, (float)s1, (float)s2, err);
+    prev = cur;
+    cur = out;
+  }
+  DFTFE_LAUNCH(k_to_f64, nblk(m->M * ncol), 256, 0, h->stream, buf[cur], ld32, X, ld, m->M, ncol);
+  int herr = 0;
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  if (herr) throw Error(DFTFE_ERR_TIMEOUT, "mixed cell kernel: a bounded wait timed out");
+}
+
+// Y = H~ X with the mixed cell products (FP64 in and out, FP32 inside); for parity tests.
+void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32) {
+  auto* m = h->mesh;
+  if (!g_mixed_attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
+    g_mixed_attr = true;
+  }
+  int nkc, nmt;
+  const uint8_t* A = mixed_tiles(h, tf32, &nkc, &nmt);
+  const int64_t ld32 = (ncol + 31) / 32 * 32;
+  float* x32 = (float*)ws_get(h, "mx_v0", sizeof(float) * m->M * (size_t)ld32);
+  float* y32 = (float*)ws_get(h, "mx_v1", sizeof(float) * m->M * (size_t)ld32);
+  int* err = (int*)ws_get(h, "mx_err", sizeof(int));
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  DFTFE_LAUNCH(k_to_f32, nblk(m->M * ncol), 256, 0, h->stream, X, ldx, x32, ld32, m->M, ncol);
+  apply_combo_mixed(h, tf32, A, nkc, nmt, x32, ld32, nullptr, 0, y32, ld32, ncol, 1.0f, 0.0f, 0.0f, err);
+  DFTFE_LAUNCH(k_to_f64, nblk(m->M * ncol), 256, 0, h->stream, y32, ld32, Y, ldy, m->M, ncol);
+  int herr = 0;
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  if (herr) throw Error(DFTFE_ERR_TIMEOUT, "mixed cell kernel: a bounded wait timed out");
+}
+
+}  // namespace dftfe

@@ -119,6 +119,8 @@ struct dftfe_ham_s {
   double* d_wq = nullptr;          // nq quadrature weights * detJ
   double* d_Hc = nullptr;          // Nc x nc x nc FP64
   bool has_potential = false;
+  int64_t potential_version = 0;   // bumped by every set_potential
+  int64_t mixed_version[2] = {-1, -1};  // potential version of the split tiles (bf16, tf32)
   // a3: nonlocal (CSR by projector and by node)
   int nproj = 0;
   double* d_h = nullptr;
@@ -154,6 +156,11 @@ void chebyshev_filter(dftfe_ham h, double* X, int64_t ld, int ncol, int degree,
                       const dftfe_bounds& b);
 void copy_block(cudaStream_t s, const double* src, int64_t lds, double* dst, int64_t ldd,
                 int64_t rows, int ncol);
+
+// hx_mixed.cu
+void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int degree,
+                            const dftfe_bounds& b, bool tf32);
+void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32);
 
 // dense.cu
 void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb,

@@ -420,6 +420,7 @@ extern "C" dftfe_status dftfe_ham_set_potential(dftfe_ham h, const double* v_qua
                  h->d_map, h->d_minvsqrt, h->d_Hc, Msym, m->Nc, m->nq, m->nc);
   }
   h->has_potential = true;
+  h->potential_version++;
   ABI_END
 }
 
