@@ -246,17 +246,84 @@ def run_ours(args, rank, world, local, tdist):
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, tdist, dev)
-    cell_ms, cell_n = dg.dftfe_profile_query(ham, "cell_gemm_fp64")
+    fam = {}
+    for name in ("pass_filter", "pass_cholgs", "pass_rr", "cell_gemm_fp64", "cell_gemm_tf32x3",
+                 "cell_gemm_bf16x3", "gram", "rotate", "syevd"):
+        t, n = dg.dftfe_profile_query(ham, name)
+        if n:
+            fam[name] = {"ms": t / args.steps, "launches": n // args.steps}
     dg.dftfe_profile_enable(ham, False)
     sec_per_pass = ms / 1e3 / args.steps
 
     nc = (wl.degree + 1) ** 3
     Nc = wl.ncell ** 3
-    apps_cols = N * wl.cheb_degree + N            # filter + Rayleigh-Ritz H~X columns per pass
-    cell_flops = 2.0 * Nc * nc * nc * apps_cols * args.steps
-    filter_flops = 2.0 * Nc * nc * nc * N * wl.cheb_degree
-    achieved = cell_flops / (cell_ms / 1e3) / 1e12 if cell_ms > 0 else None
-    filt_tflops = filter_flops / (sec_per_pass) / 1e12
+    K = args.steps
+    filter_flops = 2.0 * Nc * nc * nc * N * wl.cheb_degree          # algorithmic, per pass
+    t_filter = fam.get("pass_filter", {}).get("ms", float("nan")) / 1e3
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16_sust = peaks.get("bf16_tflops_sustained", 1700.0)
+    tensor_peak = {"bf16x3": bf16_sust, "tf32x3": bf16_sust * 1.1 / 2.25}
+    # roofline of each timed kernel family (algorithmic work / measured time)
+    roofs = {}
+    fp64_cols = (N * wl.cheb_degree + N) if args.precision == "fp64" else N
+    if "cell_gemm_fp64" in fam:
+        a = 2.0 * Nc * nc * nc * fp64_cols / (fam["cell_gemm_fp64"]["ms"] / 1e3) / 1e12
+        roofs["cell_gemm_fp64"] = {"kernel": "k_cell_fp64_wide (gather + FP64 cell GEMM + scatter-add)",
+                                   "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": a / FP64_PEAK_TFLOPS,
+                                   "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2.07 GHz (nominal 1.25)"}
+    for p in ("tf32x3", "bf16x3"):
+        key = "cell_gemm_" + p
+        if key in fam:
+            apps = wl.cheb_degree * N / wl.block
+            s_h = 8 if p == "tf32x3" else 4                         # hi + lo bytes per matrix entry
+            byt = (Nc * nc * nc * s_h + 3.0 * M * wl.block * 4) * apps
+            t = fam[key]["ms"] / 1e3
+            a = byt / t / 1e9
+            roofs[key] = {"kernel": f"k_cell_mixed<{p}> (tcgen05 split products, FP32 TMEM accumulation)",
+                          "bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
+                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                          "tensor_achieved_tflops": 3 * filter_flops / t / 1e12,
+                          "tensor_peak_tflops": tensor_peak[p],
+                          "tensor_peak_source": "measured bf16 sustained" + (" x nominal tf32/bf16 (1.1/2.25)"
+                                                                          if p == "tf32x3" else "")}
+    for key, flops, label in (("gram", 2 * M * N * N * 0.5625 * 2, "k_gram_partial (S, H^ lower tiles, FP64)"),
+                              ("rotate", 2 * M * N * N * 2.5, "k_rotate (X L^-T, X Q, W Q, FP64)")):
+        if key in fam:
+            a = flops / (fam[key]["ms"] / 1e3) / 1e12
+            roofs[key] = {"kernel": label, "bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS,
+                          "unit": "TFLOP/s", "frac": a / FP64_PEAK_TFLOPS}
+    timed = {k: v["ms"] for k, v in fam.items() if not k.startswith("pass_") and k in roofs}
+    dom = max(timed, key=timed.get) if timed else None
+    roofline = dict(roofs[dom]) if dom else None
+    if roofline is not None:
+        roofline["traffic"] = None
+        roofline["share_of_pass"] = fam[dom]["ms"] / (sec_per_pass * 1e3)
+
+    # one extra FP64 pass and one pass in the timed precision from the same state: |d eps|
+    compare = None
+    if args.precision != "fp64" and not args.no_compare:
+        Xa = X.clone()
+        ba = dg.make_bounds(bounds.a, bounds.b, bounds.a0)
+        bb = dg.make_bounds(bounds.a, bounds.b, bounds.a0)
+        eva = torch.empty_like(ev); rsa = torch.empty_like(rs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dg.dftfe_chfsi_pass(ham, Xa, wl.block, wl.cheb_degree, ba, eva, rsa, dg.DFTFE_FP64)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        dg.dftfe_chfsi_pass(ham, X, wl.block, wl.cheb_degree, bb, ev, rs, prec)
+        torch.cuda.synchronize()
+        Wa = torch.empty_like(X)
+        rg = torch.empty_like(rs)
+        dg.dftfe_ham_apply(ham, X, Wa)
+        dg.dftfe_residuals(ham, X, Wa, ev, rg, 1)
+        del Wa, Xa
+        compare = {"fp64_pass_s": t64, "max_abs_deps_Ha": float((ev - eva).abs().max().item()),
+                   "max_abs_deps_lower_half_Ha": float((ev[:N // 2] - eva[:N // 2]).abs().max().item()),
+                   "max_ghep_resid_lower_half": float(rg[:N // 2].max().item()),
+                   "note": "one FP64 pass and one pass in the timed precision from the same state"}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -281,22 +348,24 @@ def run_ours(args, rank, world, local, tdist):
                "d2h_bytes_per_step": 2 * N * 8, "steps": ne}
 
     out = {
-        "metric": "ChFSI pass seconds (FP64) with filter TFLOP/s vs peak",
+        "metric": "ChFSI pass seconds and filter TFLOP/s vs peak (mixed vs FP64)",
         "value": sec_per_pass, "unit": "s/pass", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "precision": "fp64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32x3": "tf32x3+f32 filter, f64 elsewhere",
+                  "bf16x3": "bf16x3+f32 filter, f64 elsewhere"}[args.precision],
+        "data": "synthetic", "precision": args.precision,
         "config": describe(wl) | {"parallelism": f"replicas{world}"},
-        "filter_tflops": filt_tflops,
-        "dofs_x_vectors_per_s": M * N * wl.cheb_degree / (sec_per_pass),
-        "roofline": {"kernel": "k_cell_fp64_wide (gather + dense cell GEMM + scatter-add)",
-                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-                     "traffic": None, "launches": cell_n,
-                     "peak_source": "derived: 152 SMs x 4 FP64 FLOP/clk x 2.07 GHz (nominal 1.25 TF/s)"},
+        "filter_tflops": filter_flops / t_filter / 1e12 if t_filter == t_filter else None,
+        "filter_s_per_pass": t_filter,
+        "dofs_x_vectors_per_s": M * N * wl.cheb_degree / t_filter if t_filter == t_filter else None,
+        "phases_ms_per_pass": {k: v["ms"] for k, v in fam.items()},
+        "roofline": roofline,
+        "rooflines": roofs,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
+        "mixed_vs_fp64": compare,
         "bounds": {"a": bounds.a, "b": bounds.b, "a0": bounds.a0},
         "max_resid": float(rs.max().item()),
     }
@@ -320,7 +389,7 @@ def run_reference(args, rank, world):
             vals.append(r["value"])
             last = r
     v = statistics.mean(vals)
-    return {"impl": "reference", "metric": "ChFSI pass seconds (FP64) with filter TFLOP/s vs peak",
+    return {"impl": "reference", "metric": "ChFSI pass seconds and filter TFLOP/s vs peak (mixed vs FP64)",
             "value": v, "unit": "s/pass", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": describe(wl) | {"parallelism": "cpu"},
@@ -340,6 +409,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

@@ -58,6 +58,11 @@ typedef enum {
                               vectors; CholGS, Rayleigh-Ritz and residuals in FP64 */
   DFTFE_MIXED_TF32X3 = 2   /* as above with 3-term TF32 splits (about 2^-21 relative per
                               product instead of 2^-16) */
+  /* In dftfe_cholgs, dftfe_rayleigh_ritz and the pass, either mixed value selects the
+     mixed overlap / projection / rotation of Sec. 3.2: diagonal entries of S and H^ and
+     the diagonal part of each rotation in FP64, off-diagonal parts in FP32; W = H~X,
+     the Cholesky factorisation, the eigensolve and the residuals stay FP64 (split
+     products for W move the Ritz values by 1e-6 to 2e-6 Ha). */
 } dftfe_precision;
 
 typedef struct dftfe_mesh_s* dftfe_mesh; /* opaque, library-owned */

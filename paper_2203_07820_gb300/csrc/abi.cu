@@ -14,37 +14,55 @@ static int read_status(dftfe_ham h, int* d_status) {
   return st;
 }
 
-static void cholgs_impl(dftfe_ham h, double* X, int64_t ld, int ncol) {
+static void cholgs_impl(dftfe_ham h, double* X, int64_t ld, int ncol, bool mixed) {
   auto* m = h->mesh;
   const int N = ncol;
   double* S = (double*)ws_get(h, "S", sizeof(double) * (size_t)N * N);
   double* Z = (double*)ws_get(h, "Zinv", sizeof(double) * (size_t)N * N);
   int* st = (int*)ws_get(h, "status", sizeof(int) * 4);
-  const int nsplit = gram_nsplit(h, m->M, N);
-  double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N * N);
-  gram_lower(h, X, ld, X, ld, m->M, N, S, part, nsplit);
+  if (mixed) {
+    gram_lower_mixed(h, X, ld, X, ld, m->M, N, S);
+  } else {
+    const int nsplit = gram_nsplit(h, m->M, N);
+    double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N * N);
+    gram_lower(h, X, ld, X, ld, m->M, N, S, part, nsplit);
+  }
   potrf(h->stream, S, N, st);
   const int s = read_status(h, st);
   if (s == DFTFE_ERR_NOT_SPD) throw Error(DFTFE_ERR_NOT_SPD, "overlap matrix is not positive definite");
   trtri_lower_to_upper_t(h->stream, S, Z, N);
-  rotate_inplace(h, X, ld, m->M, N, Z, true);
+  if (mixed) rotate_inplace_mixed(h, X, ld, m->M, N, Z, true);
+  else rotate_inplace(h, X, ld, m->M, N, Z, true);
 }
 
-static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals, double* W, int64_t ldw) {
+static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals, double* W, int64_t ldw,
+                    dftfe_precision prec) {
   auto* m = h->mesh;
   const int N = ncol;
+  const bool mixed = prec != DFTFE_FP64;
+  // W = H~X stays FP64 in every precision: with split-precision cell products here the
+  // Ritz values move by 1e-6 (TF32x3) to 2e-6 Ha (BF16x3), the size of the mixed tolerance
   apply_combo(h, X, ld, nullptr, 0, W, ldw, N, 1.0, 0.0, 0.0);
   double* Hh = (double*)ws_get(h, "Hhat", sizeof(double) * (size_t)N * N);
   double* Q = (double*)ws_get(h, "Q", sizeof(double) * (size_t)N * N);
   int* st = (int*)ws_get(h, "status", sizeof(int) * 4);
-  const int nsplit = gram_nsplit(h, m->M, N);
-  double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N * N);
-  gram_lower(h, X, ld, W, ldw, m->M, N, Hh, part, nsplit);
+  if (mixed) {
+    gram_lower_mixed(h, X, ld, W, ldw, m->M, N, Hh);
+  } else {
+    const int nsplit = gram_nsplit(h, m->M, N);
+    double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N * N);
+    gram_lower(h, X, ld, W, ldw, m->M, N, Hh, part, nsplit);
+  }
   syevd(h, Hh, N, evals, Q, st);
   const int s = read_status(h, st);
   if (s == DFTFE_ERR_NOCONV) throw Error(DFTFE_ERR_NOCONV, "subspace eigensolver did not converge");
-  rotate_inplace(h, X, ld, m->M, N, Q, false);
-  rotate_inplace(h, W, ldw, m->M, N, Q, false);
+  if (mixed) {
+    rotate_inplace_mixed(h, X, ld, m->M, N, Q, false);
+    rotate_inplace_mixed(h, W, ldw, m->M, N, Q, false);
+  } else {
+    rotate_inplace(h, X, ld, m->M, N, Q, false);
+    rotate_inplace(h, W, ldw, m->M, N, Q, false);
+  }
 }
 
 }  // namespace dftfe
@@ -90,7 +108,7 @@ extern "C" dftfe_status dftfe_cholgs(dftfe_ham h, double* X, int64_t ld, int nco
   DFTFE_REQUIRE(ncol >= 1 && ncol <= 2048 && ld >= ncol, "bad ncol / ld");
   DFTFE_REQUIRE(ncol <= h->mesh->M, "more columns than DoFs");
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3, "unknown precision");
-  cholgs_impl(h, X, ld, ncol);
+  cholgs_impl(h, X, ld, ncol, prec != DFTFE_FP64);
   ABI_END
 }
 
@@ -108,7 +126,7 @@ extern "C" dftfe_status dftfe_rayleigh_ritz(dftfe_ham h, double* X, int64_t ld, 
     W = (double*)ws_get(h, "W", sizeof(double) * (size_t)h->mesh->M * ncol);
     ldw = ncol;
   }
-  rr_impl(h, X, ld, ncol, evals, W, ldw);
+  rr_impl(h, X, ld, ncol, evals, W, ldw, prec);
   ABI_END
 }
 
@@ -145,12 +163,12 @@ extern "C" dftfe_status dftfe_chfsi_pass(dftfe_ham h, double* X, int64_t ld, int
   }
   {
     ProfScope ps(h, "pass_cholgs");
-    cholgs_impl(h, X, ld, ncol);
+    cholgs_impl(h, X, ld, ncol, prec != DFTFE_FP64);
   }
   double* W = (double*)ws_get(h, "W", sizeof(double) * (size_t)m->M * ncol);
   {
     ProfScope ps(h, "pass_rr");
-    rr_impl(h, X, ld, ncol, evals, W, ncol);
+    rr_impl(h, X, ld, ncol, evals, W, ncol, prec);
   }
   residual_norms(h, X, ld, W, ncol, m->M, ncol, evals, resid, 0);
   double ends[2];

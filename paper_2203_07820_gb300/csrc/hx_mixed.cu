@@ -141,6 +141,23 @@ template <> struct Split<false> {
   }
 };
 
+// 4x4 transpose inside each lane quad: lane r of the quad holds row r (4 columns) on
+// entry and column r (4 rows) on exit.
+__device__ __forceinline__ void quad_transpose(const float4 a4, int r, float* t) {
+  const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+  t[0] = t[1] = t[2] = t[3] = 0.0f;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const int idx = r ^ s;
+    const float send = idx == 0 ? a[0] : idx == 1 ? a[1] : idx == 2 ? a[2] : a[3];
+    const float got = __shfl_xor_sync(0xffffffffu, send, s);
+    t[0] = idx == 0 ? got : t[0];
+    t[1] = idx == 1 ? got : t[1];
+    t[2] = idx == 2 ? got : t[2];
+    t[3] = idx == 3 ? got : t[3];
+  }
+}
+
 }  // namespace mx
 
 // Set-up: split the FP64 cell matrices into the tile order the kernel streams:
@@ -275,31 +292,54 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     }
   } else if (warp < 6) {
     // ------------------------------------------------------------ B producers
-    const int n = threadIdx.x - 64;              // column within the tile, 0..127
-    const int col = col0 + n;
-    const bool colok = col < ncol;
+    // warp w covers tile rows (columns of X) 32w..32w+31; lane l loads a float4 of row
+    // 4q + (l & 3) at columns 32w + 4(l >> 2) .. +3, then a 4x4 transpose inside each
+    // lane quad leaves lane l with 4 consecutive k of column n = 32w + l.
+    const int w = warp - 2;
+    const int n = 32 * w + lane;
+    const int rr = lane & 3;
+    const int colq = col0 + 32 * w + 4 * (lane >> 2);
+    constexpr int QN = KC / 4;                   // row quads per K-chunk
     uint32_t tb = 0;
     for (int i = 0; i < my_cells && !*abort; ++i) {
       const int64_t cell = cells[blockIdx.x + (int64_t)i * gridDim.x];
       const int32_t* cm = map + cell * nc;
       for (int kc = 0; kc < nkc; ++kc, ++tb) {
+        float4 v[QN];
+#pragma unroll
+        for (int q = 0; q < QN; ++q) {
+          const int k = kc * KC + 4 * q + rr;
+          v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (k < nc && colq < ncol)
+            v[q] = __ldg(reinterpret_cast<const float4*>(X + (int64_t)cm[k] * ldx + colq));
+        }
         const int sb = tb % kStagesB;
         if (!mbar_wait(&sh->b_empty[sb], ((tb / kStagesB) & 1) ^ 1, abort, err)) break;
         uint8_t* bhi = sB + sb * kStageBytes;
         uint8_t* blo = bhi + kTile;
-#pragma unroll 2
-        for (int g = 0; g < KC / G; ++g) {
-          float v[G];
+        if (TF32) {
 #pragma unroll
-          for (int j = 0; j < G; ++j) {
-            const int k = kc * KC + g * G + j;
-            v[j] = (colok && k < nc) ? X[(int64_t)cm[k] * ldx + col] : 0.0f;
+          for (int q = 0; q < QN; ++q) {
+            float t[4];
+            quad_transpose(v[q], rr, t);                // t[j] = row 4q + j of column n
+            uint4 hi, lo;
+            Split<TF32>::run(t, hi, lo);
+            const uint32_t off = sw128((uint32_t)n, (uint32_t)(q * 16));
+            *reinterpret_cast<uint4*>(bhi + off) = hi;
+            *reinterpret_cast<uint4*>(blo + off) = lo;
           }
-          uint4 hi, lo;
-          Split<TF32>::run(v, hi, lo);
-          const uint32_t off = sw128((uint32_t)n, (uint32_t)(g * 16));
-          *reinterpret_cast<uint4*>(bhi + off) = hi;
-          *reinterpret_cast<uint4*>(blo + off) = lo;
+        } else {
+#pragma unroll
+          for (int q = 0; q < QN; q += 2) {               // two row quads = one chunk of 8
+            float t[8];
+            quad_transpose(v[q], rr, t);
+            quad_transpose(v[q + 1], rr, t + 4);
+            uint4 hi, lo;
+            Split<TF32>::run(t, hi, lo);
+            const uint32_t off = sw128((uint32_t)n, (uint32_t)((q / 2) * 16));
+            *reinterpret_cast<uint4*>(bhi + off) = hi;
+            *reinterpret_cast<uint4*>(blo + off) = lo;
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&sh->b_full[sb]);
@@ -358,16 +398,25 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
 }
 
 // ------------------------------------------------------------ FP32 helpers
+// Z = s1 X + s2 Xp on FP32 blocks; grid.y = row blocks, threads over float4 column groups
+// (ld and the row starts are multiples of 4 floats).
 __global__ void k_axpby_init32(float* __restrict__ Z, int64_t ldz, const float* __restrict__ X, int64_t ldx,
                                const float* __restrict__ Xp, int64_t ldp, int64_t M, int ncol, float s1, float s2) {
+  const int nq = (ncol + 3) / 4;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= M * ncol) return;
-  const int64_t i = t / ncol;
-  const int j = (int)(t - i * ncol);
-  float v = 0.0f;
-  if (s1 != 0.0f) v = s1 * X[i * ldx + j];
-  if (Xp) v = fmaf(s2, Xp[i * ldp + j], v);
-  Z[i * ldz + j] = v;
+  if (t >= M * nq) return;
+  const int64_t i = t / nq;
+  const int c = (int)(t - i * nq) * 4;
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (s1 != 0.0f) {
+    const float4 x = *reinterpret_cast<const float4*>(X + i * ldx + c);
+    v = make_float4(s1 * x.x, s1 * x.y, s1 * x.z, s1 * x.w);
+  }
+  if (Xp) {
+    const float4 p = *reinterpret_cast<const float4*>(Xp + i * ldp + c);
+    v = make_float4(fmaf(s2, p.x, v.x), fmaf(s2, p.y, v.y), fmaf(s2, p.z, v.z), fmaf(s2, p.w, v.w));
+  }
+  *reinterpret_cast<float4*>(Z + i * ldz + c) = v;
 }
 
 __global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy,
@@ -388,26 +437,52 @@ __global__ void k_to_f64(const float* __restrict__ Y, int64_t ldy, double* __res
   X[i * ldx + j] = (double)Y[i * ldy + j];
 }
 
-__global__ void __launch_bounds__(256) k_nl_coef32(const float* __restrict__ X, int64_t ldx, int ncol,
-                                                   const int64_t* __restrict__ prow, const int32_t* __restrict__ pnode,
-                                                   const double* __restrict__ pval, const double* __restrict__ hcoup,
-                                                   float* __restrict__ P) {
+// Projector coefficients in two stages for parallelism: stage 1, CTA (a, s) sums split s
+// of projector a's support (8 warps x 4 unrolled loads per lane); stage 2 adds the splits
+// in a fixed order and scales by h_a.
+constexpr int kNlSplits = 8;
+__global__ void __launch_bounds__(256) k_nl_coef32_part(const float* __restrict__ X, int64_t ldx, int ncol,
+                                                        const int64_t* __restrict__ prow,
+                                                        const int32_t* __restrict__ pnode,
+                                                        const double* __restrict__ pval, float* __restrict__ part) {
   __shared__ float red[8][32];
-  const int a = blockIdx.x;
+  const int a = blockIdx.x / kNlSplits, sidx = blockIdx.x % kNlSplits;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.y * 32 + lane;
+  const int64_t e0 = prow[a], e1 = prow[a + 1];
+  const int64_t len = (e1 - e0 + kNlSplits - 1) / kNlSplits;
+  const int64_t s0 = e0 + sidx * len, s1 = min(e1, s0 + len);
   float s = 0.0f;
-  if (col < ncol)
-    for (int64_t e = prow[a] + warp; e < prow[a + 1]; e += 8)
-      s = fmaf((float)pval[e], X[(int64_t)pnode[e] * ldx + col], s);
+  if (col < ncol) {
+    int64_t e = s0 + warp;
+    for (; e + 24 < s1; e += 32) {
+      const float x0 = X[(int64_t)pnode[e] * ldx + col], x1 = X[(int64_t)pnode[e + 8] * ldx + col];
+      const float x2 = X[(int64_t)pnode[e + 16] * ldx + col], x3 = X[(int64_t)pnode[e + 24] * ldx + col];
+      s = fmaf((float)pval[e], x0, s);
+      s = fmaf((float)pval[e + 8], x1, s);
+      s = fmaf((float)pval[e + 16], x2, s);
+      s = fmaf((float)pval[e + 24], x3, s);
+    }
+    for (; e < s1; e += 8) s = fmaf((float)pval[e], X[(int64_t)pnode[e] * ldx + col], s);
+  }
   red[warp][lane] = s;
   __syncthreads();
   if (warp == 0 && col < ncol) {
     float t = 0.0f;
 #pragma unroll
     for (int w = 0; w < 8; ++w) t += red[w][lane];
-    P[(int64_t)a * ncol + col] = (float)hcoup[a] * t;
+    part[((int64_t)blockIdx.x) * ncol + col] = t;
   }
+}
+
+__global__ void k_nl_coef32_reduce(const float* __restrict__ part, const double* __restrict__ hcoup, int nproj,
+                                   int ncol, float* __restrict__ P) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nproj * ncol) return;
+  const int a = (int)(t / ncol), col = (int)(t % ncol);
+  float s = 0.0f;
+  for (int k = 0; k < kNlSplits; ++k) s += part[((int64_t)a * kNlSplits + k) * ncol + col];
+  P[t] = (float)hcoup[a] * s;
 }
 
 __global__ void __launch_bounds__(256) k_nl_add32(float* __restrict__ Z, int64_t ldz, int ncol,
@@ -457,11 +532,15 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
                               const float* Xp, int64_t ldp, float* Z, int64_t ldz, int ncol, float alpha, float s1,
                               float s2, int* err) {
   auto* m = h->mesh;
-  DFTFE_LAUNCH(k_axpby_init32, nblk(m->M * ncol), 256, 0, h->stream, Z, ldz, X, ldx, Xp, ldp, m->M, ncol, s1, s2);
+  DFTFE_LAUNCH(k_axpby_init32, nblk(m->M * ((ncol + 3) / 4)), 256, 0, h->stream, Z, ldz, X, ldx, Xp, ldp, m->M, ncol,
+               s1, s2);
   if (h->nproj > 0) {
     float* P = (float*)ws_get(h, "nl_coef32", sizeof(float) * h->nproj * (size_t)ncol);
-    dim3 g1((unsigned)h->nproj, (unsigned)((ncol + 31) / 32));
-    DFTFE_LAUNCH(k_nl_coef32, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval, h->d_h, P);
+    float* Pp = (float*)ws_get(h, "nl_coef32_part", sizeof(float) * h->nproj * (size_t)kNlSplits * ncol);
+    dim3 g1((unsigned)(h->nproj * kNlSplits), (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_nl_coef32_part, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval, Pp);
+    DFTFE_LAUNCH(k_nl_coef32_reduce, nblk((int64_t)h->nproj * ncol), 256, 0, h->stream, Pp, h->d_h, h->nproj,
+                 ncol, P);
     dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
     DFTFE_LAUNCH(k_nl_add32, g2, 256, 0, h->stream, Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj, h->d_sval, P,
                  h->nsup, alpha);

@@ -162,6 +162,11 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
                             const dftfe_bounds& b, bool tf32);
 void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32);
 
+// dense_mixed.cu (FP64 diagonal, FP32 off-diagonal)
+void gram_lower_mixed(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
+                      double* C);
+void rotate_inplace_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper);
+
 // dense.cu
 void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb,
                 int64_t M, int N, double* C, double* part, int nsplit);

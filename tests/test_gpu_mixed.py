@@ -121,3 +121,37 @@ def test_mixed_passes_meet_tolerances(dg, pair, prec):
     ok = rg_o[:nconv] < 1e-6
     tol = 1e-5 if prec == 2 else 1e-4
     assert np.all(rgg[:nconv][ok] <= tol), (rgg[:nconv], rg_o[:nconv])
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_mixed_cholgs_orthonormalises(dg, pair, prec):
+    """FP64 diagonal / FP32 off-diagonal overlap and rotation: X^T X = I to FP32 level,
+    and the span is the oracle's (projectors agree)."""
+    om, oh, mesh, ham = pair
+    N = 24
+    X0 = synth.random_block(41, om.ndofs, N) @ np.diag(np.linspace(1.0, 20.0, N))
+    X = torch.from_numpy(X0).cuda()
+    dg.dftfe_cholgs(ham, X, prec)
+    x = X.cpu().numpy()
+    assert np.abs(x.T @ x - np.eye(N)).max() < 2e-5
+    ref, _, _ = oracle.cholgs(X0)
+    if om.ndofs <= 4000:
+        assert np.abs(x @ x.T - ref @ ref.T).max() < 2e-5
+
+
+@pytest.mark.parametrize("prec", [2, 1])
+def test_mixed_rayleigh_ritz_near_converged(dg, pair, prec):
+    """On a nearly converged basis (the mixed scheme's regime) the mixed Rayleigh-Ritz
+    gives the FP64 oracle's Ritz values within 1e-6 Ha."""
+    om, oh, mesh, ham = pair
+    N = 12
+    lam, V = np.linalg.eigh(oh.dense()) if om.ndofs <= 4000 else (None, None)
+    if V is None:
+        pytest.skip("dense reference too large")
+    noise = 1e-3 * synth.random_block(42, om.ndofs, N)
+    Xo, _, _ = oracle.cholgs(V[:, :N] + noise)
+    X = torch.from_numpy(Xo.copy()).cuda()
+    ev = torch.empty(N, dtype=torch.float64, device="cuda")
+    dg.dftfe_rayleigh_ritz(ham, X, ev, None, prec)
+    _, _, theta, _ = oracle.rayleigh_ritz(oh.apply, Xo)
+    assert np.abs(ev.cpu().numpy() - theta).max() < 1e-6
