@@ -46,3 +46,33 @@ def small_case(seed=0, n=(4, 3, 2), p=4, L=8.0, nl=True, vquad=0):
         hc = np.array([0.5 + 1.5 * s.uniform() for _ in range(4 * len(cent))])
         proj = (cent, 1.0, 2.5, hc)
     return dict(L=L, n=n, p=p, centres=cent, depth=2.0, width=1.0, vquad=vquad, proj=proj)
+
+
+def oracle_rows(om, oh, rows, ncol, seed, with_nonlocal=True, absolute=False):
+    """Rows `rows` of H~ X (or of |H~| |X|) for X = synth.random_block(seed, M, ncol),
+    computed cell by cell without forming X: only the rows the touched cells need are
+    generated.  The oracle's potential must be set for every touched cell."""
+    rows = np.asarray(rows)
+    flat = om.cell_map.ravel()
+    out = np.zeros((len(rows), ncol))
+    cache = {}
+    for r, j in enumerate(rows):
+        for s in np.nonzero(flat == j)[0]:
+            c, l = divmod(int(s), om.nodes_per_cell)
+            if c not in cache:
+                Hc = oh.cell_matrix(c)
+                Xc = synth.random_rows(seed, om.cell_map[c], ncol)
+                cache[c] = (np.abs(Hc), np.abs(Xc)) if absolute else (Hc, Xc)
+            Hc, Xc = cache[c]
+            out[r] += Hc[l] @ Xc
+    if with_nonlocal and oh.Ct is not None:
+        sup = np.unique(oh.Ct.tocoo().row)
+        Xs = synth.random_rows(seed, sup, ncol)
+        Ct = oh.Ct.tocsr()[sup]                      # support rows only
+        if absolute:
+            P = np.abs(oh.h)[:, None] * (abs(Ct).T @ np.abs(Xs))
+            out += abs(oh.Ct.tocsr()[rows]) @ P
+        else:
+            P = oh.h[:, None] * (Ct.T @ Xs)
+            out += oh.Ct.tocsr()[rows] @ P
+    return out
