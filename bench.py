@@ -248,7 +248,7 @@ def run_ours(args, rank, world, local, tdist):
     ms = max_over_ranks(ms, tdist, dev)
     fam = {}
     for name in ("pass_filter", "pass_cholgs", "pass_rr", "cell_gemm_fp64", "cell_gemm_tf32x3",
-                 "cell_gemm_bf16x3", "gram", "rotate", "syevd"):
+                 "cell_gemm_bf16x3", "cell_gemm_df", "gram", "gram_mixed", "rotate", "rotate_mixed", "syevd"):
         t, n = dg.dftfe_profile_query(ham, name)
         if n:
             fam[name] = {"ms": t / args.steps, "launches": n // args.steps}
@@ -288,6 +288,14 @@ def run_ours(args, rank, world, local, tdist):
                           "tensor_peak_tflops": tensor_peak[p],
                           "tensor_peak_source": "measured bf16 sustained" + (" x nominal tf32/bf16 (1.1/2.25)"
                                                                           if p == "tf32x3" else "")}
+    if "cell_gemm_df" in fam:
+        a = 2.0 * Nc * nc * nc * N / (fam["cell_gemm_df"]["ms"] / 1e3) / 1e12
+        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        roofs["cell_gemm_df"] = {"kernel": "k_cell_df_wide (float-pair FP64-accurate cell products, W = H~X)",
+                                 "bound": "alu", "achieved": a, "peak": fp32_peak / 12.0, "unit": "TFLOP/s",
+                                 "frac": a / (fp32_peak / 12.0),
+                                 "peak_source": "derived: FP32 peak 152 SMs x 128 FMA/clk x 2 x 2.07 GHz / 12 "
+                                                "FP32 instructions per float-pair multiply-add"}
     for key, flops, label in (("gram", 2 * M * N * N * 0.5625 * 2, "k_gram_partial (S, H^ lower tiles, FP64)"),
                               ("rotate", 2 * M * N * N * 2.5, "k_rotate (X L^-T, X Q, W Q, FP64)")):
         if key in fam:

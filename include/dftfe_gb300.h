@@ -56,13 +56,17 @@ typedef enum {
   DFTFE_MIXED_BF16X3 = 1,  /* filter: cell products as 3-term BF16 splits (hi*hi + hi*lo +
                               lo*hi) on the tensor cores (tcgen05), FP32 accumulation, FP32
                               vectors; CholGS, Rayleigh-Ritz and residuals in FP64 */
-  DFTFE_MIXED_TF32X3 = 2   /* as above with 3-term TF32 splits (about 2^-21 relative per
+  DFTFE_MIXED_TF32X3 = 2,  /* as above with 3-term TF32 splits (about 2^-21 relative per
                               product instead of 2^-16) */
+  DFTFE_FP64_FLOAT_PAIRS = 3 /* dftfe_ham_apply only: FP64-accurate cell products from pairs
+                              of floats (error-free products, TwoSum accumulation, about 44
+                              significant bits) on the FP32 pipes; FP64 in and out */
   /* In dftfe_cholgs, dftfe_rayleigh_ritz and the pass, either mixed value selects the
      mixed overlap / projection / rotation of Sec. 3.2: diagonal entries of S and H^ and
-     the diagonal part of each rotation in FP64, off-diagonal parts in FP32; W = H~X,
-     the Cholesky factorisation, the eigensolve and the residuals stay FP64 (split
-     products for W move the Ritz values by 1e-6 to 2e-6 Ha). */
+     the diagonal part of each rotation in FP64, off-diagonal parts in FP32; W = H~X
+     for the projection and the residuals uses the float-pair products of
+     DFTFE_FP64_FLOAT_PAIRS (split products there move the Ritz values by 1e-6 to
+     2e-6 Ha); the Cholesky factorisation and the eigensolve stay FP64. */
 } dftfe_precision;
 
 typedef struct dftfe_mesh_s* dftfe_mesh; /* opaque, library-owned */

@@ -40,9 +40,11 @@ static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals,
   auto* m = h->mesh;
   const int N = ncol;
   const bool mixed = prec != DFTFE_FP64;
-  // W = H~X stays FP64 in every precision: with split-precision cell products here the
-  // Ritz values move by 1e-6 (TF32x3) to 2e-6 Ha (BF16x3), the size of the mixed tolerance
-  apply_combo(h, X, ld, nullptr, 0, W, ldw, N, 1.0, 0.0, 0.0);
+  // W = H~X must be FP64-accurate in every precision (split-precision cell products here
+  // move the Ritz values by 1e-6 to 2e-6 Ha, the size of the mixed tolerance): FP64 in
+  // the FP64 pass, float pairs (about 44 bits) on the FP32 pipes in a mixed pass
+  if (mixed) apply_df(h, X, ld, W, ldw, N);
+  else apply_combo(h, X, ld, nullptr, 0, W, ldw, N, 1.0, 0.0, 0.0);
   double* Hh = (double*)ws_get(h, "Hhat", sizeof(double) * (size_t)N * N);
   double* Q = (double*)ws_get(h, "Q", sizeof(double) * (size_t)N * N);
   int* st = (int*)ws_get(h, "status", sizeof(int) * 4);

@@ -408,23 +408,28 @@ __global__ void __launch_bounds__(32) k_tql(double* __restrict__ dg, double* __r
         } else {
           ++iter;
           double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-          double r = hypot(g, 1.0);
+          double r = sqrt(fma(g, g, 1.0));
           g = d[m] - d[l] + e[l] / (g + copysign(r, g));
           double s = 1.0, c = 1.0, p = 0.0;
           int i = m - 1;
           bool early = false;
           for (; i >= l; --i) {
             const double f = s * e[i], b = c * e[i];
-            r = hypot(f, g);
-            e[i + 1] = r;
-            if (r == 0.0) {
+            // Givens rotation from (f, g): one reciprocal square root instead of a
+            // hypot and two divisions (the FP64 pipe is slow; this loop is serial)
+            const double r2 = fma(f, f, g * g);
+            if (r2 == 0.0) {
+              e[i + 1] = 0.0;
               d[i + 1] -= p;
               e[m] = 0.0;
               early = true;
               break;
             }
-            s = f / r;
-            c = g / r;
+            const double rinv = rsqrt(r2);
+            r = r2 * rinv;
+            e[i + 1] = r;
+            s = f * rinv;
+            c = g * rinv;
             g = d[i + 1] - p;
             r = (d[i] - g) * s + 2.0 * c * b;
             p = s * r;

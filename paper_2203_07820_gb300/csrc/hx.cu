@@ -239,6 +239,20 @@ void apply_combo(dftfe_ham h, const double* X, int64_t ldx, const double* Xprev,
   local_part(h, X, ldx, Z, ldz, ncol, alpha);
 }
 
+void apply_nonlocal_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {
+  auto* m = h->mesh;
+  DFTFE_LAUNCH(k_axpby_init, nblk(m->M * ncol), 256, 0, h->stream, Y, ldy, X, ldx, nullptr, 0, m->M, ncol, 0.0,
+               0.0);
+  if (h->nproj > 0) {
+    double* P = (double*)ws_get(h, "nl_coef", sizeof(double) * h->nproj * (size_t)ncol);
+    dim3 g1((unsigned)h->nproj, (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_nl_coef, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval, h->d_h, P);
+    dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_nl_add, g2, 256, 0, h->stream, Y, ldy, ncol, h->d_snode, h->d_srow, h->d_sproj, h->d_sval, P,
+                 h->nsup, 1.0);
+  }
+}
+
 // Eq. chebyfilter.  Unscaled: X1 = (H~ - c) X0 / e, X_{k+1} = 2 (H~ - c) X_k / e - X_{k-1}.
 // Scaled (Zhou-Saad): sigma1 = e / (a0 - c), X1 = sigma1 (H~ - c) X0 / e,
 // sigma_{k+1} = 1 / (2/sigma1 - sigma_k), X_{k+1} = 2 sigma_{k+1} (H~ - c) X_k / e
@@ -290,10 +304,12 @@ extern "C" dftfe_status dftfe_ham_apply(dftfe_ham h, const double* X, int64_t ld
   ABI_BEGIN
   DFTFE_REQUIRE(h && X && Y, "null argument");
   DFTFE_REQUIRE(ncol >= 0 && ldx >= ncol && ldy >= ncol, "bad ncol / leading dimension");
-  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3 ||
+                    prec == DFTFE_FP64_FLOAT_PAIRS,
                 "unknown precision");
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   if (prec == DFTFE_FP64) apply_combo(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
+  else if (prec == DFTFE_FP64_FLOAT_PAIRS) apply_df(h, X, ldx, Y, ldy, ncol);
   else apply_mixed(h, X, ldx, Y, ldy, ncol, prec == DFTFE_MIXED_TF32X3);
   ABI_END
 }

@@ -646,3 +646,106 @@ void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t l
 }
 
 }  // namespace dftfe
+
+// ---------------------------------------------------------------------------------
+// FP64-accurate H~X on the FP32 pipes (GB300 issues FP32 about 60x faster than FP64):
+// each entry as an unevaluated pair of floats h = h_hi + h_lo, x likewise; a product is
+// h_hi x_hi plus its exact rounding error (one FMA) plus the two cross terms, and the
+// running sum is kept as a pair with Knuth's TwoSum, so the result carries about 44
+// significant bits.  Same colour-ordered gather / cell product / scatter-add structure as
+// the FP64 kernel; output FP64.
+namespace dftfe {
+
+__global__ void k_split_df(const double* __restrict__ Hc, float2* __restrict__ Hdf, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double h = Hc[t];
+  const float hi = __double2float_rn(h);
+  Hdf[t] = make_float2(hi, __double2float_rn(h - (double)hi));
+}
+
+constexpr int DF_ROWS = 8;
+__global__ void __launch_bounds__(256, 2) k_cell_df_wide(const float2* __restrict__ Hdf,
+                                                         const int32_t* __restrict__ map,
+                                                         const int32_t* __restrict__ cells, int nc,
+                                                         const double* __restrict__ X, int64_t ldx,
+                                                         double* __restrict__ Z, int64_t ldz, int ncol) {
+  extern __shared__ float2 xs2[];                       // nc x 32 pairs
+  int32_t* sm = (int32_t*)(xs2 + nc * 32);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t cell = cells[blockIdx.x];
+  const int col = blockIdx.y * 32 + lane;
+  const bool colok = col < ncol;
+  const int32_t* m = map + cell * nc;
+  for (int k = threadIdx.x; k < nc; k += 256) sm[k] = m[k];
+  __syncthreads();
+  for (int k = warp; k < nc; k += 8) {
+    const double xd = colok ? X[(int64_t)sm[k] * ldx + col] : 0.0;
+    const float hi = __double2float_rn(xd);
+    xs2[k * 32 + lane] = make_float2(hi, __double2float_rn(xd - (double)hi));
+  }
+  __syncthreads();
+  const float2* H = Hdf + cell * (int64_t)nc * nc;
+  for (int r0 = warp * DF_ROWS; r0 < nc; r0 += 8 * DF_ROWS) {
+    const int nr = min(DF_ROWS, nc - r0);
+    float ah[DF_ROWS], al[DF_ROWS];
+#pragma unroll
+    for (int i = 0; i < DF_ROWS; ++i) ah[i] = al[i] = 0.0f;
+    const float2* Hr = H + (int64_t)r0 * nc;
+    for (int k = 0; k < nc; ++k) {
+      const float2 x = xs2[k * 32 + lane];
+#pragma unroll
+      for (int i = 0; i < DF_ROWS; ++i) {
+        if (i < nr) {
+          const float2 h = __ldg(Hr + (int64_t)i * nc + k);
+          const float p = h.x * x.x;
+          float e = fmaf(h.x, x.x, -p);               // exact error of the leading product
+          e = fmaf(h.x, x.y, e);
+          e = fmaf(h.y, x.x, e);
+          const float s = ah[i] + p;                  // TwoSum(ah, p)
+          const float bb = s - ah[i];
+          const float err = (ah[i] - (s - bb)) + (p - bb);
+          ah[i] = s;
+          al[i] += err + e;
+        }
+      }
+    }
+    if (colok) {
+#pragma unroll
+      for (int i = 0; i < DF_ROWS; ++i)
+        if (i < nr) Z[(int64_t)sm[r0 + i] * ldz + col] += (double)ah[i] + (double)al[i];
+    }
+  }
+}
+
+static unsigned nblk2(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// Y = H~ X with the pair-of-floats cell products (nonlocal part FP64).
+void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {
+  auto* m = h->mesh;
+  const int nc = m->nc;
+  static bool attr = false;
+  if (!attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_df_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    attr = true;
+  }
+  const size_t n2 = (size_t)m->Nc * nc * nc;
+  float2* Hdf = (float2*)ws_get(h, "cells_df", sizeof(float2) * n2);
+  if (h->df_version != h->potential_version) {
+    DFTFE_LAUNCH(k_split_df, nblk2((int64_t)n2), 256, 0, h->stream, h->d_Hc, Hdf, (int64_t)n2);
+    h->df_version = h->potential_version;
+  }
+  // zero output and the FP64 nonlocal part, then the cell products colour by colour
+  apply_nonlocal_fp64(h, X, ldx, Y, ldy, ncol);
+  const size_t sh = (size_t)nc * 32 * sizeof(float2) + nc * sizeof(int32_t);
+  for (int c = 0; c < h->ncolours; ++c) {
+    const int64_t n = h->colour_off[c + 1] - h->colour_off[c];
+    if (n == 0) continue;
+    const int32_t* cells = h->d_colour_cells + h->colour_off[c];
+    ProfScope ps(h, "cell_gemm_df");
+    dim3 grid((unsigned)n, (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_cell_df_wide, grid, 256, sh, h->stream, Hdf, h->d_map, cells, nc, X, ldx, Y, ldy, ncol);
+  }
+}
+
+}  // namespace dftfe

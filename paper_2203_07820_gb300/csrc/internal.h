@@ -121,6 +121,7 @@ struct dftfe_ham_s {
   bool has_potential = false;
   int64_t potential_version = 0;   // bumped by every set_potential
   int64_t mixed_version[2] = {-1, -1};  // potential version of the split tiles (bf16, tf32)
+  int64_t df_version = -1;              // potential version of the float-pair cell matrices
   // a3: nonlocal (CSR by projector and by node)
   int nproj = 0;
   double* d_h = nullptr;
@@ -161,6 +162,9 @@ void copy_block(cudaStream_t s, const double* src, int64_t lds, double* dst, int
 void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int degree,
                             const dftfe_bounds& b, bool tf32);
 void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32);
+void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol);
+// hx.cu: Y = H~_nl X (Y overwritten; zero when there are no projectors), FP64
+void apply_nonlocal_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol);
 
 // dense_mixed.cu (FP64 diagonal, FP32 off-diagonal)
 void gram_lower_mixed(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,

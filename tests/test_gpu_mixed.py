@@ -155,3 +155,16 @@ def test_mixed_rayleigh_ritz_near_converged(dg, pair, prec):
     dg.dftfe_rayleigh_ritz(ham, X, ev, None, prec)
     _, _, theta, _ = oracle.rayleigh_ritz(oh.apply, Xo)
     assert np.abs(ev.cpu().numpy() - theta).max() < 1e-6
+
+
+@pytest.mark.parametrize("ncol", [1, 33, 64])
+def test_float_pair_apply_is_fp64_accurate(dg, pair, ncol):
+    """DFTFE_FP64_FLOAT_PAIRS (used for W = H~X in mixed passes): error-free products and
+    TwoSum accumulation on float pairs keep about 44 bits, checked against 2^-40 |H~||X|."""
+    om, oh, mesh, ham = pair
+    X0 = synth.random_block(300 + ncol, om.ndofs, ncol)
+    X = torch.from_numpy(X0).cuda()
+    Y = torch.full_like(X, float("nan"))
+    dg.dftfe_ham_apply(ham, X, Y, dg.DFTFE_FP64_FLOAT_PAIRS)
+    err = np.abs(Y.cpu().numpy() - oh.apply(X0))
+    assert np.all(err <= 2.0 ** -40 * abs_bound(om, oh, X0) + 1e-300)
