@@ -14,8 +14,9 @@
 // One CTA per SM walks the cells of one colour (no two share a node).  Warp roles:
 //   warp 0      A producer (bulk copies of the split cell-matrix tiles, 4-stage ring)
 //   warp 1      TMEM owner and MMA issuer (one elected lane)
-//   warps 2-5   B producers (gather + split of X^c, 2-stage ring)
+//   warps 2-5   B producers (gather + split of X^c, 2-stage ring, loads one chunk ahead)
 //   warps 6-9   epilogue (tcgen05.ld of the accumulators, scatter-add alpha*Y into Z)
+//   warp 10     L2 prefetch of the next cell's X and Z rows
 // Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its
 // own copies and MMAs (bounded), frees its tensor memory and returns.
 #include "internal.h"
@@ -29,7 +30,8 @@ namespace dftfe {
 
 namespace mx {
 
-constexpr int kThreads = 320;
+constexpr int kPrefetchWarp = 10;
+constexpr int kThreads = 352;
 constexpr int kStagesA = 4, kStagesB = 2;
 constexpr int kTile = 16384;                       // one 128-row x 128-byte operand tile
 constexpr int kStageBytes = 2 * kTile;             // hi + lo
@@ -62,6 +64,7 @@ struct Shared {
   uint64_t acc_full, acc_empty, drain;
   uint32_t tmem;
   int abort;
+  int mma_cell;                                     // cell the MMA lane is working on
 };
 
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
@@ -219,6 +222,7 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     mbar_init(&sh->acc_empty, 128);
     mbar_init(&sh->drain, 1);
     sh->abort = 0;
+    sh->mma_cell = -1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -262,6 +266,7 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
       for (int i = 0; i < my_cells && !*abort; ++i) {
         if (!mbar_wait(&sh->acc_empty, (i & 1) ^ 1, abort, err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        *(volatile int*)&sh->mma_cell = i;
         for (int kc = 0; kc < nkc && !*abort; ++kc, ++tb) {
           const int sb = tb % kStagesB;
           if (!mbar_wait(&sh->b_full[sb], (tb / kStagesB) & 1, abort, err)) break;
@@ -290,7 +295,7 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
       volatile int no_abort = 0;
       mbar_wait(&sh->drain, 0, &no_abort, err);
     }
-  } else if (warp < 6) {
+  } else if (warp >= 2 && warp < 6) {
     // ------------------------------------------------------------ B producers
     // warp w covers tile rows (columns of X) 32w..32w+31; lane l loads a float4 of row
     // 4q + (l & 3) at columns 32w + 4(l >> 2) .. +3, then a 4x4 transpose inside each
@@ -300,19 +305,25 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     const int rr = lane & 3;
     const int colq = col0 + 32 * w + 4 * (lane >> 2);
     constexpr int QN = KC / 4;                   // row quads per K-chunk
-    uint32_t tb = 0;
-    for (int i = 0; i < my_cells && !*abort; ++i) {
-      const int64_t cell = cells[blockIdx.x + (int64_t)i * gridDim.x];
+    // loads of chunk tb+1 are issued before chunk tb is transposed and stored
+    const uint32_t nchunks = (uint32_t)my_cells * (uint32_t)nkc;
+    float4 v[QN], vn[QN];
+    auto load_chunk = [&](uint32_t t, float4* dst) {
+      const int64_t cell = cells[blockIdx.x + (int64_t)(t / nkc) * gridDim.x];
+      const int kc = (int)(t % nkc);
       const int32_t* cm = map + cell * nc;
-      for (int kc = 0; kc < nkc; ++kc, ++tb) {
-        float4 v[QN];
 #pragma unroll
-        for (int q = 0; q < QN; ++q) {
-          const int k = kc * KC + 4 * q + rr;
-          v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (k < nc && colq < ncol)
-            v[q] = __ldg(reinterpret_cast<const float4*>(X + (int64_t)cm[k] * ldx + colq));
-        }
+      for (int q = 0; q < QN; ++q) {
+        const int k = kc * KC + 4 * q + rr;
+        dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < nc && colq < ncol)
+          dst[q] = __ldg(reinterpret_cast<const float4*>(X + (int64_t)cm[k] * ldx + colq));
+      }
+    };
+    if (nchunks > 0) load_chunk(0, v);
+    for (uint32_t tb = 0; tb < nchunks && !*abort; ++tb) {
+      {
+        if (tb + 1 < nchunks) load_chunk(tb + 1, vn);
         const int sb = tb % kStagesB;
         if (!mbar_wait(&sh->b_empty[sb], ((tb / kStagesB) & 1) ^ 1, abort, err)) break;
         uint8_t* bhi = sB + sb * kStageBytes;
@@ -343,6 +354,34 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&sh->b_full[sb]);
+      }
+#pragma unroll
+      for (int q = 0; q < QN; ++q) v[q] = vn[q];
+    }
+  } else if (warp == kPrefetchWarp) {
+    // ------------------------------------------------------------ L2 prefetch
+    {
+      // pull the X rows (gathered by the B producers) and the Z rows (updated
+      // by the epilogue) of the next cell into L2 while the current cell is computed, so
+      // the gather and the read-modify-write do not wait on HBM latency.  The MMA lane
+      // publishes the cell it is working on; prefetching runs one cell ahead of it.
+      const uint32_t xbytes = 4u * (uint32_t)min(128, (int)(ldx - col0));
+      const uint32_t zbytes = 4u * (uint32_t)min(128, (int)(ldz - col0));
+      long spins = 0;
+      for (int next = 0; next < my_cells && !*abort;) {
+        if (next > *(volatile int*)&sh->mma_cell + 1) {
+          if (++spins > kSpinLimit) break;
+          __nanosleep(256);
+          continue;
+        }
+        const int64_t cell = cells[blockIdx.x + (int64_t)next * gridDim.x];
+        const int32_t* cm = map + cell * nc;
+        for (int k = lane; k < nc; k += 32) {
+          const int64_t g = cm[k];
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(X + g * ldx + col0), "r"(xbytes) : "memory");
+          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(Z + g * ldz + col0), "r"(zbytes) : "memory");
+        }
+        ++next;
       }
     }
   } else {
