@@ -42,6 +42,10 @@ def workload(name, seed):
         # per-cell shape of the scale workload (p = 6, 1.25 bohr cells, block 128) on a
         # 10 bohr box: 512 cells, 110,592 DoFs, cell matrices 0.48 GB (> L2)
         return synth.lattice_atoms(seed, ncell=8, L=10.0, nside=1, nstates=128, block=128, passes=1)
+    if name == "profile12":
+        # same per-cell shape, 15 bohr box, 12^3 cells (216 per colour), 8 atoms: about
+        # 4.5 GB on the device in a mixed pass (for ncu captures)
+        return synth.lattice_atoms(seed, ncell=12, L=15.0, nside=2, nstates=128, block=128, passes=1)
     return synth.lattice_atoms(seed)
 
 
@@ -408,11 +412,11 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale", choices=["scale", "small", "profile"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3", "bf16x3"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "small", "profile", "profile12"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")

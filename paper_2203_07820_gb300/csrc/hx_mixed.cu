@@ -484,33 +484,35 @@ __global__ void __launch_bounds__(256) k_nl_coef32_part(const float* __restrict_
                                                         const int64_t* __restrict__ prow,
                                                         const int32_t* __restrict__ pnode,
                                                         const double* __restrict__ pval, float* __restrict__ part) {
-  __shared__ float red[8][32];
+  // CTA (a, s): split s of projector a's support; warp w takes every 8th entry; lane l
+  // holds columns 4l..4l+3 of a 128-column tile (blockIdx.y), read as one float4
+  __shared__ float4 red[8][32];
   const int a = blockIdx.x / kNlSplits, sidx = blockIdx.x % kNlSplits;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col = blockIdx.y * 32 + lane;
+  const int c0 = blockIdx.y * 128 + 4 * lane;
   const int64_t e0 = prow[a], e1 = prow[a + 1];
   const int64_t len = (e1 - e0 + kNlSplits - 1) / kNlSplits;
   const int64_t s0 = e0 + sidx * len, s1 = min(e1, s0 + len);
-  float s = 0.0f;
-  if (col < ncol) {
-    int64_t e = s0 + warp;
-    for (; e + 24 < s1; e += 32) {
-      const float x0 = X[(int64_t)pnode[e] * ldx + col], x1 = X[(int64_t)pnode[e + 8] * ldx + col];
-      const float x2 = X[(int64_t)pnode[e + 16] * ldx + col], x3 = X[(int64_t)pnode[e + 24] * ldx + col];
-      s = fmaf((float)pval[e], x0, s);
-      s = fmaf((float)pval[e + 8], x1, s);
-      s = fmaf((float)pval[e + 16], x2, s);
-      s = fmaf((float)pval[e + 24], x3, s);
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (c0 < ncol) {
+    for (int64_t e = s0 + warp; e < s1; e += 8) {
+      const float w = (float)pval[e];
+      const float4 x = __ldg(reinterpret_cast<const float4*>(X + (int64_t)pnode[e] * ldx + c0));
+      s.x = fmaf(w, x.x, s.x); s.y = fmaf(w, x.y, s.y); s.z = fmaf(w, x.z, s.z); s.w = fmaf(w, x.w, s.w);
     }
-    for (; e < s1; e += 8) s = fmaf((float)pval[e], X[(int64_t)pnode[e] * ldx + col], s);
   }
   red[warp][lane] = s;
   __syncthreads();
-  if (warp == 0 && col < ncol) {
-    float t = 0.0f;
+  if (warp == 0) {
+    float4 t = red[0][lane];
 #pragma unroll
-    for (int w = 0; w < 8; ++w) t += red[w][lane];
-    part[((int64_t)blockIdx.x) * ncol + col] = t;
+    for (int w = 1; w < 8; ++w) {
+      const float4 u = red[w][lane];
+      t.x += u.x; t.y += u.y; t.z += u.z; t.w += u.w;
+    }
+    const float v[4] = {t.x, t.y, t.z, t.w};
+    for (int j = 0; j < 4; ++j)
+      if (c0 + j < ncol) part[((int64_t)blockIdx.x) * ncol + c0 + j] = v[j];
   }
 }
 
@@ -528,13 +530,31 @@ __global__ void __launch_bounds__(256) k_nl_add32(float* __restrict__ Z, int64_t
                                                   const int32_t* __restrict__ snode, const int64_t* __restrict__ srow,
                                                   const int32_t* __restrict__ sproj, const double* __restrict__ sval,
                                                   const float* __restrict__ P, int64_t nsup, float alpha) {
+  // one warp per support node and 128-column tile (blockIdx.y); lane l owns columns
+  // 4l..4l+3, so each node row is read and written as one contiguous 512-byte run
   const int lane = threadIdx.x & 31;
   const int64_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int col = blockIdx.y * 32 + lane;
-  if (s >= nsup || col >= ncol) return;
-  float acc = 0.0f;
-  for (int64_t t = srow[s]; t < srow[s + 1]; ++t) acc = fmaf((float)sval[t], P[(int64_t)sproj[t] * ncol + col], acc);
-  Z[(int64_t)snode[s] * ldz + col] += alpha * acc;
+  const int c0 = blockIdx.y * 128 + 4 * lane;
+  if (s >= nsup || c0 >= ncol) return;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t t = srow[s]; t < srow[s + 1]; ++t) {
+    const float w = (float)sval[t];
+    const float* p = P + (int64_t)sproj[t] * ncol + c0;
+    acc.x = fmaf(w, p[0], acc.x);
+    if (c0 + 1 < ncol) acc.y = fmaf(w, p[1], acc.y);
+    if (c0 + 2 < ncol) acc.z = fmaf(w, p[2], acc.z);
+    if (c0 + 3 < ncol) acc.w = fmaf(w, p[3], acc.w);
+  }
+  float* z = Z + (int64_t)snode[s] * ldz + c0;
+  float4 o = *reinterpret_cast<float4*>(z);          // in bounds: ldz is a multiple of 32
+  o.x = fmaf(alpha, acc.x, o.x); o.y = fmaf(alpha, acc.y, o.y);
+  o.z = fmaf(alpha, acc.z, o.z); o.w = fmaf(alpha, acc.w, o.w);
+  if (c0 + 3 < ncol) {
+    *reinterpret_cast<float4*>(z) = o;
+  } else {
+    const float v[4] = {o.x, o.y, o.z, o.w};
+    for (int j = 0; c0 + j < ncol; ++j) z[j] = v[j];
+  }
 }
 
 static unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
@@ -576,11 +596,11 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
   if (h->nproj > 0) {
     float* P = (float*)ws_get(h, "nl_coef32", sizeof(float) * h->nproj * (size_t)ncol);
     float* Pp = (float*)ws_get(h, "nl_coef32_part", sizeof(float) * h->nproj * (size_t)kNlSplits * ncol);
-    dim3 g1((unsigned)(h->nproj * kNlSplits), (unsigned)((ncol + 31) / 32));
+    dim3 g1((unsigned)(h->nproj * kNlSplits), (unsigned)((ncol + 127) / 128));
     DFTFE_LAUNCH(k_nl_coef32_part, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval, Pp);
     DFTFE_LAUNCH(k_nl_coef32_reduce, nblk((int64_t)h->nproj * ncol), 256, 0, h->stream, Pp, h->d_h, h->nproj,
                  ncol, P);
-    dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
+    dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 127) / 128));
     DFTFE_LAUNCH(k_nl_add32, g2, 256, 0, h->stream, Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj, h->d_sval, P,
                  h->nsup, alpha);
   }
@@ -731,24 +751,36 @@ __global__ void __launch_bounds__(256, 2) k_cell_df_wide(const float2* __restric
 #pragma unroll
     for (int i = 0; i < DF_ROWS; ++i) ah[i] = al[i] = 0.0f;
     const float2* Hr = H + (int64_t)r0 * nc;
-    for (int k = 0; k < nc; ++k) {
-      const float2 x = xs2[k * 32 + lane];
+    // pair product + TwoSum: exact error of the leading product, cross terms, and the
+    // rounding error of the running sum all go to the low word
+#define DF_MAC(i)                                                   \
+  {                                                                 \
+    const float2 h = __ldg(Hr + (int64_t)(i) * nc + k);            \
+    const float p = h.x * x.x;                                      \
+    float e = fmaf(h.x, x.x, -p);                                   \
+    e = fmaf(h.x, x.y, e);                                          \
+    e = fmaf(h.y, x.x, e);                                          \
+    const float s = ah[i] + p;                                      \
+    const float bb = s - ah[i];                                     \
+    const float err = (ah[i] - (s - bb)) + (p - bb);                \
+    ah[i] = s;                                                      \
+    al[i] += err + e;                                               \
+  }
+    if (nr == DF_ROWS) {
+      for (int k = 0; k < nc; ++k) {
+        const float2 x = xs2[k * 32 + lane];
 #pragma unroll
-      for (int i = 0; i < DF_ROWS; ++i) {
-        if (i < nr) {
-          const float2 h = __ldg(Hr + (int64_t)i * nc + k);
-          const float p = h.x * x.x;
-          float e = fmaf(h.x, x.x, -p);               // exact error of the leading product
-          e = fmaf(h.x, x.y, e);
-          e = fmaf(h.y, x.x, e);
-          const float s = ah[i] + p;                  // TwoSum(ah, p)
-          const float bb = s - ah[i];
-          const float err = (ah[i] - (s - bb)) + (p - bb);
-          ah[i] = s;
-          al[i] += err + e;
-        }
+        for (int i = 0; i < DF_ROWS; ++i) DF_MAC(i)
+      }
+    } else {
+      for (int k = 0; k < nc; ++k) {
+        const float2 x = xs2[k * 32 + lane];
+#pragma unroll
+        for (int i = 0; i < DF_ROWS; ++i)
+          if (i < nr) DF_MAC(i)
       }
     }
+#undef DF_MAC
     if (colok) {
 #pragma unroll
       for (int i = 0; i < DF_ROWS; ++i)
