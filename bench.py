@@ -32,6 +32,11 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
+# DRAM bytes (read + write) per cell per 128-column tile, from one ncu capture each on a
+# smaller workload with the same per-cell shape (profiles/cell_gemm_*_p6_block128.md);
+# a launch of this workload processes N_c / 8 cells, so traffic scales with the cells.
+DRAM_BYTES_PER_CELL = {"cell_gemm_tf32x3": (349.4e6 + 16.6e6) / 216,
+                       "cell_gemm_fp64": (124.1e6 + 10.2e6) / 64}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -310,7 +315,14 @@ def run_ours(args, rank, world, local, tdist):
     dom = max(timed, key=timed.get) if timed else None
     roofline = dict(roofs[dom]) if dom else None
     if roofline is not None:
-        roofline["traffic"] = None
+        cells_per_launch = Nc / 8.0
+        per_cell = DRAM_BYTES_PER_CELL.get(dom) if wl.degree == 6 else None
+        roofline["traffic"] = per_cell * cells_per_launch * min(N, 128) / 128 if per_cell else None
+        roofline["traffic_note"] = ("DRAM bytes per 128-column launch over N_c/8 cells, scaled from an ncu "
+                                    "capture on a 12^3- or 8^3-cell case" if per_cell else None)
+        if dom.startswith("cell_gemm_") and dom != "cell_gemm_fp64" and dom != "cell_gemm_df":
+            s_h = 8 if "tf32" in dom else 4
+            roofline["algorithmic_bytes_per_launch"] = (Nc * nc * nc * s_h + 3.0 * M * 128 * 4) / 8.0
         roofline["share_of_pass"] = fam[dom]["ms"] / (sec_per_pass * 1e3)
 
     # one extra FP64 pass and one pass in the timed precision from the same state: |d eps|
