@@ -16,6 +16,8 @@ It is a plain, slow, obviously-correct restatement of the paper's method
                                                                        Eq. nonlocalHamDiscrete, Alg. 4)
   chfsi.py        Chebyshev filter, Lanczos bounds, Cholesky-Gram-     (Eq. chebyfilter, Alg. 2)
                   Schmidt, Rayleigh-Ritz, residuals, one pass
+  density.py      spectrum-splitting Rayleigh-Ritz, Fermi level,      (Alg. 2 step 3a, Alg. 3)
+                  electron density at quadrature points
 
 Every function is FP64.  Library primitives used as single steps: numpy
 matmul/einsum, numpy.linalg.cholesky/eigh, scipy triangular solve, scipy.sparse
@@ -32,3 +34,4 @@ from .mesh import PeriodicMesh
 from .hamiltonian import Hamiltonian
 from .chfsi import (chebyshev_filter, lanczos_bounds, cholgs, rayleigh_ritz,
                     residuals, chfsi_pass, first_pass_bounds, Bounds)
+from .density import (fermi_dirac, fermi_level, rayleigh_ritz_split, density, KB_HA_PER_K)

@@ -73,3 +73,22 @@ def test_unscaled_potential_quadrature_weight_is_caught():
     H.set_potential(np.full((m.ncells, H.nq), 1.3))
     H.Wq = np.ones_like(H.Wq)                 # planted: quadrature weights dropped
     assert abs(H.cell_V(0).sum() - 1.3 * np.prod(m.h)) > 1e-3
+
+
+def test_density_without_mass_scaling_is_caught():
+    """Planted: psi~ used at the quadrature points without the M^-1/2 back-transform."""
+    from oracle.density import fermi_dirac, fermi_level, rayleigh_ritz_split, KB_HA_PER_K
+    m, H = wells_system(nl=False, vquad=1)
+    N, nfr = 12, 4
+    lam, V = np.linalg.eigh(H.dense())
+    X = V[:, :N]
+    th_fr, Xfr, th = rayleigh_ritz_split(H.apply, X, nfr)
+    kT = 500 * KB_HA_PER_K
+    ne = 2 * (N - nfr) + 3.1
+    f = fermi_dirac(th_fr, fermi_level(th_fr, N - nfr, ne, kT), kT)
+    bad = np.empty((m.ncells, H.nq))
+    for c in range(m.ncells):
+        rows = m.cell_map[c]
+        Po, Pf = H.Nq @ X[rows], H.Nq @ Xfr[rows]                 # missing M^-1/2
+        bad[c] = 2.0 * (np.sum(Po * Po, axis=1) + (Pf * Pf) @ (f - 1.0))
+    assert abs(np.sum(bad * (H.Wq * m.detJ)[None, :]) - ne) > 1e-2
