@@ -325,6 +325,34 @@ def run_ours(args, rank, world, local, tdist):
             roofline["algorithmic_bytes_per_launch"] = (Nc * nc * nc * s_h + 3.0 * M * 128 * 4) / 8.0
         roofline["share_of_pass"] = fam[dom]["ms"] / (sec_per_pass * 1e3)
 
+    # the downstream step of the pass (Alg. 2 step 3a + Alg. 3): split Rayleigh-Ritz on the
+    # top 12.5 % of the states, Fermi level (500 K, half-filled window), density at the
+    # quadrature points; timed once, outside the pass value
+    dens = None
+    if not args.no_density:
+        nfr = max(1, N // 8)
+        Xfr = torch.empty((M, nfr), dtype=torch.float64, device=dev)
+        evs = torch.empty(N, dtype=torch.float64, device=dev)
+        ffr = torch.empty(nfr, dtype=torch.float64, device=dev)
+        rho = torch.empty((Nc, (wl.degree + 1) ** 3), dtype=torch.float64, device=dev)
+        kT = 500.0 * 3.166811563e-6
+        ne = 2.0 * (N - nfr) + nfr
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d2 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        dg.dftfe_rayleigh_ritz_split(ham, X, nfr, evs, Xfr, prec)
+        mu = dg.dftfe_fermi_level(evs[N - nfr:], N - nfr, ne, kT, ffr)
+        d1.record(stream)
+        dg.dftfe_density(ham, X, Xfr, ffr, rho)
+        d2.record(stream)
+        torch.cuda.synchronize()
+        dens = {"split_rr_and_fermi_ms": d0.elapsed_time(d1), "density_ms": d1.elapsed_time(d2),
+                "nfr": nfr, "mu_Ha": mu, "kT_Ha": kT,
+                "density_fp64_tflops": 2.0 * Nc * (wl.degree + 1) ** 6 * (N + nfr) / (d1.elapsed_time(d2) / 1e3) / 1e12}
+        del Xfr, rho
+
     # one extra FP64 pass and one pass in the timed precision from the same state: |d eps|
     compare = None
     if args.precision != "fp64" and not args.no_compare:
@@ -390,6 +418,7 @@ def run_ours(args, rank, world, local, tdist):
         "clocks": clocks,
         "e2e": e2e,
         "mixed_vs_fp64": compare,
+        "density_step": dens,
         "bounds": {"a": bounds.a, "b": bounds.b, "a0": bounds.a0},
         "max_resid": float(rs.max().item()),
     }
@@ -434,6 +463,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-density", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

@@ -218,6 +218,34 @@ dftfe_status dftfe_chfsi_pass(dftfe_ham ham, double* X, int64_t ld, int ncol,
                               int block, int degree, dftfe_bounds* inout,
                               double* evals, double* resid, dftfe_precision prec);
 
+/* ---------------------------------------------- spectrum splitting and density */
+
+/* Spectrum-splitting Rayleigh-Ritz (Alg. 2 steps 1b, 2 and 3a) on an orthonormal X
+ * (Psi_o, e.g. after dftfe_cholgs): all ncol Ritz values, ascending, to evals (DEVICE,
+ * ncol), and the Ritz vectors of the top nfr values, Psi_fr = X Q'_fr, to Xfr (DEVICE
+ * M x nfr, ldfr >= nfr; 1 <= nfr <= min(ncol, 512)).  X is not modified.  prec as in
+ * dftfe_rayleigh_ritz.  Synchronises the stream. */
+dftfe_status dftfe_rayleigh_ritz_split(dftfe_ham ham, const double* X, int64_t ld, int ncol,
+                                       int nfr, double* evals, double* Xfr, int64_t ldfr,
+                                       dftfe_precision prec);
+
+/* Fermi level (Alg. 3 step 1): mu with 2 (n_oc + sum_i f(evals_fr[i], mu)) = n_elec,
+ * f(e, mu) = 1 / (1 + exp((e - mu) / kT)) (kT in Ha; the paper uses T = 500 K), the
+ * lowest n_oc states fully occupied.  evals_fr: DEVICE nfr values; f_fr: DEVICE nfr
+ * occupations written; mu: HOST.  DFTFE_ERR_ARG unless 2 n_oc < n_elec < 2 (n_oc + nfr).
+ * Runs on `stream` and synchronises it. */
+dftfe_status dftfe_fermi_level(const double* evals_fr, int nfr, int n_oc, double n_elec,
+                               double kT, double* f_fr, double* mu, void* stream);
+
+/* Electron density (Alg. 3 steps 2-3) at the quadrature points of every cell (the
+ * mesh's vquad rule): rho = 2 [ sum_i (n^T psi^_o,i)^2 + sum_k (f_k - 1)(n^T psi^_fr,k)^2 ]
+ * with psi^ = M^-1/2 psi~.  Xo: DEVICE M x ncol (ldo), the orthonormal basis; Xfr: DEVICE
+ * M x nfr (ldfr) and f_fr: DEVICE nfr (may be NULL when nfr = 0); rho: DEVICE
+ * ncells x quad_per_cell.  FP64. */
+dftfe_status dftfe_density(dftfe_ham ham, const double* Xo, int64_t ldo, int ncol,
+                           const double* Xfr, int64_t ldfr, int nfr, const double* f_fr,
+                           double* rho);
+
 /* Allocation-free Cholesky-Gram-Schmidt (the paper has no counterpart; this is an
  * interface for callers that cannot allocate device memory at the call site, e.g.
  * inside a fixed memory pool or a framework step that forbids cudaMalloc).  Same

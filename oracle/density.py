@@ -49,15 +49,17 @@ def rayleigh_ritz_split(apply, Xo, nfr):
     return theta[N - nfr:], Xo @ Q[:, N - nfr:], theta
 
 
-def density(ham, Xo, Xfr, f_fr):
-    """rho at the quadrature points of every cell (ncells x n_q), Alg. 3 formula."""
+def density(ham, Xo, Xfr, f_fr, cells=None):
+    """rho at the quadrature points of every cell (ncells x n_q), Alg. 3 formula; with
+    `cells`, only those cells (len(cells) x n_q)."""
     m = ham.mesh
     s = 1.0 / np.sqrt(m.mass)
-    out = np.empty((m.ncells, ham.nq))
+    cells = range(m.ncells) if cells is None else cells
+    out = np.empty((len(cells), ham.nq))
     w = np.asarray(f_fr, np.float64) - 1.0
-    for c in range(m.ncells):
+    for r, c in enumerate(cells):
         rows = m.cell_map[c]
         Po = ham.Nq @ (s[rows, None] * Xo[rows])           # psi^_o at the quadrature points
         Pf = ham.Nq @ (s[rows, None] * Xfr[rows])
-        out[c] = 2.0 * (np.sum(Po * Po, axis=1) + (Pf * Pf) @ w)
+        out[r] = 2.0 * (np.sum(Po * Po, axis=1) + (Pf * Pf) @ w)
     return out

@@ -72,6 +72,9 @@ _SIGS = {
     "dftfe_residuals": [_vp, _vp, _vp, _i64, _int, _vp, _vp, _int],
     "dftfe_chfsi_pass": [_vp, _vp, _i64, _int, _int, _int, C.POINTER(Bounds), _vp, _vp, _int],
     "dftfe_cholgs_noalloc": [_vp, _i64, _i64, _int, _vp],
+    "dftfe_rayleigh_ritz_split": [_vp, _vp, _i64, _int, _int, _vp, _vp, _i64, _int],
+    "dftfe_fermi_level": [_vp, _int, _int, _dbl, _dbl, _vp, C.POINTER(_dbl), _vp],
+    "dftfe_density": [_vp, _vp, _i64, _int, _vp, _i64, _int, _vp, _vp],
     "dftfe_profile_enable": [_vp, _int],
     "dftfe_profile_query": [_vp, C.c_char_p, C.POINTER(_dbl), C.POINTER(_i64)],
 }
@@ -242,6 +245,29 @@ def dftfe_chfsi_pass(ham, X, block, degree, bounds, evals, resid, prec=DFTFE_FP6
     _check(_lib.dftfe_chfsi_pass(ham, px, ld, X.shape[1], int(block), int(degree), C.byref(bounds),
                                  _vp(evals.data_ptr()), _vp(resid.data_ptr()), prec))
     return bounds
+
+
+def dftfe_rayleigh_ritz_split(ham, X, nfr, evals, Xfr, prec=DFTFE_FP64):
+    px, ld = _dev(X, "X")
+    pf, ldf = _dev(Xfr, "Xfr")
+    _check(_lib.dftfe_rayleigh_ritz_split(ham, px, ld, X.shape[1], int(nfr), _vp(evals.data_ptr()), pf, ldf, prec))
+
+
+def dftfe_fermi_level(evals_fr, n_oc, n_elec, kT, f_fr, stream=None):
+    mu = _dbl()
+    _check(_lib.dftfe_fermi_level(_vp(evals_fr.data_ptr()), evals_fr.numel(), int(n_oc), float(n_elec), float(kT),
+                                  _vp(f_fr.data_ptr()), C.byref(mu), _stream(stream)))
+    return mu.value
+
+
+def dftfe_density(ham, Xo, Xfr, f_fr, rho):
+    po, ldo = _dev(Xo, "Xo")
+    if Xfr is None:
+        pf, ldf, nfr, pff = None, 0, 0, None
+    else:
+        pf, ldf = _dev(Xfr, "Xfr")
+        nfr, pff = Xfr.shape[1], _vp(f_fr.data_ptr())
+    _check(_lib.dftfe_density(ham, po, ldo, Xo.shape[1], pf, ldf, nfr, pff, _vp(rho.data_ptr())))
 
 
 def dftfe_cholgs_noalloc(X, stream=None):

@@ -117,6 +117,7 @@ struct dftfe_ham_s {
   double* d_P = nullptr;           // Msym x nq packed basis products (Eq. gemmLoc)
   int32_t* d_pairs = nullptr;      // Msym x 2 (j <= k)
   double* d_wq = nullptr;          // nq quadrature weights * detJ
+  double* d_Nq = nullptr;          // nq x nc basis values at the quadrature points
   double* d_Hc = nullptr;          // Nc x nc x nc FP64
   bool has_potential = false;
   int64_t potential_version = 0;   // bumped by every set_potential

@@ -392,6 +392,15 @@ extern "C" dftfe_status dftfe_ham_create(dftfe_mesh m, void* stream, dftfe_ham* 
         wq[q] = m->quad.w[qa] * m->quad.w[qb] * m->quad.w[qc] * m->detJ;
       }
       h->d_wq = dev_upload(wq, s);
+      std::vector<double> Nq((size_t)m->nq * nc);
+      for (int q = 0; q < m->nq; ++q) {
+        const int qa = q % m->nq1, qb = (q / m->nq1) % m->nq1, qc = q / (m->nq1 * m->nq1);
+        for (int j = 0; j < nc; ++j) {
+          const int a = j % n1, b = (j / n1) % n1, c = j / (n1 * n1);
+          Nq[(size_t)q * nc + j] = m->Lq[qa * n1 + a] * m->Lq[qb * n1 + b] * m->Lq[qc * n1 + c];
+        }
+      }
+      h->d_Nq = dev_upload(Nq, s);
       double* d_Lq = dev_upload(m->Lq, s);
       DFTFE_CHECK_CUDA(cudaMalloc(&h->d_P, sizeof(double) * Msym * m->nq));
       DFTFE_LAUNCH(k_products, nblk(Msym * m->nq), 256, 0, s, h->d_P, h->d_pairs, d_Lq, Msym,
@@ -494,7 +503,7 @@ extern "C" dftfe_status dftfe_ham_destroy(dftfe_ham h) {
   free_nonlocal(h);
   cudaFree(h->d_map); cudaFree(h->d_mass); cudaFree(h->d_minvsqrt);
   cudaFree(h->d_colour_cells); cudaFree(h->d_K); cudaFree(h->d_P); cudaFree(h->d_pairs);
-  cudaFree(h->d_wq); cudaFree(h->d_Hc);
+  cudaFree(h->d_wq); cudaFree(h->d_Hc); cudaFree(h->d_Nq);
   for (auto& kv : h->ws) kv.second.release();
   for (auto& kv : h->timers)
     for (auto& ev : kv.second.events) {
