@@ -11,12 +11,16 @@
 // copies (cp.async.bulk) into shared memory.  The cell's columns of X are gathered by four
 // producer warps, split, and written transposed (K-major) into the B tiles.
 //
-// One CTA per SM walks the cells of one colour (no two share a node).  Warp roles:
+// One CTA per SM walks the cells (all of them, in one launch per 128-column tile) and
+// writes each product Y^c with plain stores to a per-cell buffer; a separate assembly
+// kernel sums every node's cell contributions in fixed order, fused with the recurrence
+// terms, so the tensor-core kernel never waits on a read-modify-write.  Warp roles:
 //   warp 0      A producer (bulk copies of the split cell-matrix tiles, 4-stage ring)
 //   warp 1      TMEM owner and MMA issuer (one elected lane)
-//   warps 2-5   B producers (gather + split of X^c, 2-stage ring, loads one chunk ahead)
-//   warps 6-9   epilogue (tcgen05.ld of the accumulators, scatter-add alpha*Y into Z)
-//   warp 10     L2 prefetch of the next cell's X and Z rows
+//   warps 2-5   B producers (coalesced gather + split of X^c, 2-stage ring, loads one
+//               chunk ahead)
+//   warps 6-9   epilogue (tcgen05.ld of the accumulators, stores of the rows of Y^c)
+//   warp 10     L2 prefetch of the next cell's X rows
 // Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its
 // own copies and MMAs (bounded), frees its tensor memory and returns.
 #include "internal.h"
@@ -37,6 +41,8 @@ constexpr int kTile = 16384;                       // one 128-row x 128-byte ope
 constexpr int kStageBytes = 2 * kTile;             // hi + lo
 constexpr int kMaxMTiles = 4;                      // 4 x 128 accumulator columns = 512 TMEM columns
 constexpr long kSpinLimit = 40000000L;
+constexpr int kPatchLd = 36;                       // epilogue patch row stride (floats)
+constexpr int kPatchBytes = 4 * 32 * kPatchLd * 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -61,7 +67,7 @@ __host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int M, int N) {
 struct Shared {
   uint64_t a_full[kStagesA], a_empty[kStagesA];
   uint64_t b_full[kStagesB], b_empty[kStagesB];
-  uint64_t acc_full, acc_empty, drain;
+  uint64_t acc_full, acc_empty[kMaxMTiles], drain;   // acc_empty per 128-column accumulator
   uint32_t tmem;
   int abort;
   int mma_cell;                                     // cell the MMA lane is working on
@@ -144,23 +150,6 @@ template <> struct Split<false> {
   }
 };
 
-// 4x4 transpose inside each lane quad: lane r of the quad holds row r (4 columns) on
-// entry and column r (4 rows) on exit.
-__device__ __forceinline__ void quad_transpose(const float4 a4, int r, float* t) {
-  const float a[4] = {a4.x, a4.y, a4.z, a4.w};
-  t[0] = t[1] = t[2] = t[3] = 0.0f;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    const int idx = r ^ s;
-    const float send = idx == 0 ? a[0] : idx == 1 ? a[1] : idx == 2 ? a[2] : a[3];
-    const float got = __shfl_xor_sync(0xffffffffu, send, s);
-    t[0] = idx == 0 ? got : t[0];
-    t[1] = idx == 1 ? got : t[1];
-    t[2] = idx == 2 ? got : t[2];
-    t[3] = idx == 3 ? got : t[3];
-  }
-}
-
 }  // namespace mx
 
 // Set-up: split the FP64 cell matrices into the tile order the kernel streams:
@@ -202,16 +191,18 @@ __global__ void k_split_cells(const double* __restrict__ Hc, uint8_t* __restrict
 
 template <bool TF32>
 __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
-    const uint8_t* __restrict__ A, const int32_t* __restrict__ map, const int32_t* __restrict__ cells,
-    int ncells, int nc, int nkc, int nmt, const float* __restrict__ X, int64_t ldx,
-    float* __restrict__ Z, int64_t ldz, int col0, int ncol, float alpha, int* err) {
+    const uint8_t* __restrict__ A, const int32_t* __restrict__ map, int ncells, int nc, int nkc, int nmt, const float* __restrict__ X, int64_t ldx,
+    float* __restrict__ Yc, int col0, int ncol, int* err) {
   using namespace mx;
   constexpr int ES = TF32 ? 4 : 2, KC = 128 / ES, G = Split<TF32>::G;
+  // cell of the i-th work item of this CTA (cells dealt round-robin over the grid)
+  auto cell_of = [&](int64_t i) -> int64_t { return blockIdx.x + i * gridDim.x; };
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;                                    // kStagesA x (hi 16K | lo 16K)
   uint8_t* sB = base + kStagesA * kStageBytes;           // kStagesB x (hi 16K | lo 16K)
-  Shared* sh = (Shared*)(sB + kStagesB * kStageBytes);
+  uint8_t* sP = sB + kStagesB * kStageBytes;            // 4 epilogue patches of 32 x kPatchLd floats
+  Shared* sh = (Shared*)(sP + kPatchBytes);
   volatile int* abort = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -219,7 +210,7 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     for (int s = 0; s < kStagesA; ++s) { mbar_init(&sh->a_full[s], 1); mbar_init(&sh->a_empty[s], 1); }
     for (int s = 0; s < kStagesB; ++s) { mbar_init(&sh->b_full[s], 128); mbar_init(&sh->b_empty[s], 1); }
     mbar_init(&sh->acc_full, 1);
-    mbar_init(&sh->acc_empty, 128);
+    for (int t = 0; t < kMaxMTiles; ++t) mbar_init(&sh->acc_empty[t], 128);
     mbar_init(&sh->drain, 1);
     sh->abort = 0;
     sh->mma_cell = -1;
@@ -241,7 +232,7 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     if (lane == 0) {
       uint32_t ta = 0;
       for (int i = 0; i < my_cells && !*abort; ++i) {
-        const int64_t cell = cells[blockIdx.x + (int64_t)i * gridDim.x];
+        const int64_t cell = cell_of(i);
         for (int kc = 0; kc < nkc && !*abort; ++kc)
           for (int mt = 0; mt < nmt; ++mt, ++ta) {
             const int s = ta % kStagesA;
@@ -264,8 +255,6 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     if (lane == 0) {
       uint32_t ta = 0, tb = 0;
       for (int i = 0; i < my_cells && !*abort; ++i) {
-        if (!mbar_wait(&sh->acc_empty, (i & 1) ^ 1, abort, err)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         *(volatile int*)&sh->mma_cell = i;
         for (int kc = 0; kc < nkc && !*abort; ++kc, ++tb) {
           const int sb = tb % kStagesB;
@@ -273,6 +262,9 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
           const uint32_t bhi = smem_u32(sB + sb * kStageBytes), blo = bhi + kTile;
           for (int mt = 0; mt < nmt; ++mt, ++ta) {
             const int sa = ta % kStagesA;
+            // the first product into accumulator mt waits until the epilogue has read
+            // that accumulator of the previous cell (it drains them in the same order)
+            if (kc == 0 && !mbar_wait(&sh->acc_empty[mt], (i & 1) ^ 1, abort, err)) break;
             if (!mbar_wait(&sh->a_full[sa], (ta / kStagesA) & 1, abort, err)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t ahi = smem_u32(sA + sa * kStageBytes), alo = ahi + kTile;
@@ -297,27 +289,25 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     }
   } else if (warp >= 2 && warp < 6) {
     // ------------------------------------------------------------ B producers
-    // warp w covers tile rows (columns of X) 32w..32w+31; lane l loads a float4 of row
-    // 4q + (l & 3) at columns 32w + 4(l >> 2) .. +3, then a 4x4 transpose inside each
-    // lane quad leaves lane l with 4 consecutive k of column n = 32w + l.
+    // warp w covers tile rows (columns of X) n = 32w + lane: for every row k of the chunk
+    // the warp reads 32 consecutive floats of X row map[k] (one 128-byte line), so lane
+    // l holds column n for all k of the chunk without any exchange between lanes.
     const int w = warp - 2;
     const int n = 32 * w + lane;
-    const int rr = lane & 3;
-    const int colq = col0 + 32 * w + 4 * (lane >> 2);
+    const int col = col0 + n;
     constexpr int QN = KC / 4;                   // row quads per K-chunk
-    // loads of chunk tb+1 are issued before chunk tb is transposed and stored
+    // loads of chunk tb+1 are issued before chunk tb is split and stored
     const uint32_t nchunks = (uint32_t)my_cells * (uint32_t)nkc;
-    float4 v[QN], vn[QN];
-    auto load_chunk = [&](uint32_t t, float4* dst) {
-      const int64_t cell = cells[blockIdx.x + (int64_t)(t / nkc) * gridDim.x];
+    float v[KC], vn[KC];
+    auto load_chunk = [&](uint32_t t, float* dst) {
+      const int64_t cell = cell_of(t / nkc);
       const int kc = (int)(t % nkc);
       const int32_t* cm = map + cell * nc;
 #pragma unroll
-      for (int q = 0; q < QN; ++q) {
-        const int k = kc * KC + 4 * q + rr;
-        dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < nc && colq < ncol)
-          dst[q] = __ldg(reinterpret_cast<const float4*>(X + (int64_t)cm[k] * ldx + colq));
+      for (int j = 0; j < KC; ++j) {
+        const int k = kc * KC + j;
+        dst[j] = 0.0f;
+        if (k < nc && col < ncol) dst[j] = __ldg(X + (int64_t)__ldg(cm + k) * ldx + col);
       }
     };
     if (nchunks > 0) load_chunk(0, v);
@@ -328,45 +318,27 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
         if (!mbar_wait(&sh->b_empty[sb], ((tb / kStagesB) & 1) ^ 1, abort, err)) break;
         uint8_t* bhi = sB + sb * kStageBytes;
         uint8_t* blo = bhi + kTile;
-        if (TF32) {
 #pragma unroll
-          for (int q = 0; q < QN; ++q) {
-            float t[4];
-            quad_transpose(v[q], rr, t);                // t[j] = row 4q + j of column n
-            uint4 hi, lo;
-            Split<TF32>::run(t, hi, lo);
-            const uint32_t off = sw128((uint32_t)n, (uint32_t)(q * 16));
-            *reinterpret_cast<uint4*>(bhi + off) = hi;
-            *reinterpret_cast<uint4*>(blo + off) = lo;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < QN; q += 2) {               // two row quads = one chunk of 8
-            float t[8];
-            quad_transpose(v[q], rr, t);
-            quad_transpose(v[q + 1], rr, t + 4);
-            uint4 hi, lo;
-            Split<TF32>::run(t, hi, lo);
-            const uint32_t off = sw128((uint32_t)n, (uint32_t)((q / 2) * 16));
-            *reinterpret_cast<uint4*>(bhi + off) = hi;
-            *reinterpret_cast<uint4*>(blo + off) = lo;
-          }
+        for (int q = 0; q < QN; q += G / 4) {     // one 16-byte chunk of the row per step
+          uint4 hi, lo;
+          Split<TF32>::run(v + 4 * q, hi, lo);
+          const uint32_t off = sw128((uint32_t)n, (uint32_t)((q / (G / 4)) * 16));
+          *reinterpret_cast<uint4*>(bhi + off) = hi;
+          *reinterpret_cast<uint4*>(blo + off) = lo;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&sh->b_full[sb]);
       }
 #pragma unroll
-      for (int q = 0; q < QN; ++q) v[q] = vn[q];
+      for (int j = 0; j < KC; ++j) v[j] = vn[j];
     }
   } else if (warp == kPrefetchWarp) {
     // ------------------------------------------------------------ L2 prefetch
     {
-      // pull the X rows (gathered by the B producers) and the Z rows (updated
-      // by the epilogue) of the next cell into L2 while the current cell is computed, so
-      // the gather and the read-modify-write do not wait on HBM latency.  The MMA lane
+      // pull the X rows gathered by the B producers for the next cell into L2 while the
+      // current cell is computed, so the gather does not wait on HBM latency.  The MMA lane
       // publishes the cell it is working on; prefetching runs one cell ahead of it.
       const uint32_t xbytes = 4u * (uint32_t)min(128, (int)(ldx - col0));
-      const uint32_t zbytes = 4u * (uint32_t)min(128, (int)(ldz - col0));
       long spins = 0;
       for (int next = 0; next < my_cells && !*abort;) {
         if (next > *(volatile int*)&sh->mma_cell + 1) {
@@ -374,26 +346,28 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
           __nanosleep(256);
           continue;
         }
-        const int64_t cell = cells[blockIdx.x + (int64_t)next * gridDim.x];
+        const int64_t cell = cell_of(next);
         const int32_t* cm = map + cell * nc;
         for (int k = lane; k < nc; k += 32) {
           const int64_t g = cm[k];
           asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(X + g * ldx + col0), "r"(xbytes) : "memory");
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(Z + g * ldz + col0), "r"(zbytes) : "memory");
         }
         ++next;
       }
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // each warp reads 32 accumulator rows x 32 columns at a time (lane = row), turns them
+    // around in its shared-memory patch (row stride 36 floats) and writes 4 rows x 128 B
+    // per store instruction; accumulator mt is released as soon as it has been read.
     const int q = warp & 3;                       // TMEM lane quadrant of this warp
+    float* patch = reinterpret_cast<float*>(sP) + q * (32 * kPatchLd);
     for (int i = 0; i < my_cells; ++i) {
       if (!mbar_wait(&sh->acc_full, i & 1, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t cell = cells[blockIdx.x + (int64_t)i * gridDim.x];
+      const int64_t cell = cell_of(i);
       for (int mt = 0; mt < nmt; ++mt) {
-        const int row = mt * 128 + q * 32 + lane;
-        const int64_t g = row < nc ? (int64_t)map[cell * nc + row] : -1;
+        const int row0 = mt * 128 + q * 32;       // first accumulator row of this warp
         for (int cb = 0; cb < 4; ++cb) {
           uint32_t r[32];
           const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128 + cb * 32);
@@ -405,28 +379,25 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
                          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                        : "r"(taddr));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (g >= 0) {
-            float* z = Z + g * ldz + col0 + cb * 32;
-            const int cbase = col0 + cb * 32;
-            if (cbase + 32 <= ncol) {
+          if (row0 >= nc) continue;               // whole patch is padding (warp-uniform)
 #pragma unroll
-              for (int j = 0; j < 32; j += 4) {
-                float4 o = *reinterpret_cast<float4*>(z + j);
-                o.x = fmaf(alpha, __uint_as_float(r[j]), o.x);
-                o.y = fmaf(alpha, __uint_as_float(r[j + 1]), o.y);
-                o.z = fmaf(alpha, __uint_as_float(r[j + 2]), o.z);
-                o.w = fmaf(alpha, __uint_as_float(r[j + 3]), o.w);
-                *reinterpret_cast<float4*>(z + j) = o;
-              }
-            } else {
-              for (int j = 0; j < 32; ++j)
-                if (cbase + j < ncol) z[j] = fmaf(alpha, __uint_as_float(r[j]), z[j]);
-            }
+          for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<uint4*>(patch + lane * kPatchLd + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int rl = it * 4 + (lane >> 3);  // patch row of this lane
+            const int row = row0 + rl;
+            const float4 val = *reinterpret_cast<const float4*>(patch + rl * kPatchLd + 4 * (lane & 7));
+            // row `row` of Y^c is slot cell * nc + row of the per-cell output (128 floats)
+            if (row < nc)
+              *reinterpret_cast<float4*>(Yc + (cell * nc + row) * (int64_t)128 + cb * 32 + 4 * (lane & 7)) = val;
           }
+          __syncwarp();
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&sh->acc_empty[mt]);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&sh->acc_empty);
     }
   }
   __syncwarp();
@@ -437,26 +408,6 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
 }
 
 // ------------------------------------------------------------ FP32 helpers
-// Z = s1 X + s2 Xp on FP32 blocks; grid.y = row blocks, threads over float4 column groups
-// (ld and the row starts are multiples of 4 floats).
-__global__ void k_axpby_init32(float* __restrict__ Z, int64_t ldz, const float* __restrict__ X, int64_t ldx,
-                               const float* __restrict__ Xp, int64_t ldp, int64_t M, int ncol, float s1, float s2) {
-  const int nq = (ncol + 3) / 4;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= M * nq) return;
-  const int64_t i = t / nq;
-  const int c = (int)(t - i * nq) * 4;
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (s1 != 0.0f) {
-    const float4 x = *reinterpret_cast<const float4*>(X + i * ldx + c);
-    v = make_float4(s1 * x.x, s1 * x.y, s1 * x.z, s1 * x.w);
-  }
-  if (Xp) {
-    const float4 p = *reinterpret_cast<const float4*>(Xp + i * ldp + c);
-    v = make_float4(fmaf(s2, p.x, v.x), fmaf(s2, p.y, v.y), fmaf(s2, p.z, v.z), fmaf(s2, p.w, v.w));
-  }
-  *reinterpret_cast<float4*>(Z + i * ldz + c) = v;
-}
 
 __global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy,
                          int64_t M, int ncol) {
@@ -560,7 +511,8 @@ __global__ void __launch_bounds__(256) k_nl_add32(float* __restrict__ Z, int64_t
 static unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 static size_t mixed_smem() {
-  return 1024 + (size_t)mx::kStagesA * mx::kStageBytes + (size_t)mx::kStagesB * mx::kStageBytes + sizeof(mx::Shared);
+  return 1024 + (size_t)mx::kStagesA * mx::kStageBytes + (size_t)mx::kStagesB * mx::kStageBytes + mx::kPatchBytes +
+         sizeof(mx::Shared);
 }
 
 // build (once per potential and precision) the split cell-matrix tiles
@@ -586,13 +538,94 @@ static uint8_t* mixed_tiles(dftfe_ham h, bool tf32, int* nkc_out, int* nmt_out) 
   return A;
 }
 
-// Z = alpha H~ X + s1 X + s2 Xp on FP32 blocks (ld multiple of 4), mixed cell products
+// Assembly of the per-cell products fused with the recurrence:
+//   Z[g] = s1 X[g] + s2 Xp[g] + alpha * sum_{slots (c, l) of node g} Y^c[l]
+// one warp per node, lane l owns columns col0 + 4l .. +3 (float4); the slots of a node are
+// summed in increasing cell order, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_assemble32(float* __restrict__ Z, int64_t ldz, const float* __restrict__ X,
+                                                    int64_t ldx, const float* __restrict__ Xp, int64_t ldp,
+                                                    const float* __restrict__ Yc, const int32_t* __restrict__ nptr,
+                                                    const int32_t* __restrict__ nslot, int64_t M, int col0, int ncol,
+                                                    float alpha, float s1, float s2) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int c = col0 + 4 * lane;
+  if (g >= M || c >= ncol) return;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int t = nptr[g]; t < nptr[g + 1]; ++t) {
+    const float4 y = __ldg(reinterpret_cast<const float4*>(Yc + (int64_t)nslot[t] * 128 + 4 * lane));
+    acc.x += y.x; acc.y += y.y; acc.z += y.z; acc.w += y.w;
+  }
+  const float4 x = *reinterpret_cast<const float4*>(X + g * ldx + c);     // in bounds: ld % 32 == 0
+  float4 o = make_float4(fmaf(alpha, acc.x, s1 * x.x), fmaf(alpha, acc.y, s1 * x.y),
+                         fmaf(alpha, acc.z, s1 * x.z), fmaf(alpha, acc.w, s1 * x.w));
+  if (Xp) {
+    const float4 p = *reinterpret_cast<const float4*>(Xp + g * ldp + c);
+    o.x = fmaf(s2, p.x, o.x); o.y = fmaf(s2, p.y, o.y); o.z = fmaf(s2, p.z, o.z); o.w = fmaf(s2, p.w, o.w);
+  }
+  float* z = Z + g * ldz + c;
+  if (c + 3 < ncol) {
+    *reinterpret_cast<float4*>(z) = o;
+  } else {
+    const float v[4] = {o.x, o.y, o.z, o.w};
+    for (int j = 0; c + j < ncol; ++j) z[j] = v[j];
+  }
+}
+
+// node -> (cell, local row) slots in CSR, cells in increasing order (built once per ham)
+static void node_slots(dftfe_ham h, const int32_t** ptr, const int32_t** slots) {
+  auto* m = h->mesh;
+  if (!h->d_node_ptr) {
+    // the cell map itself (cell c, local row l) -> node, read back once
+    const int nc = m->nc;
+    DFTFE_REQUIRE(m->Nc * (int64_t)nc < INT32_MAX, "too many cell rows for 32-bit slots");
+    std::vector<int32_t> map((size_t)m->Nc * nc);
+    DFTFE_CHECK_CUDA(cudaMemcpyAsync(map.data(), h->d_map, sizeof(int32_t) * map.size(), cudaMemcpyDeviceToHost,
+                                     h->stream));
+    DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+    std::vector<int32_t> cnt(m->M + 1, 0);
+    auto node_of = [&](int64_t c, int l) -> int64_t { return map[c * nc + l]; };
+    for (int64_t c = 0; c < m->Nc; ++c)
+      for (int l = 0; l < nc; ++l) cnt[node_of(c, l) + 1]++;
+    for (int64_t g = 0; g < m->M; ++g) cnt[g + 1] += cnt[g];
+    std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1), sl((size_t)m->Nc * nc);
+    for (int64_t c = 0; c < m->Nc; ++c)
+      for (int l = 0; l < nc; ++l) sl[fill[node_of(c, l)]++] = (int32_t)(c * nc + l);
+    DFTFE_CHECK_CUDA(cudaMalloc(&h->d_node_ptr, sizeof(int32_t) * cnt.size()));
+    DFTFE_CHECK_CUDA(cudaMalloc(&h->d_node_slot, sizeof(int32_t) * sl.size()));
+    DFTFE_CHECK_CUDA(cudaMemcpy(h->d_node_ptr, cnt.data(), sizeof(int32_t) * cnt.size(), cudaMemcpyHostToDevice));
+    DFTFE_CHECK_CUDA(cudaMemcpy(h->d_node_slot, sl.data(), sizeof(int32_t) * sl.size(), cudaMemcpyHostToDevice));
+  }
+  *ptr = h->d_node_ptr;
+  *slots = h->d_node_slot;
+}
+
+// Z = alpha H~ X + s1 X + s2 Xp on FP32 blocks (ld multiple of 32), mixed cell products:
+// per 128-column tile, one launch of the cell kernel over all cells (per-cell outputs,
+// plain stores) and one assembly launch; then the nonlocal part.
 static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc, int nmt, const float* X, int64_t ldx,
                               const float* Xp, int64_t ldp, float* Z, int64_t ldz, int ncol, float alpha, float s1,
                               float s2, int* err) {
   auto* m = h->mesh;
-  DFTFE_LAUNCH(k_axpby_init32, nblk(m->M * ((ncol + 3) / 4)), 256, 0, h->stream, Z, ldz, X, ldx, Xp, ldp, m->M, ncol,
-               s1, s2);
+  const int32_t *nptr, *nslot;
+  node_slots(h, &nptr, &nslot);
+  float* Yc = (float*)ws_get(h, "mx_yc", sizeof(float) * (size_t)m->Nc * m->nc * 128);
+  const size_t sh = mixed_smem();
+  const unsigned grid = (unsigned)std::min<int64_t>(m->Nc, h->sm_count);
+  for (int col0 = 0; col0 < ncol; col0 += 128) {
+    {
+      ProfScope ps(h, tf32 ? "cell_gemm_tf32x3" : "cell_gemm_bf16x3");
+      if (tf32)
+        DFTFE_LAUNCH(k_cell_mixed<true>, grid, mx::kThreads, sh, h->stream, A, h->d_map, (int)m->Nc, m->nc,
+                     nkc, nmt, X, ldx, Yc, col0, ncol, err);
+      else
+        DFTFE_LAUNCH(k_cell_mixed<false>, grid, mx::kThreads, sh, h->stream, A, h->d_map, (int)m->Nc, m->nc,
+                     nkc, nmt, X, ldx, Yc, col0, ncol, err);
+    }
+    ProfScope ps(h, "assemble32");
+    DFTFE_LAUNCH(k_assemble32, nblk((m->M + 7) / 8 * 256), 256, 0, h->stream, Z, ldz, X, ldx, Xp, ldp, Yc, nptr, nslot,
+                 m->M, col0, ncol, alpha, s1, s2);
+  }
   if (h->nproj > 0) {
     float* P = (float*)ws_get(h, "nl_coef32", sizeof(float) * h->nproj * (size_t)ncol);
     float* Pp = (float*)ws_get(h, "nl_coef32_part", sizeof(float) * h->nproj * (size_t)kNlSplits * ncol);
@@ -603,22 +636,6 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
     dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 127) / 128));
     DFTFE_LAUNCH(k_nl_add32, g2, 256, 0, h->stream, Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj, h->d_sval, P,
                  h->nsup, alpha);
-  }
-  const size_t sh = mixed_smem();
-  for (int c = 0; c < h->ncolours; ++c) {
-    const int64_t n = h->colour_off[c + 1] - h->colour_off[c];
-    if (n == 0) continue;
-    const int32_t* cells = h->d_colour_cells + h->colour_off[c];
-    const unsigned grid = (unsigned)std::min<int64_t>(n, h->sm_count);
-    for (int col0 = 0; col0 < ncol; col0 += 128) {
-      ProfScope ps(h, tf32 ? "cell_gemm_tf32x3" : "cell_gemm_bf16x3");
-      if (tf32)
-        DFTFE_LAUNCH(k_cell_mixed<true>, grid, mx::kThreads, sh, h->stream, A, h->d_map, cells, (int)n, m->nc, nkc,
-                     nmt, X, ldx, Z, ldz, col0, ncol, alpha, err);
-      else
-        DFTFE_LAUNCH(k_cell_mixed<false>, grid, mx::kThreads, sh, h->stream, A, h->d_map, cells, (int)n, m->nc, nkc,
-                     nmt, X, ldx, Z, ldz, col0, ncol, alpha, err);
-    }
   }
 }
 

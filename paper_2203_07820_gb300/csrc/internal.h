@@ -112,6 +112,8 @@ struct dftfe_ham_s {
   int ncolours = 0;
   std::vector<int64_t> colour_off; // ncolours + 1
   int32_t* d_colour_cells = nullptr;
+  int32_t* d_node_ptr = nullptr;   // node -> (cell, local row) slots, CSR (built on first mixed use)
+  int32_t* d_node_slot = nullptr;
   // a2: cell matrices
   double* d_K = nullptr;           // nc x nc shared stiffness
   double* d_P = nullptr;           // Msym x nq packed basis products (Eq. gemmLoc)

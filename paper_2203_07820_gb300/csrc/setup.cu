@@ -502,7 +502,7 @@ extern "C" dftfe_status dftfe_ham_destroy(dftfe_ham h) {
   if (h->stream || true) cudaStreamSynchronize(h->stream);
   free_nonlocal(h);
   cudaFree(h->d_map); cudaFree(h->d_mass); cudaFree(h->d_minvsqrt);
-  cudaFree(h->d_colour_cells); cudaFree(h->d_K); cudaFree(h->d_P); cudaFree(h->d_pairs);
+  cudaFree(h->d_colour_cells); cudaFree(h->d_node_ptr); cudaFree(h->d_node_slot); cudaFree(h->d_K); cudaFree(h->d_P); cudaFree(h->d_pairs);
   cudaFree(h->d_wq); cudaFree(h->d_Hc); cudaFree(h->d_Nq);
   for (auto& kv : h->ws) kv.second.release();
   for (auto& kv : h->timers)
