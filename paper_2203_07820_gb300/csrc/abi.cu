@@ -58,6 +58,7 @@ static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals,
   syevd(h, Hh, N, evals, Q, st);
   const int s = read_status(h, st);
   if (s == DFTFE_ERR_NOCONV) throw Error(DFTFE_ERR_NOCONV, "subspace eigensolver did not converge");
+  if (s != 0) throw Error((dftfe_status)s, "subspace eigensolver: a bounded grid wait timed out");
   if (mixed) {
     rotate_inplace_mixed(h, X, ld, m->M, N, Q, false);
     rotate_inplace_mixed(h, W, ldw, m->M, N, Q, false);

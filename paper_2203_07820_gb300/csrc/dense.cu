@@ -268,100 +268,223 @@ void rotate_inplace(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const 
 }
 
 // -------------------------------------------------------------- eigensolver
-// Householder step k on the symmetric A (N x N, full storage): x = A[k][k+1..N-1],
-// H_k = I - tau v v^T with v_0 = 1 maps x to beta e_1 (LAPACK dlarfg convention).
-// Each CTA rebuilds v in shared memory and computes p = tau A22 v for its rows.
-__global__ void __launch_bounds__(256) k_hh_matvec(const double* __restrict__ A, int N, int k,
-                                                   double* __restrict__ V, double* __restrict__ tau,
-                                                   double* __restrict__ d, double* __restrict__ e,
-                                                   double* __restrict__ p) {
-  extern __shared__ double sv[];  // n
-  __shared__ double red[9];
-  const int n = N - k - 1;
-  const double* xr = A + (int64_t)k * N + k + 1;
-  double part = 0.0;
-  for (int i = 1 + threadIdx.x; i < n; i += 256) part += xr[i] * xr[i];
-  const double xn2 = block_sum<256>(part, red);
-  const double x0 = xr[0];
-  double beta, t, scal;
-  if (xn2 == 0.0) {
-    beta = x0; t = 0.0; scal = 0.0;
-  } else {
-    beta = -copysign(sqrt(x0 * x0 + xn2), x0);
-    t = (beta - x0) / beta;
-    scal = 1.0 / (x0 - beta);
-  }
-  for (int i = threadIdx.x; i < n; i += 256) sv[i] = (i == 0) ? 1.0 : xr[i] * scal;
+// Dense symmetric eigensolver: cyclic two-sided Jacobi with the round-robin (circle)
+// pairing, so each round rotates N/2 disjoint planes at once (Golub & Van Loan, parallel
+// Jacobi).  One cooperative launch runs all sweeps; the CTAs meet at a bounded grid
+// barrier after every round.  Every CTA computes all N/2 rotations of a round from the
+// same matrix entries, so all agree on them and on convergence without exchanging them.
+namespace jac {
+
+constexpr long kBarrierSpins = 20000000L;   // x 64 ns sleep: about a second
+
+struct Barrier {
+  unsigned int count;
+  unsigned int gen;
+  int abort;
+  unsigned int reads;   // CTAs that have read the rotation inputs, summed over rounds
+};
+
+// split barrier: the rotation inputs of a round (A_pp, A_qq, A_pq of every pair) may be
+// overwritten only once every CTA has read them
+__device__ void arrive_read(Barrier* b) {
   __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&b->reads, 1u);
+  }
+}
+
+__device__ bool wait_reads(Barrier* b, unsigned int target, int* status) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vr = &b->reads;
+    volatile int* vabort = &b->abort;
+    long it = 0;
+    while (*vr < target) {
+      if (*vabort || ++it > kBarrierSpins) {
+        ok = 0;
+        atomicExch(&b->abort, 1);
+        atomicCAS(status, 0, (int)DFTFE_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// grid-wide barrier (all CTAs are co-resident under the cooperative launch); false when
+// a wait ran out or another CTA gave up
+__device__ bool grid_barrier(Barrier* b, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int* vgen = &b->gen;
+    volatile int* vabort = &b->abort;
+    const unsigned int g = *vgen;
+    __threadfence();
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      long it = 0;
+      while (*vgen == g) {
+        if (*vabort || ++it > kBarrierSpins) {
+          ok = 0;
+          atomicExch(&b->abort, 1);
+          atomicCAS(status, 0, (int)DFTFE_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// players a, b of pair P in round k of the circle method on Ne (even) indices
+__device__ __forceinline__ void pairing(int k, int P, int Ne, int& p, int& q) {
+  const int m = Ne - 1;
+  int a, b;
+  if (P == 0) {
+    a = 0;
+    b = 1 + k % m;
+  } else {
+    a = 1 + (k + P) % m;
+    b = 1 + (k - P + m) % m;
+  }
+  p = min(a, b);
+  q = max(a, b);
+}
+
+}  // namespace jac
+
+// A (N x N symmetric, only the lower triangle is read) -> VT (rows = eigenvectors) and
+// d (eigenvalues, unsorted).  Dynamic shared memory: 3 doubles + 2 ints per pair.
+__global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A, double* __restrict__ VT, double* __restrict__ d,
+                                                int N, int max_sweeps, const double* __restrict__ anorm_p,
+                                                jac::Barrier* bar, int* status) {
+  extern __shared__ double jsm[];
+  const int Ne = N + (N & 1), NP = Ne / 2, m = Ne - 1;
+  double* cs = jsm;
+  double* sn = cs + NP;
+  double* tn = sn + NP;
+  int* pp = reinterpret_cast<int*>(tn + NP);
+  int* qq = pp + NP;
+  __shared__ int rotated;
+  const double anorm = *anorm_p;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  // full symmetric copy from the lower triangle, VT = I
+  for (int64_t w = gtid; w < (int64_t)N * N; w += gthreads) {
+    const int i = (int)(w / N), j = (int)(w % N);
+    if (i < j) A[w] = A[(int64_t)j * N + i];
+    VT[w] = i == j ? 1.0 : 0.0;
+  }
+  if (!jac::grid_barrier(bar, status)) return;
+  bool converged = false;
+  unsigned int round = 0;
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+      // the N/2 rotations of this round (Golub & Van Loan's symmetric 2x2 Schur form)
+      for (int P = threadIdx.x; P < NP; P += blockDim.x) {
+        int p, q;
+        jac::pairing(k, P, Ne, p, q);
+        double c = 1.0, s = 0.0, t = 0.0;
+        if (q < N) {
+          const double apq = A[(int64_t)p * N + q];
+          const double app = A[(int64_t)p * N + p], aqq = A[(int64_t)q * N + q];
+          const double small = fmax(1e-15 * sqrt(fabs(app) * fabs(aqq)), 1e-18 * anorm);
+          if (fabs(apq) > small) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+            c = 1.0 / sqrt(fma(t, t, 1.0));
+            s = t * c;
+            rotated = 1;
+          }
+        }
+        cs[P] = c;
+        sn[P] = s;
+        tn[P] = t;
+        pp[P] = p;
+        qq[P] = q;
+      }
+      jac::arrive_read(bar);   // ends with the CTA's rotations in shared memory
+      ++round;
+      // A <- J^T A J, one 2 x 2 block (row pair P, column pair R) per work item; the
+      // diagonal blocks (which hold the rotation inputs) come last
+      for (int64_t w = gtid; w < (int64_t)NP * NP; w += gthreads) {
+        const int P = (int)(w / NP), R = (int)(w % NP);
+        const double c = cs[P], s = sn[P], c2 = cs[R], s2 = sn[R];
+        if ((s == 0.0 && s2 == 0.0) || P == R) continue;
+        const int p = pp[P], q = qq[P], p2 = pp[R], q2 = qq[R];
+        // with N odd one pair per round holds the absent index N: that row / column is
+        // left out (its entries count as zero), the rest of the block is rotated as usual
+        const bool hq = q < N, hq2 = q2 < N;
+        double* rp = A + (int64_t)p * N;
+        double* rq = A + (int64_t)(hq ? q : p) * N;
+        const double x00 = rp[p2], x01 = hq2 ? rp[q2] : 0.0;
+        const double x10 = hq ? rq[p2] : 0.0, x11 = hq && hq2 ? rq[q2] : 0.0;
+        const double t00 = c * x00 - s * x10, t01 = c * x01 - s * x11;
+        const double t10 = s * x00 + c * x10, t11 = s * x01 + c * x11;
+        rp[p2] = t00 * c2 - t01 * s2;
+        if (hq2) rp[q2] = t00 * s2 + t01 * c2;
+        if (hq) rq[p2] = t10 * c2 - t11 * s2;
+        if (hq && hq2) rq[q2] = t10 * s2 + t11 * c2;
+      }
+      if (!jac::wait_reads(bar, round * gridDim.x, status)) return;
+      for (int64_t P = gtid; P < NP; P += gthreads) {
+        if (sn[P] == 0.0) continue;
+        double* rp = A + (int64_t)pp[P] * N;
+        double* rq = A + (int64_t)qq[P] * N;
+        const int p = pp[P], q = qq[P];
+        const double apq = rp[q], t = tn[P];
+        rp[p] -= t * apq;
+        rq[q] += t * apq;
+        rp[q] = 0.0;
+        rq[p] = 0.0;
+      }
+      // V <- V J on the rows of VT
+      for (int64_t w = gtid; w < (int64_t)NP * N; w += gthreads) {
+        const int P = (int)(w / N), i = (int)(w % N);
+        const double s = sn[P];
+        if (s == 0.0 || qq[P] >= N) continue;
+        const double c = cs[P];
+        double* vp = VT + (int64_t)pp[P] * N + i;
+        double* vq = VT + (int64_t)qq[P] * N + i;
+        const double a = *vp, b = *vq;
+        *vp = c * a - s * b;
+        *vq = s * a + c * b;
+      }
+      if (!jac::grid_barrier(bar, status)) return;
+    }
+    converged = rotated == 0;   // same in every CTA
+    __syncthreads();            // everyone has read the flag before it is reset
+  }
   if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < n; i += 256) V[(int64_t)k * N + i] = sv[i];
-    if (threadIdx.x == 0) {
-      tau[k] = t;
-      d[k] = A[(int64_t)k * N + k];
-      e[k] = beta;
-    }
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = blockIdx.x * 8 + warp; i < n; i += gridDim.x * 8) {
-    const double* row = A + (int64_t)(k + 1 + i) * N + k + 1;
-    double s = 0.0;
-    for (int j = lane; j < n; j += 32) s = fma(row[j], sv[j], s);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-    if (lane == 0) p[i] = t * s;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) d[i] = A[(int64_t)i * N + i];
+    if (threadIdx.x == 0 && !converged) atomicCAS(status, 0, (int)DFTFE_ERR_NOCONV);
   }
 }
 
-// A22 -= v w^T + w v^T with w = p - (tau/2)(p.v) v.
-__global__ void __launch_bounds__(256) k_hh_update(double* __restrict__ A, int N, int k,
-                                                   const double* __restrict__ V,
-                                                   const double* __restrict__ tau,
-                                                   const double* __restrict__ p) {
+__global__ void k_fro_norm(const double* __restrict__ A, int N, double* out) {
   __shared__ double red[9];
-  const int n = N - k - 1;
-  const double* v = V + (int64_t)k * N;
-  double part = 0.0;
-  for (int i = threadIdx.x; i < n; i += 256) part += p[i] * v[i];
-  const double pv = block_sum<256>(part, red);
-  const double a2 = -0.5 * tau[k] * pv;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const double vi = v[i], wi = p[i] + a2 * vi;
-    double* row = A + (int64_t)(k + 1 + i) * N + k + 1;
-    for (int j = threadIdx.x; j < n; j += 256) {
-      const double wj = p[j] + a2 * v[j];
-      row[j] -= vi * wj + wi * v[j];
-    }
+  double s = 0.0;
+  for (int64_t w = threadIdx.x; w < (int64_t)N * N; w += blockDim.x) {
+    const int i = (int)(w / N), j = (int)(w % N);
+    if (i >= j) s = fma(i > j ? 2.0 * A[w] : A[w], A[w], s);   // lower triangle, off-diagonal twice
   }
-}
-
-__global__ void k_hh_tail(const double* A, int N, double* d, double* e) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (N >= 2) {
-    d[N - 2] = A[(int64_t)(N - 2) * N + N - 2];
-    e[N - 2] = A[(int64_t)(N - 1) * N + N - 2];
-  }
-  d[N - 1] = A[(int64_t)(N - 1) * N + N - 1];
-  e[N - 1] = 0.0;
-}
-
-__global__ void k_identity(double* Q, int N) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t < (int64_t)N * N) Q[t] = (t / N == t % N) ? 1.0 : 0.0;
-}
-
-// Q <- H_k Q on rows/cols k+1..N-1; thread = column (owns it entirely).
-__global__ void k_formq(double* __restrict__ Q, int N, int k, const double* __restrict__ V,
-                        const double* __restrict__ tau) {
-  const int n = N - k - 1;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const double* v = V + (int64_t)k * N;
-  const double t = tau[k];
-  double* col = Q + (int64_t)(k + 1) * N + k + 1 + j;
-  double w = 0.0;
-  for (int i = 0; i < n; ++i) w = fma(v[i], col[(int64_t)i * N], w);
-  w *= t;
-  for (int i = 0; i < n; ++i) col[(int64_t)i * N] -= v[i] * w;
+  s = block_sum<256>(s, red);
+  if (threadIdx.x == 0) *out = sqrt(s);
 }
 
 // Implicit QL with Wilkinson shifts on (d, e); rotations are replayed on the rows of Z
@@ -497,6 +620,7 @@ __global__ void k_rank(const double* d, int N, int* perm, double* evals) {
   evals[r] = di;
 }
 
+// Z holds the eigenvectors as rows (Z[src * N + r] = component r of vector src)
 __global__ void __launch_bounds__(256) k_sign_copy(const double* __restrict__ Z, const int* perm, int N,
                                                    double* __restrict__ Q) {
   __shared__ double bv[256];
@@ -506,7 +630,7 @@ __global__ void __launch_bounds__(256) k_sign_copy(const double* __restrict__ Z,
   double best = -1.0;
   int bidx = N;
   for (int r = threadIdx.x; r < N; r += 256) {
-    const double a = fabs(Z[(int64_t)r * N + src]);
+    const double a = fabs(Z[(int64_t)src * N + r]);
     if (a > best || (a == best && r < bidx)) { best = a; bidx = r; }
   }
   bv[threadIdx.x] = best;
@@ -523,33 +647,42 @@ __global__ void __launch_bounds__(256) k_sign_copy(const double* __restrict__ Z,
     }
     __syncthreads();
   }
-  const double sgn = Z[(int64_t)bi[0] * N + src] < 0.0 ? -1.0 : 1.0;
-  for (int r = threadIdx.x; r < N; r += 256) Q[(int64_t)r * N + c] = sgn * Z[(int64_t)r * N + src];
+  const double sgn = Z[(int64_t)src * N + bi[0]] < 0.0 ? -1.0 : 1.0;
+  for (int r = threadIdx.x; r < N; r += 256) Q[(int64_t)r * N + c] = sgn * Z[(int64_t)src * N + r];
 }
 
 void syevd(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_status) {
   cudaStream_t s = h->stream;
   ProfScope ps(h, "syevd");
-  double* V = (double*)ws_get(h, "eig_V", sizeof(double) * (size_t)N * N);
-  double* Z = (double*)ws_get(h, "eig_Z", sizeof(double) * (size_t)N * N);
-  double* vec = (double*)ws_get(h, "eig_vec", sizeof(double) * 4 * (size_t)N + 64);
-  double* tau = vec, *d = vec + N, *e = vec + 2 * N, *p = vec + 3 * N;
+  const int NP = (N + (N & 1)) / 2;
+  double* VT = (double*)ws_get(h, "eig_V", sizeof(double) * (size_t)N * N);
+  double* vec = (double*)ws_get(h, "eig_vec", sizeof(double) * (size_t)N + 64);
+  double* d = vec;
+  double* anorm = vec + N;
+  jac::Barrier* bar = (jac::Barrier*)ws_get(h, "eig_bar", sizeof(jac::Barrier));
   int* perm = (int*)ws_get(h, "eig_perm", sizeof(int) * (size_t)N);
-  const int grid = std::max(1, std::min(h->sm_count * 2, (N + 7) / 8));
-  for (int k = 0; k + 2 < N; ++k) {
-    const int n = N - k - 1;
-    DFTFE_LAUNCH(k_hh_matvec, grid, 256, sizeof(double) * n, s, A, N, k, V, tau, d, e, p);
-    DFTFE_LAUNCH(k_hh_update, std::min(n, h->sm_count * 4), 256, 0, s, A, N, k, V, tau, p);
+  const size_t sh = (size_t)NP * (3 * sizeof(double) + 2 * sizeof(int));
+  static bool attr = false;
+  if (!attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024));
+    attr = true;
   }
-  DFTFE_LAUNCH(k_hh_tail, 1, 32, 0, s, A, N, d, e);
-  DFTFE_LAUNCH(k_identity, nblk((int64_t)N * N), 256, 0, s, Z, N);
-  for (int k = N - 3; k >= 0; --k) {
-    const int n = N - k - 1;
-    DFTFE_LAUNCH(k_formq, nblk(n, 128), 128, 0, s, Z, N, k, V, tau);
-  }
-  tridiag_ql(s, d, e, Z, N, d_status);
+  if (sh > 48 * 1024) throw Error(DFTFE_ERR_ARG, "dense eigensolver: N too large");
+  int per_sm = 0;
+  DFTFE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi, 256, sh));
+  if (per_sm < 1) throw Error(DFTFE_ERR_CUDA, "dense eigensolver: kernel does not fit on an SM");
+  // enough CTAs for the widest round, never more than can be co-resident
+  const int want = (int)std::min<int64_t>(h->sm_count, ((int64_t)NP * N + 255) / 256);
+  int grid = std::max(1, want);
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(jac::Barrier), s));
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+  DFTFE_LAUNCH(k_fro_norm, 1, 256, 0, s, A, N, anorm);
+  int maxs = 60;
+  void* args[] = {&A, &VT, &d, &N, &maxs, &anorm, &bar, &d_status};
+  DFTFE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi, dim3(grid), dim3(256), args, sh, s));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   DFTFE_LAUNCH(k_rank, nblk(N, 128), 128, 0, s, d, N, perm, evals);
-  DFTFE_LAUNCH(k_sign_copy, N, 256, 0, s, Z, perm, N, Q);
+  DFTFE_LAUNCH(k_sign_copy, N, 256, 0, s, VT, perm, N, Q);
 }
 
 // ----------------------------------------------------------------- residuals

@@ -222,6 +222,7 @@ extern "C" dftfe_status dftfe_rayleigh_ritz_split(dftfe_ham h, const double* X, 
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&s, st, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
   if (s == DFTFE_ERR_NOCONV) throw Error(DFTFE_ERR_NOCONV, "subspace eigensolver did not converge");
+  if (s != 0) throw Error((dftfe_status)s, "subspace eigensolver: a bounded grid wait timed out");
   // Psi_fr = X Q'_fr: the last nfr columns of Q (row stride N)
   rotate_out(h, X, ld, m->M, N, Q + (N - nfr), N, nfr, Xfr, ldfr);
   ABI_END
