@@ -808,8 +808,204 @@ __global__ void __launch_bounds__(256, 2) k_cell_df_wide(const float2* __restric
 
 static unsigned nblk2(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Tiled float-pair cell products.  The cell matrix is stored k-major as pairs,
+// Hk[cell][k][r] = H~^c[r][k] with rows padded to RP = 32 TM (zeros), and streamed in
+// chunks of kDfKt values of k by bulk copies into a double buffer; X^c (32 columns) sits
+// in shared memory as pairs.  Thread (rg, cg) = (lane, warp) owns rows rg + 32 i (i < TM)
+// and columns 4 cg .. 4 cg + 3: per k it reads TM row entries (consecutive across the warp)
+// and one broadcast 32-byte column group, then runs 4 TM independent pair products.
+constexpr int kDfKt = 16;
+constexpr long kDfSpin = 40000000L;
+
+__global__ void k_split_df_k(const double* __restrict__ Hc, float2* __restrict__ Hk, int64_t Nc, int nc, int RP) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= Nc * nc * RP) return;
+  const int r = (int)(t % RP);
+  const int64_t ck = t / RP;                 // cell * nc + k
+  const int k = (int)(ck % nc);
+  const int64_t cell = ck / nc;
+  float2 v = make_float2(0.f, 0.f);
+  if (r < nc) {
+    const double h = Hc[(cell * nc + r) * nc + k];
+    const float hi = __double2float_rn(h);
+    v = make_float2(hi, __double2float_rn(h - (double)hi));
+  }
+  Hk[t] = v;
+}
+
+__device__ __forceinline__ bool df_wait(uint64_t* b, uint32_t parity, int* err) {
+  const uint32_t addr = mx::smem_u32(b);
+  for (long it = 0; it < kDfSpin; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}"
+                 : "=r"(done) : "r"(addr), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  atomicExch(err, (int)DFTFE_ERR_TIMEOUT);
+  return false;
+}
+
+template <int TM>
+__global__ void __launch_bounds__(256, 1) k_cell_df_tiled(const float2* __restrict__ Hk,
+                                                          const int32_t* __restrict__ map,
+                                                          const int32_t* __restrict__ cells, int nc,
+                                                          const double* __restrict__ X, int64_t ldx,
+                                                          double* __restrict__ Z, int64_t ldz, int ncol, int* err) {
+  constexpr int RP = 32 * TM;
+  extern __shared__ __align__(16) uint8_t dsm[];
+  // [0, hbytes): two H chunks (kDfKt x RP pairs each), later the output patch (RP x 33 doubles)
+  constexpr size_t hbytes = (size_t)RP * 33 * 8 > (size_t)2 * kDfKt * RP * 8 ? (size_t)RP * 33 * 8
+                                                                             : (size_t)2 * kDfKt * RP * 8;
+  float2* hs = reinterpret_cast<float2*>(dsm);
+  float2* xs = reinterpret_cast<float2*>(dsm + hbytes);           // nc x 32 pairs
+  int32_t* sm = reinterpret_cast<int32_t*>(xs + (size_t)nc * 32);  // nc node ids
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + ((nc + 3) & ~3));  // 2 mbarriers (8-byte aligned)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t cell = cells[blockIdx.x];
+  const int col0 = blockIdx.y * 32;
+  const int nkt = (nc + kDfKt - 1) / kDfKt;
+  const float2* Hc = Hk + cell * (int64_t)nc * RP;
+  auto issue = [&](int t) {
+    const int k0 = t * kDfKt;
+    const uint32_t bytes = (uint32_t)(min(kDfKt, nc - k0) * RP * 8);
+    const uint32_t b = mx::smem_u32(&bar[t & 1]);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(mx::smem_u32(hs + (size_t)(t & 1) * kDfKt * RP)), "l"(Hc + (size_t)k0 * RP), "r"(bytes), "r"(b)
+                 : "memory");
+  };
+  if (threadIdx.x == 0) {
+    mx::mbar_init(&bar[0], 1);
+    mx::mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    issue(0);
+    if (nkt > 1) issue(1);
+  }
+  const int32_t* cm = map + cell * nc;
+  for (int k = threadIdx.x; k < nc; k += 256) sm[k] = cm[k];
+  __syncthreads();
+  for (int k = warp; k < nc; k += 8) {
+    const int col = col0 + lane;
+    const double xd = col < ncol ? X[(int64_t)sm[k] * ldx + col] : 0.0;
+    const float hi = __double2float_rn(xd);
+    xs[k * 32 + lane] = make_float2(hi, __double2float_rn(xd - (double)hi));
+  }
+  __syncthreads();
+  float ah[TM][4], al[TM][4];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ah[i][j] = al[i][j] = 0.0f;
+  bool ok = true;
+  int issued = nkt > 1 ? 2 : 1;                    // chunks handed to the copy engine (thread 0)
+  for (int t = 0; t < nkt && ok; ++t) {
+    const bool got = df_wait(&bar[t & 1], (t >> 1) & 1, err);
+    if (got) {
+      const float2* hb = hs + (size_t)(t & 1) * kDfKt * RP + lane;
+      const float2* xb = xs + (size_t)t * kDfKt * 32 + 4 * warp;
+      const int kt = min(kDfKt, nc - t * kDfKt);
+#pragma unroll 2
+      for (int kk = 0; kk < kt; ++kk) {
+        const float4 xa = *reinterpret_cast<const float4*>(xb + kk * 32);
+        const float4 xc = *reinterpret_cast<const float4*>(xb + kk * 32 + 2);
+        const float2 x[4] = {make_float2(xa.x, xa.y), make_float2(xa.z, xa.w), make_float2(xc.x, xc.y),
+                             make_float2(xc.z, xc.w)};
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+          const float2 h = hb[kk * RP + 32 * i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // pair product (exact error of the leading term + cross terms) and TwoSum
+            const float p = h.x * x[j].x;
+            float e = fmaf(h.x, x[j].x, -p);
+            e = fmaf(h.x, x[j].y, e);
+            e = fmaf(h.y, x[j].x, e);
+            const float s = ah[i][j] + p;
+            const float bb = s - ah[i][j];
+            const float er = (ah[i][j] - (s - bb)) + (p - bb);
+            ah[i][j] = s;
+            al[i][j] += er + e;
+          }
+        }
+      }
+    }
+    ok = __syncthreads_and(got) != 0;               // chunk t fully read, by every thread
+    if (threadIdx.x == 0 && ok && t + 2 < nkt) {
+      issue(t + 2);
+      issued = t + 3;
+    }
+  }
+  if (!ok) {
+    // let the copies still in flight land before shared memory is given up: the last
+    // chunk issued into each buffer (bounded waits)
+    if (threadIdx.x == 0)
+      for (int t = max(0, issued - 2); t < issued; ++t) df_wait(&bar[t & 1], (t >> 1) & 1, err);
+    __syncthreads();
+    return;
+  }
+  // output patch over the (now idle) H buffers: RP x 33 doubles, then coalesced row updates
+  double* out = reinterpret_cast<double*>(dsm);
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[(lane + 32 * i) * 33 + 4 * warp + j] = (double)ah[i][j] + (double)al[i][j];
+  __syncthreads();
+  const int col = col0 + lane;
+  if (col < ncol)
+    for (int r = warp; r < nc; r += 8) Z[(int64_t)sm[r] * ldz + col] += out[r * 33 + lane];
+}
+
+template <int TM>
+static size_t df_tiled_smem(int nc) {
+  const size_t RP = 32 * TM;
+  const size_t hbytes = std::max(RP * 33 * 8, (size_t)2 * kDfKt * RP * 8);
+  return hbytes + (size_t)nc * 32 * 8 + (size_t)((nc + 3) & ~3) * 4 + 16;
+}
+
+template <int TM>
+static bool apply_df_tiled(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {
+  auto* m = h->mesh;
+  const int nc = m->nc;
+  if (nc > 32 * TM || nc <= 32 * (TM - 1)) return false;
+  const size_t sh = df_tiled_smem<TM>(nc);
+  if (sh > 227 * 1024) return false;
+  static bool attr = false;
+  if (!attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_df_tiled<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  const int RP = 32 * TM;
+  const size_t n2 = (size_t)m->Nc * nc * RP;
+  float2* Hk = (float2*)ws_get(h, "cells_df_k", sizeof(float2) * n2);
+  if (h->df_version != h->potential_version) {
+    DFTFE_LAUNCH(k_split_df_k, nblk2((int64_t)n2), 256, 0, h->stream, h->d_Hc, Hk, (int64_t)m->Nc, nc, RP);
+    h->df_version = h->potential_version;
+  }
+  int* err = (int*)ws_get(h, "df_err", sizeof(int));
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  apply_nonlocal_fp64(h, X, ldx, Y, ldy, ncol);
+  for (int c = 0; c < h->ncolours; ++c) {
+    const int64_t n = h->colour_off[c + 1] - h->colour_off[c];
+    if (n == 0) continue;
+    const int32_t* cells = h->d_colour_cells + h->colour_off[c];
+    ProfScope ps(h, "cell_gemm_df");
+    dim3 grid((unsigned)n, (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_cell_df_tiled<TM>, grid, 256, sh, h->stream, Hk, h->d_map, cells, nc, X, ldx, Y, ldy, ncol, err);
+  }
+  int herr = 0;
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  if (herr) throw Error(DFTFE_ERR_TIMEOUT, "float-pair cell kernel: a bounded wait timed out");
+  return true;
+}
+
 // Y = H~ X with the pair-of-floats cell products (nonlocal part FP64).
 void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {
+  // tiled kernel for the degrees it is instantiated for (rows per thread TM = ceil(nc/32))
+  if (apply_df_tiled<1>(h, X, ldx, Y, ldy, ncol) || apply_df_tiled<2>(h, X, ldx, Y, ldy, ncol) ||
+      apply_df_tiled<4>(h, X, ldx, Y, ldy, ncol) || apply_df_tiled<7>(h, X, ldx, Y, ldy, ncol) ||
+      apply_df_tiled<11>(h, X, ldx, Y, ldy, ncol))
+    return;
   auto* m = h->mesh;
   const int nc = m->nc;
   static bool attr = false;
