@@ -49,7 +49,7 @@ def build(verbose=False, force=False):
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
     deps = [os.path.join(CSRC, s) for s in srcs] + [
-        os.path.join(CSRC, "internal.h"),
+        os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".h")] + [
         os.path.join(os.path.dirname(HERE), "include", "dftfe_gb300.h")]
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps)):

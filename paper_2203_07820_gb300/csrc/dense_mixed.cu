@@ -213,6 +213,8 @@ static void launch_rotate_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, i
 
 void rotate_inplace_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {
   if (M == 0 || N == 0) return;
+  // tensor cores (TF32x3 off-diagonal, FP64 diagonal) whenever the result panel fits TMEM
+  if (rotate_inplace_tc(h, X, ld, M, N, Z, upper)) return;
   float* Zf = (float*)ws_get(h, "rotmix_Zf", sizeof(float) * (size_t)N * N);
   double* zd = (double*)ws_get(h, "rotmix_zd", sizeof(double) * (size_t)N);
   DFTFE_LAUNCH(k_split_rot, nblk((int64_t)N * N), 256, 0, h->stream, Z, N, Zf, zd);

@@ -24,6 +24,7 @@
 // Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its
 // own copies and MMAs (bounded), frees its tensor memory and returns.
 #include "internal.h"
+#include "tcgen05.h"
 
 #include <cuda_bf16.h>
 
@@ -40,29 +41,19 @@ constexpr int kStagesA = 4, kStagesB = 2;
 constexpr int kTile = 16384;                       // one 128-row x 128-byte operand tile
 constexpr int kStageBytes = 2 * kTile;             // hi + lo
 constexpr int kMaxMTiles = 4;                      // 4 x 128 accumulator columns = 512 TMEM columns
-constexpr long kSpinLimit = 40000000L;
+constexpr long kSpinLimit = tc::kSpinLimit;
 constexpr int kPatchLd = 36;                       // epilogue patch row stride (floats)
 constexpr int kPatchBytes = 4 * 32 * kPatchLd * 4;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// byte offset of (row, byte) in a K-major 128-byte-swizzled tile
-__host__ __device__ __forceinline__ uint32_t sw128(uint32_t row, uint32_t b) {
-  return (row >> 3) * 1024u + (row & 7u) * 128u + ((((b >> 4) ^ (row & 7u)) & 7u) << 4) + (b & 15u);
-}
-
-// shared-memory matrix descriptor: start, LBO 16 B (unused for swizzled K-major),
-// SBO 1024 B (between 8-row atoms), version 1, layout SWIZZLE_128B
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-// instruction descriptor: D = F32, A/B format (BF16 = 1 under kind::f16, TF32 = 2 under
-// kind::tf32), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-__host__ __device__ constexpr uint32_t idesc(uint32_t fmt, int M, int N) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
+using tc::idesc;
+using tc::mbar_arrive;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::sdesc;
+using tc::smem_u32;
+using tc::sw128;
+using tc::tc_commit;
+using tc::tf32_rn;
 
 struct Shared {
   uint64_t a_full[kStagesA], a_empty[kStagesA];
@@ -73,34 +64,6 @@ struct Shared {
   int mma_cell;                                     // cell the MMA lane is working on
 };
 
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count));
-}
-
-// bounded wait on a phase parity; false on time-out or abort
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, int* err) {
-  const uint32_t addr = smem_u32(b);
-  for (long it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile("{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}"
-                 : "=r"(done) : "r"(addr), "r"(parity) : "memory");
-    if (done) return true;
-    if (*abort) return false;
-  }
-  *abort = 1;
-  atomicExch(err, (int)DFTFE_ERR_TIMEOUT);
-  return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(b)) : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t* b) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-               :: "r"(smem_u32(b)) : "memory");
-}
-
 template <bool TF32>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
   constexpr uint32_t id = idesc(TF32 ? 2u : 1u, 128, 128);
@@ -110,12 +73,6 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
   else
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
                  :: "r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
-}
-
-__device__ __forceinline__ uint32_t tf32_rn(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
 }
 
 // split x into two terms of the operand type, packed as the 16-byte chunk layout needs

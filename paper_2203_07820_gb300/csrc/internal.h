@@ -173,6 +173,9 @@ void apply_nonlocal_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Y, i
 void gram_lower_mixed(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
                       double* C);
 void rotate_inplace_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper);
+// X <- X Z with the offdiagonal of Z as TF32x3 tensor-core products and its diagonal in FP64
+// (N <= 512); false when not applicable
+bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper);
 
 // dense.cu
 void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb,

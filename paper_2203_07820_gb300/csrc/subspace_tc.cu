@@ -1,0 +1,307 @@
+// Mixed-precision subspace GEMMs on the tensor cores (Sec. 3.2 and Sec. 4.4): the FP32
+// off-diagonal parts of the rotations X <- X Z (Z = L^-T in CholGS, Z = Q in Rayleigh-Ritz)
+// run as 3-term TF32 split products (hi hi + hi lo + lo hi, FP32 accumulation in tensor
+// memory); the diagonal of Z is applied in FP64 in the epilogue, so
+//   X <- X diag(Z) (FP64) + X offdiag(Z) (TF32x3, about FP32 accuracy).
+//
+// k_rot_tc: one CTA per panel of 128 rows of X (N <= 512, so the whole 128 x N product
+// fits the 512 TMEM columns); it writes the FP32 product X offdiag(Z) to a buffer, and
+// k_rot_diag then forms X diag(Z) + that product in FP64, in place.  Warp roles:
+//   warp 0      B producer: bulk copies of the pre-split Z^T tiles (2-stage ring of
+//               (k-chunk, 256-column half) tiles)
+//   warp 1      TMEM owner and MMA issuer (one elected lane)
+//   warps 2-9   A producers in two groups of four (even / odd chunks): each warp reads rows
+//               of the panel (one 256-byte line per row, its next chunk ahead), splits
+//               them into TF32 hi / lo and writes the swizzled K-major tiles; afterwards
+//               warps 2-5 are the epilogue (TMEM -> FP32 product buffer)
+// Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its own
+// copies and MMAs (bounded), frees its tensor memory and returns.
+#include "internal.h"
+#include "tcgen05.h"
+
+#include <algorithm>
+
+namespace dftfe {
+
+namespace rt {
+
+constexpr int kThreads = 320;
+constexpr int kATile = 16384;                // 128 rows x 128 bytes
+constexpr int kAStage = 2 * kATile;          // hi + lo
+constexpr int kBTile = 32768;                // 256 rows x 128 bytes
+constexpr int kBStage = 2 * kBTile;          // hi + lo
+constexpr int kStages = 2;
+
+struct Shared {
+  uint64_t a_full[kStages], a_empty[kStages];
+  uint64_t b_full[kStages], b_empty[kStages];
+  uint64_t acc_full, drain;
+  uint32_t tmem;
+  int abort;
+};
+
+constexpr size_t smem_bytes() { return 1024 + kStages * (size_t)(kAStage + kBStage) + sizeof(Shared); }
+
+}  // namespace rt
+
+// Zt tiles: tile (kc, h) holds rows n = 256 h + r (r < 256) and k = 32 kc + kk (kk < 32) of
+// Z^T, i.e. Z[k][n], split into TF32 hi | lo, K-major 128-byte swizzle; zero on the diagonal,
+// outside N x N, and (upper) below the diagonal.  zd = diag(Z) in FP64.
+__global__ void k_rot_tiles(const double* __restrict__ Z, int N, int upper, int nkc, int nh,
+                            uint8_t* __restrict__ Bt, double* __restrict__ zd) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)nkc * nh * 256 * 32;
+  if (t >= total) return;
+  const int kk = (int)(t % 32);
+  const int r = (int)((t / 32) % 256);
+  const int64_t tile = t / (32 * 256);       // kc * nh + h
+  const int h = (int)(tile % nh), kc = (int)(tile / nh);
+  const int n = 256 * h + r, k = 32 * kc + kk;
+  double v = 0.0;
+  if (n < N && k < N && k != n && (!upper || k < n)) v = Z[(int64_t)k * N + n];
+  uint32_t hi, lo;
+  tc::split_tf32(v, hi, lo);
+  uint8_t* base = Bt + tile * (int64_t)rt::kBStage;
+  const uint32_t off = tc::sw128((uint32_t)r, (uint32_t)(4 * kk));
+  *reinterpret_cast<uint32_t*>(base + off) = hi;
+  *reinterpret_cast<uint32_t*>(base + rt::kBTile + off) = lo;
+  if (n < N && k == n) zd[n] = Z[(int64_t)k * N + n];
+}
+
+__global__ void __launch_bounds__(rt::kThreads, 1) k_rot_tc(const double* __restrict__ X, int64_t ld, int64_t M,
+                                                            int N, const uint8_t* __restrict__ Bt, int nkc, int nh,
+                                                            float* __restrict__ Yo, int64_t ldo, int* err) {
+  using namespace rt;
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;                                   // kStages x (hi 16K | lo 16K)
+  uint8_t* sB = base + kStages * kAStage;               // kStages x (hi 32K | lo 32K)
+  Shared* sh = (Shared*)(sB + kStages * kBStage);
+  volatile int* abort = &sh->abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * 128;
+  const int Np = (N + 15) / 16 * 16;                    // MMA N is a multiple of 16
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sh->a_full[s], 128);
+      mbar_init(&sh->a_empty[s], 1);
+      mbar_init(&sh->b_full[s], 1);
+      mbar_init(&sh->b_empty[s], 1);
+    }
+    mbar_init(&sh->acc_full, 1);
+    mbar_init(&sh->drain, 1);
+    sh->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&sh->tmem)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh->tmem;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ B producer
+    if (lane == 0) {
+      uint32_t t = 0;
+      for (int kc = 0; kc < nkc && !*abort; ++kc)
+        for (int h = 0; h < nh; ++h, ++t) {
+          const int s = t % kStages;
+          if (!mbar_wait(&sh->b_empty[s], ((t / kStages) & 1) ^ 1, abort, err)) break;
+          const uint32_t full = smem_u32(&sh->b_full[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(kBStage) : "memory");
+          const uint8_t* src = Bt + ((int64_t)kc * nh + h) * kBStage;
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       :: "r"(smem_u32(sB + s * kBStage)), "l"(src), "r"(kBStage), "r"(full) : "memory");
+        }
+      // drain: every issued copy has landed before the CTA may exit
+      for (uint32_t u = (t > (uint32_t)kStages ? t - kStages : 0); u < t; ++u) {
+        volatile int no_abort = 0;
+        mbar_wait(&sh->b_full[u % kStages], (u / kStages) & 1, &no_abort, err);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t tb = 0;
+      for (int kc = 0; kc < nkc && !*abort; ++kc) {
+        const int sa = kc % kStages;
+        if (!mbar_wait(&sh->a_full[sa], (kc / kStages) & 1, abort, err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ahi = smem_u32(sA + sa * kAStage), alo = ahi + kATile;
+        for (int h = 0; h < nh && !*abort; ++h, ++tb) {
+          const int sb = tb % kStages;
+          if (!mbar_wait(&sh->b_full[sb], (tb / kStages) & 1, abort, err)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t bhi = smem_u32(sB + sb * kBStage), blo = bhi + kBTile;
+          const int nn = min(256, Np - 256 * h);
+          const uint32_t id = idesc(2u, 128, nn);
+          const uint32_t d = tmem + (uint32_t)(256 * h);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_tf32(d, sdesc(ahi + o), sdesc(bhi + o), id, (kc > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32(d, sdesc(ahi + o), sdesc(blo + o), id, 1u);
+            mma_tf32(d, sdesc(alo + o), sdesc(bhi + o), id, 1u);
+          }
+          tc_commit(&sh->b_empty[sb]);
+        }
+        tc_commit(&sh->a_empty[sa]);
+      }
+      tc_commit(&sh->acc_full);
+      // drain: all issued MMAs complete before tensor memory is released
+      tc_commit(&sh->drain);
+      volatile int no_abort = 0;
+      mbar_wait(&sh->drain, 0, &no_abort, err);
+    }
+  } else {
+    // ------------------------------------------------------------ A producers
+    // two groups of four warps; group g fills the A stage of every chunk kc = g (mod 2), so
+    // each group has two chunk periods to hide its load latency.  In a group, warp w writes
+    // panel rows 32 w .. 32 w + 31 with lane l holding column k = 32 kc + l of a row (one
+    // 256-byte line per row); the raw FP64 values of its next chunk are loaded before the
+    // current one is narrowed, split and stored.
+    const int g = (warp - 2) >> 2;
+    const int w = (warp - 2) & 3;
+    const int q = warp & 3;                             // TMEM lane quadrant (epilogue)
+    if (g == 0) {
+      // pull the panel's rows into L2 first (one bulk prefetch per row)
+      const int64_t m = m0 + 32 * w + lane;
+      const uint32_t bytes = (uint32_t)(8 * N) & ~15u;
+      if (m < M && bytes > 0 && ((uintptr_t)X % 16) == 0 && (ld % 2) == 0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(X + m * ld), "r"(bytes) : "memory");
+    }
+    double raw[32];
+    auto load_a = [&](int kc) {
+      const int k = 32 * kc + lane;
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) {
+        const int64_t m = m0 + 32 * w + rr;
+        raw[rr] = (m < M && k < N) ? X[m * ld + k] : 0.0;
+      }
+    };
+    if (g < nkc) load_a(g);
+    for (int kc = g; kc < nkc && !*abort; kc += kStages) {
+      const int s = kc % kStages;                       // == g
+      // FP64 -> FP32 narrowing (integer operations: this part runs FP64 conversions on its
+      // narrow FP64 pipe), then the TF32 split in FP32; the bits dropped by the narrowing
+      // lie below the accuracy of the 3-term product
+      float v[32];
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) v[rr] = narrow_f64(raw[rr]);
+      if (kc + kStages < nkc) load_a(kc + kStages);
+      if (!mbar_wait(&sh->a_empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
+      uint8_t* ahi = sA + s * kAStage;
+#pragma unroll
+      for (int rr = 0; rr < 32; ++rr) {
+        uint32_t hi, lo;
+        split_tf32f(v[rr], hi, lo);
+        const uint32_t off = sw128((uint32_t)(32 * w + rr), (uint32_t)(4 * lane));
+        *reinterpret_cast<uint32_t*>(ahi + off) = hi;
+        *reinterpret_cast<uint32_t*>(ahi + kATile + off) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&sh->a_full[s]);
+    }
+    // ------------------------------------------------------------ epilogue
+    // Yo[m][n] = acc[m][n] (FP32): the warp reads 32 rows x 32 accumulator columns
+    // (lane = row), turns them around in a shared-memory patch and stores 4 rows x 128 B per
+    // instruction.  The FP64 diagonal term is added by k_rot_diag, whose many warps keep
+    // the narrow FP64 pipe busy where these four could not.
+    if (g == 0 && mbar_wait(&sh->acc_full, 0, abort, err)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* patch = reinterpret_cast<float*>(sA) + q * (32 * 36);
+      const int64_t mq = m0 + 32 * q;
+      const int rows = (int)max((int64_t)0, min((int64_t)32, M - mq));
+      for (int cb = 0; cb * 32 < N; ++cb) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), r);
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<uint4*>(patch + lane * 36 + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+        __syncwarp();
+        const int c4 = 4 * (lane & 7), n = cb * 32 + c4;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int rr = 4 * it + (lane >> 3);
+          if (rr < rows && n < N) {
+            const float4 val = *reinterpret_cast<const float4*>(patch + rr * 36 + c4);
+            float* y = Yo + (mq + rr) * (int64_t)ldo + n;
+            if (n + 3 < N) {
+              *reinterpret_cast<float4*>(y) = val;
+            } else {
+              const float t[4] = {val.x, val.y, val.z, val.w};
+              for (int j = 0; n + j < N; ++j) y[j] = t[j];
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
+// X[m][n] <- X[m][n] zd[n] + Yo[m][n] in FP64 (the diagonal of the rotation), two columns
+// per thread
+__global__ void k_rot_diag(double* __restrict__ X, int64_t ld, const float* __restrict__ Yo, int64_t ldo, int64_t M,
+                           int N, const double* __restrict__ zd) {
+  const int nh = (N + 1) / 2;
+  const int64_t total = M * nh;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = t / nh;
+    const int n = 2 * (int)(t - m * nh);
+    double* x = X + m * ld + n;
+    const float* y = Yo + m * ldo + n;
+    x[0] = fma(x[0], zd[n], (double)y[0]);
+    if (n + 1 < N) x[1] = fma(x[1], zd[n + 1], (double)y[1]);
+  }
+}
+
+static unsigned nblk_tc(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// X <- X Z (in place) for N <= 512 with the tensor-core kernel; false when not applicable
+bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {
+  if (N > 512 || N < 1 || M < 1) return false;
+  static bool attr = false;
+  if (!attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)rt::smem_bytes()));
+    attr = true;
+  }
+  const int nkc = (N + 31) / 32, nh = (N + 255) / 256;
+  uint8_t* Bt = (uint8_t*)ws_get(h, "rot_tc_tiles", (size_t)nkc * nh * rt::kBStage);
+  double* zd = (double*)ws_get(h, "rot_tc_zd", sizeof(double) * (size_t)N);
+  int* err = (int*)ws_get(h, "rot_tc_err", sizeof(int));
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  DFTFE_LAUNCH(k_rot_tiles, nblk_tc((int64_t)nkc * nh * 256 * 32), 256, 0, h->stream, Z, N, upper ? 1 : 0, nkc, nh,
+               Bt, zd);
+  const int64_t ldo = (N + 3) / 4 * 4;
+  float* Yo = (float*)ws_get(h, "rot_tc_out", sizeof(float) * (size_t)M * ldo);
+  {
+    ProfScope ps(h, "rotate_tc");
+    DFTFE_LAUNCH(k_rot_tc, (unsigned)((M + 127) / 128), rt::kThreads, rt::smem_bytes(), h->stream, X, ld, M, N, Bt,
+                 nkc, nh, Yo, ldo, err);
+  }
+  {
+    ProfScope ps(h, "rotate_diag");
+    DFTFE_LAUNCH(k_rot_diag, (unsigned)std::min<int64_t>((int64_t)h->sm_count * 16, nblk_tc(M * ((N + 1) / 2))), 256, 0,
+                 h->stream, X, ld, Yo, ldo, M, N, zd);
+  }
+  int herr = 0;
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  if (herr) throw Error(DFTFE_ERR_TIMEOUT, "tensor-core rotation: a bounded wait timed out");
+  return true;
+}
+
+}  // namespace dftfe
