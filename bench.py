@@ -257,7 +257,7 @@ def run_ours(args, rank, world, local, tdist):
     ms = max_over_ranks(ms, tdist, dev)
     fam = {}
     for name in ("pass_filter", "pass_cholgs", "pass_rr", "cell_gemm_fp64", "cell_gemm_tf32x3",
-                 "cell_gemm_bf16x3", "assemble32", "cell_gemm_df", "rotate_tc", "rotate_diag", "gram", "gram_mixed", "rotate", "rotate_mixed", "syevd"):
+                 "cell_gemm_bf16x3", "assemble32", "cell_gemm_df", "rotate_tc", "rotate_diag", "gram_tc", "coldot", "gram", "gram_mixed", "rotate", "rotate_mixed", "syevd"):
         t, n = dg.dftfe_profile_query(ham, name)
         if n:
             fam[name] = {"ms": t / args.steps, "launches": n // args.steps}

@@ -176,6 +176,10 @@ void rotate_inplace_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, 
 // X <- X Z with the offdiagonal of Z as TF32x3 tensor-core products and its diagonal in FP64
 // (N <= 512); false when not applicable
 bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper);
+// C = A^T B (both triangles) with TF32x3 tensor-core off-diagonal entries and the FP64
+// diagonal from column-dot partials dpart[nchunk][N] (N <= 512); false when not applicable
+bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
+                   double* C, const double* dpart, int nchunk);
 
 // dense.cu
 void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb,

@@ -267,6 +267,233 @@ __global__ void k_rot_diag(double* __restrict__ X, int64_t ld, const float* __re
   }
 }
 
+// ----------------------------------------------------------------------- Gram
+// k_gram_tc: part[s][i][j] = sum over rows m of split s of A[m][i] B[m][j] (TF32x3 products,
+// FP32 accumulation in tensor memory) for the 128-row block b of i and j < min(N, 128 (b+1))
+// (the lower triangle and the diagonal block).  Both operands are read transposed: a
+// producer warp covers 32 columns, lane l loads column c0 + l of 32 consecutive rows (each
+// warp load one 256-byte line), narrows and splits them and writes the lane's row of the
+// K-major tile as 16-byte chunks.  Warp roles: warp 1 TMEM owner and MMA issuer; warps 2-9
+// producers (A stage: warps 2-5, B stages: all eight); afterwards warps 2-5 are the
+// epilogue (TMEM -> FP32 partial block).  Warp 0 only takes part in set-up and teardown.
+namespace gt {
+constexpr int kThreads = 320;
+using rt::kATile;
+using rt::kAStage;
+using rt::kBTile;
+using rt::kBStage;
+using rt::kStages;
+using rt::Shared;
+constexpr size_t smem_bytes() { return rt::smem_bytes(); }
+}  // namespace gt
+
+__global__ void __launch_bounds__(gt::kThreads, 1) k_gram_tc(const double* __restrict__ A, int64_t lda,
+                                                             const double* __restrict__ B, int64_t ldb, int64_t M,
+                                                             int N, int NB, int64_t rows_per_split,
+                                                             float* __restrict__ part, int* err) {
+  using namespace gt;
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + kStages * kAStage;
+  Shared* sh = (Shared*)(sB + kStages * kBStage);
+  volatile int* abort = &sh->abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // heavier blocks (larger b) first
+  const int b = NB - 1 - (int)(blockIdx.x % NB);
+  const int64_t sidx = blockIdx.x / NB;
+  const int64_t k0 = sidx * rows_per_split;
+  const int64_t k1 = min(M, k0 + rows_per_split);
+  const int i0 = 128 * b;
+  const int jn = min(N, 128 * (b + 1));
+  const int Np = (jn + 15) / 16 * 16;
+  const int nh = (Np + 255) / 256;
+  const int nkc = (int)((max((int64_t)0, k1 - k0) + 31) / 32);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sh->a_full[s], 128);
+      mbar_init(&sh->a_empty[s], 1);
+      mbar_init(&sh->b_full[s], 256);
+      mbar_init(&sh->b_empty[s], 1);
+    }
+    mbar_init(&sh->acc_full, 1);
+    mbar_init(&sh->drain, 1);
+    sh->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&sh->tmem)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh->tmem;
+
+  if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t tb = 0;
+      for (int kc = 0; kc < nkc && !*abort; ++kc) {
+        const int sa = kc % kStages;
+        if (!mbar_wait(&sh->a_full[sa], (kc / kStages) & 1, abort, err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ahi = smem_u32(sA + sa * kAStage), alo = ahi + kATile;
+        for (int h = 0; h < nh && !*abort; ++h, ++tb) {
+          const int sb = tb % kStages;
+          if (!mbar_wait(&sh->b_full[sb], (tb / kStages) & 1, abort, err)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t bhi = smem_u32(sB + sb * kBStage), blo = bhi + kBTile;
+          const int nn = min(256, Np - 256 * h);
+          const uint32_t id = idesc(2u, 128, nn);
+          const uint32_t d = tmem + (uint32_t)(256 * h);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t o = ks * 32;
+            mma_tf32(d, sdesc(ahi + o), sdesc(bhi + o), id, (kc > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32(d, sdesc(ahi + o), sdesc(blo + o), id, 1u);
+            mma_tf32(d, sdesc(alo + o), sdesc(bhi + o), id, 1u);
+          }
+          tc_commit(&sh->b_empty[sb]);
+        }
+        tc_commit(&sh->a_empty[sa]);
+      }
+      tc_commit(&sh->acc_full);
+      tc_commit(&sh->drain);
+      volatile int no_abort = 0;
+      mbar_wait(&sh->drain, 0, &no_abort, err);
+    }
+  } else if (warp >= 2) {
+    // ------------------------------------------------------------ producers
+    const int pw = warp - 2;                            // 0..7
+    // unit list per chunk: A unit (pw < 4: columns i0 + 32 pw) then one B unit per half
+    // (columns 256 h + 32 pw); the raw FP64 values of the next unit are loaded before the
+    // current one is narrowed, split and stored
+    const int units = (pw < 4 ? 1 : 0) + nh;
+    const int total = nkc * units;
+    double raw[32];
+    auto unit_src = [&](int u, const double*& src, int64_t& ldm, int& col, int& kc) {
+      kc = u / units;
+      const int r = u % units;
+      if (pw < 4 && r == 0) {
+        src = A; ldm = lda; col = i0 + 32 * pw;
+      } else {
+        const int h = r - (pw < 4 ? 1 : 0);
+        src = B; ldm = ldb; col = 256 * h + 32 * pw;
+      }
+    };
+    auto load = [&](int u) {
+      const double* src; int64_t ldm; int col, kc;
+      unit_src(u, src, ldm, col, kc);
+      const int c = col + lane;
+      const bool cok = c < (src == A ? N : jn);
+#pragma unroll
+      for (int kk = 0; kk < 32; ++kk) {
+        const int64_t m = k0 + 32 * kc + kk;
+        raw[kk] = (cok && m < k1) ? src[m * ldm + c] : 0.0;
+      }
+    };
+    if (total > 0) load(0);
+    for (int u = 0; u < total && !*abort; ++u) {
+      const double* src; int64_t ldm; int col, kc;
+      unit_src(u, src, ldm, col, kc);
+      float v[32];
+#pragma unroll
+      for (int kk = 0; kk < 32; ++kk) v[kk] = narrow_f64(raw[kk]);
+      if (u + 1 < total) load(u + 1);
+      const bool isA = (pw < 4) && (u % units == 0);
+      uint8_t* tile;
+      int trow;
+      if (isA) {
+        const int s = kc % kStages;
+        if (!mbar_wait(&sh->a_empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
+        tile = sA + s * kAStage;
+        trow = 32 * pw + lane;
+      } else {
+        const int h = (u % units) - (pw < 4 ? 1 : 0);
+        const uint32_t t = (uint32_t)kc * nh + h;
+        const int s = t % kStages;
+        if (!mbar_wait(&sh->b_empty[s], ((t / kStages) & 1) ^ 1, abort, err)) break;
+        tile = sB + s * kBStage;
+        trow = 32 * pw + lane;
+      }
+      const int tileb = isA ? kATile : kBTile;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) split_tf32f(v[4 * c + e], hi[e], lo[e]);
+        const uint32_t off = sw128((uint32_t)trow, (uint32_t)(16 * c));
+        *reinterpret_cast<uint4*>(tile + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(tile + tileb + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (isA) {
+        mbar_arrive(&sh->a_full[kc % kStages]);
+      } else {
+        const int h = (u % units) - (pw < 4 ? 1 : 0);
+        mbar_arrive(&sh->b_full[((uint32_t)kc * nh + h) % kStages]);
+      }
+    }
+    // ------------------------------------------------------------ epilogue
+    // part[s][i0 + r][j] for r < 128, j < jn: accumulators read 32 rows x 32 columns at a
+    // time (lane = row), turned around in a shared-memory patch, stored 4 rows x 128 B per
+    // instruction
+    if (pw < 4 && mbar_wait(&sh->acc_full, 0, abort, err)) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int q = warp & 3;
+      float* patch = reinterpret_cast<float*>(sA) + q * (32 * 36);
+      float* out = part + sidx * (int64_t)N * N;
+      for (int cb = 0; cb * 32 < jn; ++cb) {
+        uint32_t r[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), r);
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<uint4*>(patch + lane * 36 + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+        __syncwarp();
+        const int c4 = 4 * (lane & 7), n = cb * 32 + c4;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int rr = 4 * it + (lane >> 3);
+          const int i = i0 + 32 * q + rr;
+          if (i < N && n < jn) {
+            const float4 val = *reinterpret_cast<const float4*>(patch + rr * 36 + c4);
+            float* y = out + (int64_t)i * N + n;
+            const float t[4] = {val.x, val.y, val.z, val.w};
+            for (int j = 0; j < 4 && n + j < jn; ++j) y[j] = t[j];
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
+// C[i][j] = C[j][i] = sum_s part[s][i][j] (i > j, FP64 sum in split order); C[i][i] = sum of
+// the FP64 column-dot partials
+__global__ void k_gram_tc_reduce(const float* __restrict__ part, int nsplit, const double* __restrict__ dpart,
+                                 int nchunk, int N, double* __restrict__ C) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)N * N) return;
+  const int i = (int)(t / N), j = (int)(t % N);
+  if (i < j) return;
+  double s = 0.0;
+  if (i == j)
+    for (int c = 0; c < nchunk; ++c) s += dpart[(int64_t)c * N + i];
+  else
+    for (int k = 0; k < nsplit; ++k) s += (double)part[(int64_t)k * N * N + t];
+  C[(int64_t)i * N + j] = s;
+  C[(int64_t)j * N + i] = s;
+}
+
 static unsigned nblk_tc(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // X <- X Z (in place) for N <= 512 with the tensor-core kernel; false when not applicable
@@ -301,6 +528,42 @@ bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, con
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
   if (herr) throw Error(DFTFE_ERR_TIMEOUT, "tensor-core rotation: a bounded wait timed out");
+  return true;
+}
+
+}  // namespace dftfe
+
+namespace dftfe {
+
+// C (N x N, both triangles) = A^T B with TF32x3 off-diagonal entries and FP64 diagonal
+// (N <= 512); false when not applicable
+bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
+                   double* C, const double* dpart, int nchunk) {
+  if (N > 512 || N < 1 || M < 1) return false;
+  static bool attr = false;
+  if (!attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)gt::smem_bytes()));
+    attr = true;
+  }
+  const int NB = (N + 127) / 128;
+  const int64_t want = std::max<int64_t>(1, (2LL * h->sm_count + NB - 1) / NB);
+  const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(want, (M + 1023) / 1024));
+  const int64_t rows = ((M + nsplit - 1) / nsplit + 31) / 32 * 32;
+  const int64_t ns = (M + rows - 1) / rows;
+  float* part = (float*)ws_get(h, "gram_tc_part", sizeof(float) * (size_t)ns * N * N);
+  int* err = (int*)ws_get(h, "gram_tc_err", sizeof(int));
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  {
+    ProfScope ps(h, "gram_tc");
+    DFTFE_LAUNCH(k_gram_tc, (unsigned)(ns * NB), gt::kThreads, gt::smem_bytes(), h->stream, A, lda, B, ldb, M, N, NB,
+                 rows, part, err);
+  }
+  DFTFE_LAUNCH(k_gram_tc_reduce, nblk_tc((int64_t)N * N), 256, 0, h->stream, part, (int)ns, dpart, nchunk, N, C);
+  int herr = 0;
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  if (herr) throw Error(DFTFE_ERR_TIMEOUT, "tensor-core Gram: a bounded wait timed out");
   return true;
 }
 
