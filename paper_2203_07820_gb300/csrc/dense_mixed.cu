@@ -112,7 +112,8 @@ void gram_lower_mixed(dftfe_ham h, const double* A, int64_t lda, const double* B
         ProfScope ps(h, "coldot");
         DFTFE_LAUNCH(k_coldot_partial, nchunk, 256, 0, h->stream, A, lda, B, ldb, M, N, drows, dpart);
       }
-      if (gram_lower_tc(h, A, lda, B, ldb, M, N, C, dpart, nchunk)) return;
+      // three TF32 slices (FP32-equivalent off-diagonal entries, as the mixed scheme asks)
+      if (gram_lower_tc(h, A, lda, B, ldb, M, N, C, dpart, nchunk, 3)) return;
     }
   }
   const int T = (N + G32T - 1) / G32T;

@@ -268,64 +268,77 @@ __global__ void k_rot_diag(double* __restrict__ X, int64_t ld, const float* __re
 }
 
 // ----------------------------------------------------------------------- Gram
-// k_gram_tc: part[s][i][j] = sum over rows m of split s of A[m][i] B[m][j] (TF32x3 products,
-// FP32 accumulation in tensor memory) for the 128-row block b of i and j < min(N, 128 (b+1))
-// (the lower triangle and the diagonal block).  Both operands are read transposed: a
-// producer warp covers 32 columns, lane l loads column c0 + l of 32 consecutive rows (each
-// warp load one 256-byte line), narrows and splits them and writes the lane's row of the
-// K-major tile as 16-byte chunks.  Warp roles: warp 1 TMEM owner and MMA issuer; warps 2-9
-// producers (A stage: warps 2-5, B stages: all eight); afterwards warps 2-5 are the
-// epilogue (TMEM -> FP32 partial block).  Warp 0 only takes part in set-up and teardown.
+// k_gram_tc<SL>: part[s][i][j] = sum over the rows m of split s of A[m][i] B[m][j] for one
+// 128 x 128 block (bi, bj), bi >= bj, of the lower triangle.  Each FP64 operand is narrowed
+// to FP32 and cut into SL TF32 slices (exact for SL = 3: 11 + 11 + 2 bits); the products
+// kept are the slice pairs of order <= SL - 1:
+//   SL = 2: a1 b1 + a1 b2 + a2 b1                    (TF32x3, about 22-bit operands)
+//   SL = 3: the above + a1 b3 + a2 b2 + a3 b1        (FP32-equivalent)
+// The tensor cores' FP32 accumulation loses accuracy systematically with the length of an
+// accumulation chain, so every 32-row chunk goes to a fresh accumulator (two in tensor
+// memory, alternating) and the epilogue warps add each chunk's product into FP32 registers
+// (rounded to nearest), as a plain FP32 dot product would.
+// Both operands are read transposed: a producer warp covers 32 columns, lane l loads
+// column c0 + l of 32 consecutive rows (one 256-byte line per warp load), narrows and splits
+// them and writes the lane's row of the K-major tile as 16-byte chunks.
+// Warp roles: warp 1 TMEM owner and MMA issuer; warps 2-5 producers (A and B unit of each
+// chunk); warps 6-9 epilogue (accumulators of one TMEM lane quadrant each).  Warp 0 only
+// takes part in set-up and teardown.
 namespace gt {
 constexpr int kThreads = 320;
-using rt::kATile;
-using rt::kAStage;
-using rt::kBTile;
-using rt::kBStage;
-using rt::kStages;
-using rt::Shared;
-constexpr size_t smem_bytes() { return rt::smem_bytes(); }
+constexpr int kStages = 2;
+constexpr int kTile = 16384;                                // 128 rows x 128 bytes, one slice
+template <int SL> struct Cfg {
+  static constexpr int Stage = 2 * SL * kTile;              // A slices | B slices
+  static constexpr size_t smem() { return 1024 + kStages * (size_t)Stage + 128; }
+};
+struct Bars {
+  uint64_t full[kStages], empty[kStages];
+  uint64_t acc_full[2], acc_empty[2], drain;
+  uint32_t tmem;
+  int abort;
+};
 }  // namespace gt
 
+template <int SL>
 __global__ void __launch_bounds__(gt::kThreads, 1) k_gram_tc(const double* __restrict__ A, int64_t lda,
                                                              const double* __restrict__ B, int64_t ldb, int64_t M,
-                                                             int N, int NB, int64_t rows_per_split,
+                                                             int N, int npairs, int64_t rows_per_split,
                                                              float* __restrict__ part, int* err) {
-  using namespace gt;
   using namespace tc;
+  using C = gt::Cfg<SL>;
+  constexpr int kStages = gt::kStages, kTile = gt::kTile;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = base;
-  uint8_t* sB = base + kStages * kAStage;
-  Shared* sh = (Shared*)(sB + kStages * kBStage);
+  gt::Bars* sh = (gt::Bars*)(base + kStages * C::Stage);
   volatile int* abort = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // heavier blocks (larger b) first
-  const int b = NB - 1 - (int)(blockIdx.x % NB);
-  const int64_t sidx = blockIdx.x / NB;
+  const int pidx = (int)(blockIdx.x % npairs);
+  const int64_t sidx = blockIdx.x / npairs;
+  int bi = (int)((sqrtf(8.0f * pidx + 1.0f) - 1.0f) * 0.5f);
+  while (bi * (bi + 1) / 2 > pidx) --bi;
+  while ((bi + 1) * (bi + 2) / 2 <= pidx) ++bi;
+  const int bj = pidx - bi * (bi + 1) / 2;
   const int64_t k0 = sidx * rows_per_split;
   const int64_t k1 = min(M, k0 + rows_per_split);
-  const int i0 = 128 * b;
-  const int jn = min(N, 128 * (b + 1));
-  const int Np = (jn + 15) / 16 * 16;
-  const int nh = (Np + 255) / 256;
   const int nkc = (int)((max((int64_t)0, k1 - k0) + 31) / 32);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&sh->a_full[s], 128);
-      mbar_init(&sh->a_empty[s], 1);
-      mbar_init(&sh->b_full[s], 256);
-      mbar_init(&sh->b_empty[s], 1);
+      mbar_init(&sh->full[s], 128);
+      mbar_init(&sh->empty[s], 1);
     }
-    mbar_init(&sh->acc_full, 1);
+    for (int t = 0; t < 2; ++t) {
+      mbar_init(&sh->acc_full[t], 1);
+      mbar_init(&sh->acc_empty[t], 128);
+    }
     mbar_init(&sh->drain, 1);
     sh->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&sh->tmem)), "r"(512));
+                 :: "r"(smem_u32(&sh->tmem)), "r"(256));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -336,145 +349,119 @@ __global__ void __launch_bounds__(gt::kThreads, 1) k_gram_tc(const double* __res
   if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t tb = 0;
+      const uint32_t id = idesc(2u, 128, 128);
       for (int kc = 0; kc < nkc && !*abort; ++kc) {
-        const int sa = kc % kStages;
-        if (!mbar_wait(&sh->a_full[sa], (kc / kStages) & 1, abort, err)) break;
+        const int s = kc % kStages, buf = kc & 1;
+        if (!mbar_wait(&sh->acc_empty[buf], ((kc >> 1) & 1) ^ 1, abort, err)) break;
+        if (!mbar_wait(&sh->full[s], (kc / kStages) & 1, abort, err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ahi = smem_u32(sA + sa * kAStage), alo = ahi + kATile;
-        for (int h = 0; h < nh && !*abort; ++h, ++tb) {
-          const int sb = tb % kStages;
-          if (!mbar_wait(&sh->b_full[sb], (tb / kStages) & 1, abort, err)) break;
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t bhi = smem_u32(sB + sb * kBStage), blo = bhi + kBTile;
-          const int nn = min(256, Np - 256 * h);
-          const uint32_t id = idesc(2u, 128, nn);
-          const uint32_t d = tmem + (uint32_t)(256 * h);
+        const uint32_t a0 = smem_u32(base + s * C::Stage), b0 = a0 + SL * kTile;
+        const uint32_t d = tmem + (uint32_t)(128 * buf);
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t o = ks * 32;
-            mma_tf32(d, sdesc(ahi + o), sdesc(bhi + o), id, (kc > 0 || ks > 0) ? 1u : 0u);
-            mma_tf32(d, sdesc(ahi + o), sdesc(blo + o), id, 1u);
-            mma_tf32(d, sdesc(alo + o), sdesc(bhi + o), id, 1u);
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t o = ks * 32;
+          mma_tf32(d, sdesc(a0 + o), sdesc(b0 + o), id, ks > 0 ? 1u : 0u);
+          mma_tf32(d, sdesc(a0 + o), sdesc(b0 + kTile + o), id, 1u);
+          mma_tf32(d, sdesc(a0 + kTile + o), sdesc(b0 + o), id, 1u);
+          if (SL == 3) {
+            mma_tf32(d, sdesc(a0 + o), sdesc(b0 + 2 * kTile + o), id, 1u);
+            mma_tf32(d, sdesc(a0 + kTile + o), sdesc(b0 + kTile + o), id, 1u);
+            mma_tf32(d, sdesc(a0 + 2 * kTile + o), sdesc(b0 + o), id, 1u);
           }
-          tc_commit(&sh->b_empty[sb]);
         }
-        tc_commit(&sh->a_empty[sa]);
+        tc_commit(&sh->empty[s]);
+        tc_commit(&sh->acc_full[buf]);
       }
-      tc_commit(&sh->acc_full);
       tc_commit(&sh->drain);
       volatile int no_abort = 0;
       mbar_wait(&sh->drain, 0, &no_abort, err);
     }
-  } else if (warp >= 2) {
+  } else if (warp >= 2 && warp < 6) {
     // ------------------------------------------------------------ producers
-    const int pw = warp - 2;                            // 0..7
-    // unit list per chunk: A unit (pw < 4: columns i0 + 32 pw) then one B unit per half
-    // (columns 256 h + 32 pw); the raw FP64 values of the next unit are loaded before the
-    // current one is narrowed, split and stored
-    const int units = (pw < 4 ? 1 : 0) + nh;
-    const int total = nkc * units;
+    // per chunk: the A unit (columns 128 bi + 32 w) and the B unit (columns 128 bj + 32 w);
+    // the raw FP64 values of the next unit are loaded before the current one is narrowed,
+    // split and stored
+    const int w = warp - 2;
+    const int total = 2 * nkc;
     double raw[32];
-    auto unit_src = [&](int u, const double*& src, int64_t& ldm, int& col, int& kc) {
-      kc = u / units;
-      const int r = u % units;
-      if (pw < 4 && r == 0) {
-        src = A; ldm = lda; col = i0 + 32 * pw;
-      } else {
-        const int h = r - (pw < 4 ? 1 : 0);
-        src = B; ldm = ldb; col = 256 * h + 32 * pw;
-      }
-    };
     auto load = [&](int u) {
-      const double* src; int64_t ldm; int col, kc;
-      unit_src(u, src, ldm, col, kc);
-      const int c = col + lane;
-      const bool cok = c < (src == A ? N : jn);
+      const int kc = u >> 1;
+      const bool isA = (u & 1) == 0;
+      const double* src = isA ? A : B;
+      const int64_t ldm = isA ? lda : ldb;
+      const int c = 128 * (isA ? bi : bj) + 32 * w + lane;
 #pragma unroll
       for (int kk = 0; kk < 32; ++kk) {
         const int64_t m = k0 + 32 * kc + kk;
-        raw[kk] = (cok && m < k1) ? src[m * ldm + c] : 0.0;
+        raw[kk] = (c < N && m < k1) ? src[m * ldm + c] : 0.0;
       }
     };
     if (total > 0) load(0);
     for (int u = 0; u < total && !*abort; ++u) {
-      const double* src; int64_t ldm; int col, kc;
-      unit_src(u, src, ldm, col, kc);
+      const int kc = u >> 1, s = kc % kStages;
+      const bool isA = (u & 1) == 0;
       float v[32];
 #pragma unroll
       for (int kk = 0; kk < 32; ++kk) v[kk] = narrow_f64(raw[kk]);
       if (u + 1 < total) load(u + 1);
-      const bool isA = (pw < 4) && (u % units == 0);
-      uint8_t* tile;
-      int trow;
-      if (isA) {
-        const int s = kc % kStages;
-        if (!mbar_wait(&sh->a_empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
-        tile = sA + s * kAStage;
-        trow = 32 * pw + lane;
-      } else {
-        const int h = (u % units) - (pw < 4 ? 1 : 0);
-        const uint32_t t = (uint32_t)kc * nh + h;
-        const int s = t % kStages;
-        if (!mbar_wait(&sh->b_empty[s], ((t / kStages) & 1) ^ 1, abort, err)) break;
-        tile = sB + s * kBStage;
-        trow = 32 * pw + lane;
-      }
-      const int tileb = isA ? kATile : kBTile;
+      if (isA && !mbar_wait(&sh->empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
+      uint8_t* tile = base + s * C::Stage + (isA ? 0 : SL * kTile);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        uint32_t hi[4], lo[4];
+        uint32_t s1[4], s2[4], s3[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) split_tf32f(v[4 * c + e], hi[e], lo[e]);
-        const uint32_t off = sw128((uint32_t)trow, (uint32_t)(16 * c));
-        *reinterpret_cast<uint4*>(tile + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(tile + tileb + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        for (int e = 0; e < 4; ++e) {
+          const float f = v[4 * c + e];
+          s1[e] = tf32_rn(f);
+          const float r1 = f - __uint_as_float(s1[e]);
+          s2[e] = tf32_rn(r1);
+          s3[e] = tf32_rn(r1 - __uint_as_float(s2[e]));
+        }
+        const uint32_t off = sw128((uint32_t)(32 * w + lane), (uint32_t)(16 * c));
+        *reinterpret_cast<uint4*>(tile + off) = make_uint4(s1[0], s1[1], s1[2], s1[3]);
+        *reinterpret_cast<uint4*>(tile + kTile + off) = make_uint4(s2[0], s2[1], s2[2], s2[3]);
+        if (SL == 3) *reinterpret_cast<uint4*>(tile + 2 * kTile + off) = make_uint4(s3[0], s3[1], s3[2], s3[3]);
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (isA) {
-        mbar_arrive(&sh->a_full[kc % kStages]);
-      } else {
-        const int h = (u % units) - (pw < 4 ? 1 : 0);
-        mbar_arrive(&sh->b_full[((uint32_t)kc * nh + h) % kStages]);
+      if (!isA) {                                      // the stage is complete (A and B written)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&sh->full[s]);
       }
     }
+  } else if (warp >= 6) {
     // ------------------------------------------------------------ epilogue
-    // part[s][i0 + r][j] for r < 128, j < jn: accumulators read 32 rows x 32 columns at a
-    // time (lane = row), turned around in a shared-memory patch, stored 4 rows x 128 B per
-    // instruction
-    if (pw < 4 && mbar_wait(&sh->acc_full, 0, abort, err)) {
+    const int q = warp & 3;                             // TMEM lane quadrant
+    float acc[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
+    bool ok = true;
+    for (int kc = 0; kc < nkc; ++kc) {
+      const int buf = kc & 1;
+      if (!mbar_wait(&sh->acc_full[buf], (kc >> 1) & 1, abort, err)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int q = warp & 3;
-      float* patch = reinterpret_cast<float*>(sA) + q * (32 * 36);
-      float* out = part + sidx * (int64_t)N * N;
-      for (int cb = 0; cb * 32 < jn; ++cb) {
+#pragma unroll
+      for (int cb = 0; cb < 4; ++cb) {
         uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), r);
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(128 * buf + 32 * cb), r);
 #pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          *reinterpret_cast<uint4*>(patch + lane * 36 + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
-        __syncwarp();
-        const int c4 = 4 * (lane & 7), n = cb * 32 + c4;
-#pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int rr = 4 * it + (lane >> 3);
-          const int i = i0 + 32 * q + rr;
-          if (i < N && n < jn) {
-            const float4 val = *reinterpret_cast<const float4*>(patch + rr * 36 + c4);
-            float* y = out + (int64_t)i * N + n;
-            const float t[4] = {val.x, val.y, val.z, val.w};
-            for (int j = 0; j < 4 && n + j < jn; ++j) y[j] = t[j];
-          }
-        }
-        __syncwarp();
+        for (int j = 0; j < 32; ++j) acc[32 * cb + j] += __uint_as_float(r[j]);
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&sh->acc_empty[buf]);
+    }
+    const int i = 128 * bi + 32 * q + lane;
+    if (ok && i < N) {
+      float* out = part + sidx * (int64_t)N * N + (int64_t)i * N + 128 * bj;
+      const int ncols = min(128, N - 128 * bj);
+#pragma unroll
+      for (int j = 0; j < 128; ++j)
+        if (j < ncols) out[j] = acc[j];
     }
   }
   __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256));
 }
 
 // C[i][j] = C[j][i] = sum_s part[s][i][j] (i > j, FP64 sum in split order); C[i][i] = sum of
@@ -538,16 +525,19 @@ namespace dftfe {
 // C (N x N, both triangles) = A^T B with TF32x3 off-diagonal entries and FP64 diagonal
 // (N <= 512); false when not applicable
 bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
-                   double* C, const double* dpart, int nchunk) {
-  if (N > 512 || N < 1 || M < 1) return false;
+                   double* C, const double* dpart, int nchunk, int slices) {
+  if (N > 512 || N < 1 || M < 1 || (slices != 2 && slices != 3)) return false;
   static bool attr = false;
   if (!attr) {
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)gt::smem_bytes()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)gt::Cfg<2>::smem()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)gt::Cfg<3>::smem()));
     attr = true;
   }
   const int NB = (N + 127) / 128;
-  const int64_t want = std::max<int64_t>(1, (2LL * h->sm_count + NB - 1) / NB);
+  const int npairs = NB * (NB + 1) / 2;
+  const int64_t want = std::max<int64_t>(1, (2LL * h->sm_count + npairs - 1) / npairs);
   const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(want, (M + 1023) / 1024));
   const int64_t rows = ((M + nsplit - 1) / nsplit + 31) / 32 * 32;
   const int64_t ns = (M + rows - 1) / rows;
@@ -556,8 +546,12 @@ bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, i
   DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
   {
     ProfScope ps(h, "gram_tc");
-    DFTFE_LAUNCH(k_gram_tc, (unsigned)(ns * NB), gt::kThreads, gt::smem_bytes(), h->stream, A, lda, B, ldb, M, N, NB,
-                 rows, part, err);
+    if (slices == 2)
+      DFTFE_LAUNCH(k_gram_tc<2>, (unsigned)(ns * npairs), gt::kThreads, gt::Cfg<2>::smem(), h->stream, A, lda, B,
+                   ldb, M, N, npairs, rows, part, err);
+    else
+      DFTFE_LAUNCH(k_gram_tc<3>, (unsigned)(ns * npairs), gt::kThreads, gt::Cfg<3>::smem(), h->stream, A, lda, B,
+                   ldb, M, N, npairs, rows, part, err);
   }
   DFTFE_LAUNCH(k_gram_tc_reduce, nblk_tc((int64_t)N * N), 256, 0, h->stream, part, (int)ns, dpart, nchunk, N, C);
   int herr = 0;
