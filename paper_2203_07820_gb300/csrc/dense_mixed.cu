@@ -107,13 +107,12 @@ void gram_lower_mixed(dftfe_ham h, const double* A, int64_t lda, const double* B
     const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(h->sm_count * 4, M / 64));
     const int64_t drows = (M + nchunk - 1) / nchunk;
     double* dpart = (double*)ws_get(h, "coldot_part", sizeof(double) * (size_t)nchunk * N);
-    if (N <= 512 && M >= 1) {
+    if (M >= 1) {
       {
         ProfScope ps(h, "coldot");
         DFTFE_LAUNCH(k_coldot_partial, nchunk, 256, 0, h->stream, A, lda, B, ldb, M, N, drows, dpart);
       }
-      // three TF32 slices (FP32-equivalent off-diagonal entries, as the mixed scheme asks)
-      if (gram_lower_tc(h, A, lda, B, ldb, M, N, C, dpart, nchunk, 3)) return;
+      if (gram_lower_tc(h, A, lda, B, ldb, M, N, C, dpart, nchunk)) return;
     }
   }
   const int T = (N + G32T - 1) / G32T;

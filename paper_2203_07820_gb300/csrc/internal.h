@@ -173,14 +173,13 @@ void apply_nonlocal_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Y, i
 void gram_lower_mixed(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
                       double* C);
 void rotate_inplace_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper);
-// X <- X Z with the offdiagonal of Z as TF32x3 tensor-core products and its diagonal in FP64
-// (N <= 512); false when not applicable
+// X <- X Z with the offdiagonal of Z as FP32-equivalent tensor-core products and its
+// diagonal in FP64; false when not applicable
 bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper);
-// C = A^T B (both triangles) with tensor-core off-diagonal entries from `slices` TF32 slices
-// per operand (2: TF32x3, 3: FP32-equivalent) and the FP64 diagonal from column-dot
-// partials dpart[nchunk][N] (N <= 512); false when not applicable
+// C = A^T B (both triangles) with FP32-equivalent tensor-core off-diagonal entries and the
+// FP64 diagonal from column-dot partials dpart[nchunk][N]; false when not applicable
 bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
-                   double* C, const double* dpart, int nchunk, int slices);
+                   double* C, const double* dpart, int nchunk);
 
 // dense.cu
 void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb,

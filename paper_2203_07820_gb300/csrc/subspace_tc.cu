@@ -1,19 +1,26 @@
 // Mixed-precision subspace GEMMs on the tensor cores (Sec. 3.2 and Sec. 4.4): the FP32
-// off-diagonal parts of the rotations X <- X Z (Z = L^-T in CholGS, Z = Q in Rayleigh-Ritz)
-// run as 3-term TF32 split products (hi hi + hi lo + lo hi, FP32 accumulation in tensor
-// memory); the diagonal of Z is applied in FP64 in the epilogue, so
-//   X <- X diag(Z) (FP64) + X offdiag(Z) (TF32x3, about FP32 accuracy).
+// off-diagonal parts of the Gram matrices S = X^T X, H^ = X^T W and of the rotations
+// X <- X Z (Z = L^-T in CholGS, Z = Q in Rayleigh-Ritz) run as TF32 split products with
+// FP32 accumulation; the diagonals stay FP64 (column dots; X diag(Z) in the epilogue pass).
 //
-// k_rot_tc: one CTA per panel of 128 rows of X (N <= 512, so the whole 128 x N product
-// fits the 512 TMEM columns); it writes the FP32 product X offdiag(Z) to a buffer, and
-// k_rot_diag then forms X diag(Z) + that product in FP64, in place.  Warp roles:
-//   warp 0      B producer: bulk copies of the pre-split Z^T tiles (2-stage ring of
-//               (k-chunk, 256-column half) tiles)
+// Precision.  Each FP64 operand is narrowed to FP32 and cut into three TF32 slices (exact:
+// 11 + 11 + 2 bits); the six slice products of order <= 2 (a1 b1, a1 b2, a2 b1, a1 b3,
+// a2 b2, a3 b1) give FP32-equivalent products.  The tensor cores' FP32 accumulation loses
+// accuracy systematically with the length of an accumulation chain, so every 32-deep chunk
+// of the contraction goes to a fresh accumulator (two in tensor memory, alternating) and
+// epilogue warps add the chunk products into FP32 registers rounded to nearest, as a plain
+// FP32 dot product would.
+//
+// k_rot_tc: one CTA per (panel of 128 rows of X, tile of 128 output columns), the four
+// column tiles of a panel adjacent in launch order so the panel is re-read from L2.  The
+// FP32 product X offdiag(Z) goes to a buffer; k_rot_diag then forms X diag(Z) + product in
+// FP64, in place.  Warp roles:
+//   warp 0      B producer: bulk copies of the pre-split Z^T tiles (2-stage ring)
 //   warp 1      TMEM owner and MMA issuer (one elected lane)
-//   warps 2-9   A producers in two groups of four (even / odd chunks): each warp reads rows
-//               of the panel (one 256-byte line per row, its next chunk ahead), splits
-//               them into TF32 hi / lo and writes the swizzled K-major tiles; afterwards
-//               warps 2-5 are the epilogue (TMEM -> FP32 product buffer)
+//   warps 2-5   A producers: each warp reads rows of the panel (one 256-byte line per row,
+//               its next chunk ahead), narrows and splits them and writes the swizzled
+//               K-major tiles
+//   warps 6-9   epilogue: chunk products of one TMEM lane quadrant into FP32 registers
 // Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its own
 // copies and MMAs (bounded), frees its tensor memory and returns.
 #include "internal.h"
@@ -23,81 +30,122 @@
 
 namespace dftfe {
 
-namespace rt {
+namespace st {
 
 constexpr int kThreads = 320;
-constexpr int kATile = 16384;                // 128 rows x 128 bytes
-constexpr int kAStage = 2 * kATile;          // hi + lo
-constexpr int kBTile = 32768;                // 256 rows x 128 bytes
-constexpr int kBStage = 2 * kBTile;          // hi + lo
 constexpr int kStages = 2;
+constexpr int kSlices = 3;
+constexpr int kTile = 16384;                 // 128 rows x 128 bytes, one slice
+constexpr int kOperand = kSlices * kTile;    // one 128 x 32 operand block, all slices
+constexpr int kStage = 2 * kOperand;         // A | B
 
-struct Shared {
-  uint64_t a_full[kStages], a_empty[kStages];
-  uint64_t b_full[kStages], b_empty[kStages];
-  uint64_t acc_full, drain;
+struct Bars {
+  uint64_t a_full[kStages], b_full[kStages], empty[kStages];
+  uint64_t acc_full[2], acc_empty[2], drain;
   uint32_t tmem;
   int abort;
 };
 
-constexpr size_t smem_bytes() { return 1024 + kStages * (size_t)(kAStage + kBStage) + sizeof(Shared); }
+constexpr size_t smem_bytes() { return 1024 + kStages * (size_t)kStage + sizeof(Bars); }
 
-}  // namespace rt
+// the three TF32 slices of an FP32 value (exact)
+__device__ __forceinline__ void slices3(float f, uint32_t& s1, uint32_t& s2, uint32_t& s3) {
+  s1 = tc::tf32_rn(f);
+  const float r1 = f - __uint_as_float(s1);
+  s2 = tc::tf32_rn(r1);
+  s3 = tc::tf32_rn(r1 - __uint_as_float(s2));
+}
 
-// Zt tiles: tile (kc, h) holds rows n = 256 h + r (r < 256) and k = 32 kc + kk (kk < 32) of
-// Z^T, i.e. Z[k][n], split into TF32 hi | lo, K-major 128-byte swizzle; zero on the diagonal,
-// outside N x N, and (upper) below the diagonal.  zd = diag(Z) in FP64.
-__global__ void k_rot_tiles(const double* __restrict__ Z, int N, int upper, int nkc, int nh,
+// the six slice products of one 32-deep chunk into accumulator d (fresh)
+__device__ __forceinline__ void chunk_mma(uint32_t d, uint32_t a0, uint32_t b0) {
+  const uint32_t id = tc::idesc(2u, 128, 128);
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    const uint32_t o = ks * 32;
+    tc::mma_tf32(d, tc::sdesc(a0 + o), tc::sdesc(b0 + o), id, ks > 0 ? 1u : 0u);
+    tc::mma_tf32(d, tc::sdesc(a0 + o), tc::sdesc(b0 + kTile + o), id, 1u);
+    tc::mma_tf32(d, tc::sdesc(a0 + kTile + o), tc::sdesc(b0 + o), id, 1u);
+    tc::mma_tf32(d, tc::sdesc(a0 + o), tc::sdesc(b0 + 2 * kTile + o), id, 1u);
+    tc::mma_tf32(d, tc::sdesc(a0 + kTile + o), tc::sdesc(b0 + kTile + o), id, 1u);
+    tc::mma_tf32(d, tc::sdesc(a0 + 2 * kTile + o), tc::sdesc(b0 + o), id, 1u);
+  }
+}
+
+// epilogue: add chunk kc's 32 x 128 accumulator block of this warp's quadrant into acc
+__device__ __forceinline__ bool drain_chunk(Bars* sh, uint32_t tmem, int q, int kc, float* acc,
+                                            volatile int* abort, int* err) {
+  const int buf = kc & 1;
+  if (!tc::mbar_wait(&sh->acc_full[buf], (kc >> 1) & 1, abort, err)) return false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+  for (int cb = 0; cb < 4; ++cb) {
+    uint32_t r[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(128 * buf + 32 * cb), r);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[32 * cb + j] += __uint_as_float(r[j]);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  tc::mbar_arrive(&sh->acc_empty[buf]);
+  return true;
+}
+
+}  // namespace st
+
+// Zt tiles: tile (kc, nt) holds rows n = 128 nt + r (r < 128) and k = 32 kc + kk (kk < 32)
+// of Z^T, i.e. Z[k][n], as three TF32 slices, K-major 128-byte swizzle; zero on the
+// diagonal, outside N x N, and (upper) below the diagonal.  zd = diag(Z) in FP64.
+__global__ void k_rot_tiles(const double* __restrict__ Z, int N, int upper, int nkc, int nt,
                             uint8_t* __restrict__ Bt, double* __restrict__ zd) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t total = (int64_t)nkc * nh * 256 * 32;
+  const int64_t total = (int64_t)nkc * nt * 128 * 32;
   if (t >= total) return;
   const int kk = (int)(t % 32);
-  const int r = (int)((t / 32) % 256);
-  const int64_t tile = t / (32 * 256);       // kc * nh + h
-  const int h = (int)(tile % nh), kc = (int)(tile / nh);
-  const int n = 256 * h + r, k = 32 * kc + kk;
+  const int r = (int)((t / 32) % 128);
+  const int64_t tile = t / (32 * 128);       // kc * nt + column tile
+  const int ct = (int)(tile % nt), kc = (int)(tile / nt);
+  const int n = 128 * ct + r, k = 32 * kc + kk;
   double v = 0.0;
   if (n < N && k < N && k != n && (!upper || k < n)) v = Z[(int64_t)k * N + n];
-  uint32_t hi, lo;
-  tc::split_tf32(v, hi, lo);
-  uint8_t* base = Bt + tile * (int64_t)rt::kBStage;
+  uint32_t s1, s2, s3;
+  st::slices3(tc::narrow_f64(v), s1, s2, s3);
+  uint8_t* base = Bt + tile * (int64_t)st::kOperand;
   const uint32_t off = tc::sw128((uint32_t)r, (uint32_t)(4 * kk));
-  *reinterpret_cast<uint32_t*>(base + off) = hi;
-  *reinterpret_cast<uint32_t*>(base + rt::kBTile + off) = lo;
+  *reinterpret_cast<uint32_t*>(base + off) = s1;
+  *reinterpret_cast<uint32_t*>(base + st::kTile + off) = s2;
+  *reinterpret_cast<uint32_t*>(base + 2 * st::kTile + off) = s3;
   if (n < N && k == n) zd[n] = Z[(int64_t)k * N + n];
 }
 
-__global__ void __launch_bounds__(rt::kThreads, 1) k_rot_tc(const double* __restrict__ X, int64_t ld, int64_t M,
-                                                            int N, const uint8_t* __restrict__ Bt, int nkc, int nh,
+__global__ void __launch_bounds__(st::kThreads, 1) k_rot_tc(const double* __restrict__ X, int64_t ld, int64_t M,
+                                                            int N, const uint8_t* __restrict__ Bt, int nkc, int nt,
                                                             float* __restrict__ Yo, int64_t ldo, int* err) {
-  using namespace rt;
+  using namespace st;
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = base;                                   // kStages x (hi 16K | lo 16K)
-  uint8_t* sB = base + kStages * kAStage;               // kStages x (hi 32K | lo 32K)
-  Shared* sh = (Shared*)(sB + kStages * kBStage);
+  Bars* sh = (Bars*)(base + kStages * kStage);
   volatile int* abort = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * 128;
-  const int Np = (N + 15) / 16 * 16;                    // MMA N is a multiple of 16
+  const int ct = (int)(blockIdx.x % nt);               // output column tile
+  const int64_t m0 = (int64_t)(blockIdx.x / nt) * 128;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&sh->a_full[s], 128);
-      mbar_init(&sh->a_empty[s], 1);
       mbar_init(&sh->b_full[s], 1);
-      mbar_init(&sh->b_empty[s], 1);
+      mbar_init(&sh->empty[s], 1);
     }
-    mbar_init(&sh->acc_full, 1);
+    for (int t = 0; t < 2; ++t) {
+      mbar_init(&sh->acc_full[t], 1);
+      mbar_init(&sh->acc_empty[t], 128);
+    }
     mbar_init(&sh->drain, 1);
     sh->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 :: "r"(smem_u32(&sh->tmem)), "r"(512));
+                 :: "r"(smem_u32(&sh->tmem)), "r"(256));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -108,19 +156,19 @@ __global__ void __launch_bounds__(rt::kThreads, 1) k_rot_tc(const double* __rest
   if (warp == 0) {
     // ------------------------------------------------------------ B producer
     if (lane == 0) {
-      uint32_t t = 0;
-      for (int kc = 0; kc < nkc && !*abort; ++kc)
-        for (int h = 0; h < nh; ++h, ++t) {
-          const int s = t % kStages;
-          if (!mbar_wait(&sh->b_empty[s], ((t / kStages) & 1) ^ 1, abort, err)) break;
-          const uint32_t full = smem_u32(&sh->b_full[s]);
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(kBStage) : "memory");
-          const uint8_t* src = Bt + ((int64_t)kc * nh + h) * kBStage;
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                       :: "r"(smem_u32(sB + s * kBStage)), "l"(src), "r"(kBStage), "r"(full) : "memory");
-        }
+      int kc = 0;
+      for (; kc < nkc && !*abort; ++kc) {
+        const int s = kc % kStages;
+        if (!mbar_wait(&sh->empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
+        const uint32_t full = smem_u32(&sh->b_full[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(kOperand) : "memory");
+        const uint8_t* src = Bt + ((int64_t)kc * nt + ct) * kOperand;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     :: "r"(smem_u32(base + s * kStage + kOperand)), "l"(src), "r"(kOperand), "r"(full)
+                     : "memory");
+      }
       // drain: every issued copy has landed before the CTA may exit
-      for (uint32_t u = (t > (uint32_t)kStages ? t - kStages : 0); u < t; ++u) {
+      for (int u = max(0, kc - kStages); u < kc; ++u) {
         volatile int no_abort = 0;
         mbar_wait(&sh->b_full[u % kStages], (u / kStages) & 1, &no_abort, err);
       }
@@ -128,54 +176,27 @@ __global__ void __launch_bounds__(rt::kThreads, 1) k_rot_tc(const double* __rest
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      uint32_t tb = 0;
       for (int kc = 0; kc < nkc && !*abort; ++kc) {
-        const int sa = kc % kStages;
-        if (!mbar_wait(&sh->a_full[sa], (kc / kStages) & 1, abort, err)) break;
+        const int s = kc % kStages, buf = kc & 1;
+        if (!mbar_wait(&sh->acc_empty[buf], ((kc >> 1) & 1) ^ 1, abort, err)) break;
+        if (!mbar_wait(&sh->a_full[s], (kc / kStages) & 1, abort, err)) break;
+        if (!mbar_wait(&sh->b_full[s], (kc / kStages) & 1, abort, err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ahi = smem_u32(sA + sa * kAStage), alo = ahi + kATile;
-        for (int h = 0; h < nh && !*abort; ++h, ++tb) {
-          const int sb = tb % kStages;
-          if (!mbar_wait(&sh->b_full[sb], (tb / kStages) & 1, abort, err)) break;
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t bhi = smem_u32(sB + sb * kBStage), blo = bhi + kBTile;
-          const int nn = min(256, Np - 256 * h);
-          const uint32_t id = idesc(2u, 128, nn);
-          const uint32_t d = tmem + (uint32_t)(256 * h);
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks) {
-            const uint32_t o = ks * 32;
-            mma_tf32(d, sdesc(ahi + o), sdesc(bhi + o), id, (kc > 0 || ks > 0) ? 1u : 0u);
-            mma_tf32(d, sdesc(ahi + o), sdesc(blo + o), id, 1u);
-            mma_tf32(d, sdesc(alo + o), sdesc(bhi + o), id, 1u);
-          }
-          tc_commit(&sh->b_empty[sb]);
-        }
-        tc_commit(&sh->a_empty[sa]);
+        const uint32_t a0 = smem_u32(base + s * kStage);
+        chunk_mma(tmem + (uint32_t)(128 * buf), a0, a0 + kOperand);
+        tc_commit(&sh->empty[s]);
+        tc_commit(&sh->acc_full[buf]);
       }
-      tc_commit(&sh->acc_full);
-      // drain: all issued MMAs complete before tensor memory is released
       tc_commit(&sh->drain);
       volatile int no_abort = 0;
       mbar_wait(&sh->drain, 0, &no_abort, err);
     }
-  } else {
+  } else if (warp < 6) {
     // ------------------------------------------------------------ A producers
-    // two groups of four warps; group g fills the A stage of every chunk kc = g (mod 2), so
-    // each group has two chunk periods to hide its load latency.  In a group, warp w writes
-    // panel rows 32 w .. 32 w + 31 with lane l holding column k = 32 kc + l of a row (one
-    // 256-byte line per row); the raw FP64 values of its next chunk are loaded before the
-    // current one is narrowed, split and stored.
-    const int g = (warp - 2) >> 2;
-    const int w = (warp - 2) & 3;
-    const int q = warp & 3;                             // TMEM lane quadrant (epilogue)
-    if (g == 0) {
-      // pull the panel's rows into L2 first (one bulk prefetch per row)
-      const int64_t m = m0 + 32 * w + lane;
-      const uint32_t bytes = (uint32_t)(8 * N) & ~15u;
-      if (m < M && bytes > 0 && ((uintptr_t)X % 16) == 0 && (ld % 2) == 0)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(X + m * ld), "r"(bytes) : "memory");
-    }
+    // warp w writes panel rows 32 w .. 32 w + 31 of each chunk, lane l holding column
+    // k = 32 kc + l of a row; the raw FP64 values of the next chunk are loaded before the
+    // current one is narrowed, split and stored
+    const int w = warp - 2;
     double raw[32];
     auto load_a = [&](int kc) {
       const int k = 32 * kc + lane;
@@ -185,62 +206,48 @@ __global__ void __launch_bounds__(rt::kThreads, 1) k_rot_tc(const double* __rest
         raw[rr] = (m < M && k < N) ? X[m * ld + k] : 0.0;
       }
     };
-    if (g < nkc) load_a(g);
-    for (int kc = g; kc < nkc && !*abort; kc += kStages) {
-      const int s = kc % kStages;                       // == g
-      // FP64 -> FP32 narrowing (integer operations: this part runs FP64 conversions on its
-      // narrow FP64 pipe), then the TF32 split in FP32; the bits dropped by the narrowing
-      // lie below the accuracy of the 3-term product
+    if (nkc > 0) load_a(0);
+    for (int kc = 0; kc < nkc && !*abort; ++kc) {
+      const int s = kc % kStages;
       float v[32];
 #pragma unroll
       for (int rr = 0; rr < 32; ++rr) v[rr] = narrow_f64(raw[rr]);
-      if (kc + kStages < nkc) load_a(kc + kStages);
-      if (!mbar_wait(&sh->a_empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
-      uint8_t* ahi = sA + s * kAStage;
+      if (kc + 1 < nkc) load_a(kc + 1);
+      if (!mbar_wait(&sh->empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
+      uint8_t* tile = base + s * kStage;
 #pragma unroll
       for (int rr = 0; rr < 32; ++rr) {
-        uint32_t hi, lo;
-        split_tf32f(v[rr], hi, lo);
+        uint32_t s1, s2, s3;
+        slices3(v[rr], s1, s2, s3);
         const uint32_t off = sw128((uint32_t)(32 * w + rr), (uint32_t)(4 * lane));
-        *reinterpret_cast<uint32_t*>(ahi + off) = hi;
-        *reinterpret_cast<uint32_t*>(ahi + kATile + off) = lo;
+        *reinterpret_cast<uint32_t*>(tile + off) = s1;
+        *reinterpret_cast<uint32_t*>(tile + kTile + off) = s2;
+        *reinterpret_cast<uint32_t*>(tile + 2 * kTile + off) = s3;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&sh->a_full[s]);
     }
+  } else {
     // ------------------------------------------------------------ epilogue
-    // Yo[m][n] = acc[m][n] (FP32): the warp reads 32 rows x 32 accumulator columns
-    // (lane = row), turns them around in a shared-memory patch and stores 4 rows x 128 B per
-    // instruction.  The FP64 diagonal term is added by k_rot_diag, whose many warps keep
-    // the narrow FP64 pipe busy where these four could not.
-    if (g == 0 && mbar_wait(&sh->acc_full, 0, abort, err)) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float* patch = reinterpret_cast<float*>(sA) + q * (32 * 36);
-      const int64_t mq = m0 + 32 * q;
-      const int rows = (int)max((int64_t)0, min((int64_t)32, M - mq));
-      for (int cb = 0; cb * 32 < N; ++cb) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), r);
+    const int q = warp & 3;
+    float acc[128];
 #pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          *reinterpret_cast<uint4*>(patch + lane * 36 + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
-        __syncwarp();
-        const int c4 = 4 * (lane & 7), n = cb * 32 + c4;
+    for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
+    bool ok = true;
+    for (int kc = 0; kc < nkc && ok; ++kc) ok = drain_chunk(sh, tmem, q, kc, acc, abort, err);
+    const int64_t m = m0 + 32 * q + lane;
+    const int n0 = 128 * ct;
+    if (ok && m < M) {
+      float* y = Yo + m * ldo + n0;
+      const int ncols = min(128, N - n0);
+      if (ncols == 128) {
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int rr = 4 * it + (lane >> 3);
-          if (rr < rows && n < N) {
-            const float4 val = *reinterpret_cast<const float4*>(patch + rr * 36 + c4);
-            float* y = Yo + (mq + rr) * (int64_t)ldo + n;
-            if (n + 3 < N) {
-              *reinterpret_cast<float4*>(y) = val;
-            } else {
-              const float t[4] = {val.x, val.y, val.z, val.w};
-              for (int j = 0; n + j < N; ++j) y[j] = t[j];
-            }
-          }
-        }
-        __syncwarp();
+        for (int j = 0; j < 128; j += 4)
+          *reinterpret_cast<float4*>(y + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 128; ++j)
+          if (j < ncols) y[j] = acc[j];
       }
     }
   }
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(rt::kThreads, 1) k_rot_tc(const double* __rest
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(256));
 }
 
 // X[m][n] <- X[m][n] zd[n] + Yo[m][n] in FP64 (the diagonal of the rotation), two columns
@@ -268,49 +275,23 @@ __global__ void k_rot_diag(double* __restrict__ X, int64_t ld, const float* __re
 }
 
 // ----------------------------------------------------------------------- Gram
-// k_gram_tc<SL>: part[s][i][j] = sum over the rows m of split s of A[m][i] B[m][j] for one
-// 128 x 128 block (bi, bj), bi >= bj, of the lower triangle.  Each FP64 operand is narrowed
-// to FP32 and cut into SL TF32 slices (exact for SL = 3: 11 + 11 + 2 bits); the products
-// kept are the slice pairs of order <= SL - 1:
-//   SL = 2: a1 b1 + a1 b2 + a2 b1                    (TF32x3, about 22-bit operands)
-//   SL = 3: the above + a1 b3 + a2 b2 + a3 b1        (FP32-equivalent)
-// The tensor cores' FP32 accumulation loses accuracy systematically with the length of an
-// accumulation chain, so every 32-row chunk goes to a fresh accumulator (two in tensor
-// memory, alternating) and the epilogue warps add each chunk's product into FP32 registers
-// (rounded to nearest), as a plain FP32 dot product would.
+// k_gram_tc: part[s][i][j] = sum over the rows m of split s of A[m][i] B[m][j] for one
+// 128 x 128 block (bi, bj), bi >= bj, of the lower triangle (three TF32 slices, 32-row
+// chunks into alternating accumulators, FP32 register sums; see the top of this file).
 // Both operands are read transposed: a producer warp covers 32 columns, lane l loads
-// column c0 + l of 32 consecutive rows (one 256-byte line per warp load), narrows and splits
-// them and writes the lane's row of the K-major tile as 16-byte chunks.
-// Warp roles: warp 1 TMEM owner and MMA issuer; warps 2-5 producers (A and B unit of each
-// chunk); warps 6-9 epilogue (accumulators of one TMEM lane quadrant each).  Warp 0 only
-// takes part in set-up and teardown.
-namespace gt {
-constexpr int kThreads = 320;
-constexpr int kStages = 2;
-constexpr int kTile = 16384;                                // 128 rows x 128 bytes, one slice
-template <int SL> struct Cfg {
-  static constexpr int Stage = 2 * SL * kTile;              // A slices | B slices
-  static constexpr size_t smem() { return 1024 + kStages * (size_t)Stage + 128; }
-};
-struct Bars {
-  uint64_t full[kStages], empty[kStages];
-  uint64_t acc_full[2], acc_empty[2], drain;
-  uint32_t tmem;
-  int abort;
-};
-}  // namespace gt
-
-template <int SL>
-__global__ void __launch_bounds__(gt::kThreads, 1) k_gram_tc(const double* __restrict__ A, int64_t lda,
+// column c0 + l of 32 consecutive rows (one 256-byte line per warp load), narrows and
+// splits them and writes the lane's row of the K-major tile as 16-byte chunks.
+// Warp roles: warp 1 TMEM owner and MMA issuer; warps 2-5 producers (the A and the B unit
+// of each chunk); warps 6-9 epilogue.  Warp 0 only takes part in set-up and teardown.
+__global__ void __launch_bounds__(st::kThreads, 1) k_gram_tc(const double* __restrict__ A, int64_t lda,
                                                              const double* __restrict__ B, int64_t ldb, int64_t M,
                                                              int N, int npairs, int64_t rows_per_split,
                                                              float* __restrict__ part, int* err) {
+  using namespace st;
   using namespace tc;
-  using C = gt::Cfg<SL>;
-  constexpr int kStages = gt::kStages, kTile = gt::kTile;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  gt::Bars* sh = (gt::Bars*)(base + kStages * C::Stage);
+  Bars* sh = (Bars*)(base + kStages * kStage);
   volatile int* abort = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pidx = (int)(blockIdx.x % npairs);
@@ -325,7 +306,8 @@ __global__ void __launch_bounds__(gt::kThreads, 1) k_gram_tc(const double* __res
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(&sh->full[s], 128);
+      mbar_init(&sh->a_full[s], 128);
+      mbar_init(&sh->b_full[s], 1);                     // unused here
       mbar_init(&sh->empty[s], 1);
     }
     for (int t = 0; t < 2; ++t) {
@@ -349,26 +331,13 @@ __global__ void __launch_bounds__(gt::kThreads, 1) k_gram_tc(const double* __res
   if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t id = idesc(2u, 128, 128);
       for (int kc = 0; kc < nkc && !*abort; ++kc) {
         const int s = kc % kStages, buf = kc & 1;
         if (!mbar_wait(&sh->acc_empty[buf], ((kc >> 1) & 1) ^ 1, abort, err)) break;
-        if (!mbar_wait(&sh->full[s], (kc / kStages) & 1, abort, err)) break;
+        if (!mbar_wait(&sh->a_full[s], (kc / kStages) & 1, abort, err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(base + s * C::Stage), b0 = a0 + SL * kTile;
-        const uint32_t d = tmem + (uint32_t)(128 * buf);
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint32_t o = ks * 32;
-          mma_tf32(d, sdesc(a0 + o), sdesc(b0 + o), id, ks > 0 ? 1u : 0u);
-          mma_tf32(d, sdesc(a0 + o), sdesc(b0 + kTile + o), id, 1u);
-          mma_tf32(d, sdesc(a0 + kTile + o), sdesc(b0 + o), id, 1u);
-          if (SL == 3) {
-            mma_tf32(d, sdesc(a0 + o), sdesc(b0 + 2 * kTile + o), id, 1u);
-            mma_tf32(d, sdesc(a0 + kTile + o), sdesc(b0 + kTile + o), id, 1u);
-            mma_tf32(d, sdesc(a0 + 2 * kTile + o), sdesc(b0 + o), id, 1u);
-          }
-        }
+        const uint32_t a0 = smem_u32(base + s * kStage);
+        chunk_mma(tmem + (uint32_t)(128 * buf), a0, a0 + kOperand);
         tc_commit(&sh->empty[s]);
         tc_commit(&sh->acc_full[buf]);
       }
@@ -405,49 +374,30 @@ __global__ void __launch_bounds__(gt::kThreads, 1) k_gram_tc(const double* __res
       for (int kk = 0; kk < 32; ++kk) v[kk] = narrow_f64(raw[kk]);
       if (u + 1 < total) load(u + 1);
       if (isA && !mbar_wait(&sh->empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
-      uint8_t* tile = base + s * C::Stage + (isA ? 0 : SL * kTile);
+      uint8_t* tile = base + s * kStage + (isA ? 0 : kOperand);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         uint32_t s1[4], s2[4], s3[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float f = v[4 * c + e];
-          s1[e] = tf32_rn(f);
-          const float r1 = f - __uint_as_float(s1[e]);
-          s2[e] = tf32_rn(r1);
-          s3[e] = tf32_rn(r1 - __uint_as_float(s2[e]));
-        }
+        for (int e = 0; e < 4; ++e) slices3(v[4 * c + e], s1[e], s2[e], s3[e]);
         const uint32_t off = sw128((uint32_t)(32 * w + lane), (uint32_t)(16 * c));
         *reinterpret_cast<uint4*>(tile + off) = make_uint4(s1[0], s1[1], s1[2], s1[3]);
         *reinterpret_cast<uint4*>(tile + kTile + off) = make_uint4(s2[0], s2[1], s2[2], s2[3]);
-        if (SL == 3) *reinterpret_cast<uint4*>(tile + 2 * kTile + off) = make_uint4(s3[0], s3[1], s3[2], s3[3]);
+        *reinterpret_cast<uint4*>(tile + 2 * kTile + off) = make_uint4(s3[0], s3[1], s3[2], s3[3]);
       }
       if (!isA) {                                      // the stage is complete (A and B written)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&sh->full[s]);
+        mbar_arrive(&sh->a_full[s]);
       }
     }
   } else if (warp >= 6) {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;                             // TMEM lane quadrant
+    const int q = warp & 3;
     float acc[128];
 #pragma unroll
     for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
     bool ok = true;
-    for (int kc = 0; kc < nkc; ++kc) {
-      const int buf = kc & 1;
-      if (!mbar_wait(&sh->acc_full[buf], (kc >> 1) & 1, abort, err)) { ok = false; break; }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int cb = 0; cb < 4; ++cb) {
-        uint32_t r[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(128 * buf + 32 * cb), r);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) acc[32 * cb + j] += __uint_as_float(r[j]);
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&sh->acc_empty[buf]);
-    }
+    for (int kc = 0; kc < nkc && ok; ++kc) ok = drain_chunk(sh, tmem, q, kc, acc, abort, err);
     const int i = 128 * bi + 32 * q + lane;
     if (ok && i < N) {
       float* out = part + sidx * (int64_t)N * N + (int64_t)i * N + 128 * bj;
@@ -485,26 +435,26 @@ static unsigned nblk_tc(int64_t n, int t = 256) { return (unsigned)((n + t - 1) 
 
 // X <- X Z (in place) for N <= 512 with the tensor-core kernel; false when not applicable
 bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {
-  if (N > 512 || N < 1 || M < 1) return false;
+  if (N < 1 || M < 1) return false;
   static bool attr = false;
   if (!attr) {
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_rot_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)rt::smem_bytes()));
+                                          (int)st::smem_bytes()));
     attr = true;
   }
-  const int nkc = (N + 31) / 32, nh = (N + 255) / 256;
-  uint8_t* Bt = (uint8_t*)ws_get(h, "rot_tc_tiles", (size_t)nkc * nh * rt::kBStage);
+  const int nkc = (N + 31) / 32, nt = (N + 127) / 128;
+  uint8_t* Bt = (uint8_t*)ws_get(h, "rot_tc_tiles", (size_t)nkc * nt * st::kOperand);
   double* zd = (double*)ws_get(h, "rot_tc_zd", sizeof(double) * (size_t)N);
   int* err = (int*)ws_get(h, "rot_tc_err", sizeof(int));
   DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
-  DFTFE_LAUNCH(k_rot_tiles, nblk_tc((int64_t)nkc * nh * 256 * 32), 256, 0, h->stream, Z, N, upper ? 1 : 0, nkc, nh,
+  DFTFE_LAUNCH(k_rot_tiles, nblk_tc((int64_t)nkc * nt * 128 * 32), 256, 0, h->stream, Z, N, upper ? 1 : 0, nkc, nt,
                Bt, zd);
   const int64_t ldo = (N + 3) / 4 * 4;
   float* Yo = (float*)ws_get(h, "rot_tc_out", sizeof(float) * (size_t)M * ldo);
   {
     ProfScope ps(h, "rotate_tc");
-    DFTFE_LAUNCH(k_rot_tc, (unsigned)((M + 127) / 128), rt::kThreads, rt::smem_bytes(), h->stream, X, ld, M, N, Bt,
-                 nkc, nh, Yo, ldo, err);
+    DFTFE_LAUNCH(k_rot_tc, (unsigned)(((M + 127) / 128) * nt), st::kThreads, st::smem_bytes(), h->stream, X, ld, M, N,
+                 Bt, nkc, nt, Yo, ldo, err);
   }
   {
     ProfScope ps(h, "rotate_diag");
@@ -525,14 +475,12 @@ namespace dftfe {
 // C (N x N, both triangles) = A^T B with TF32x3 off-diagonal entries and FP64 diagonal
 // (N <= 512); false when not applicable
 bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
-                   double* C, const double* dpart, int nchunk, int slices) {
-  if (N > 512 || N < 1 || M < 1 || (slices != 2 && slices != 3)) return false;
+                   double* C, const double* dpart, int nchunk) {
+  if (N < 1 || M < 1) return false;
   static bool attr = false;
   if (!attr) {
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)gt::Cfg<2>::smem()));
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)gt::Cfg<3>::smem()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)st::smem_bytes()));
     attr = true;
   }
   const int NB = (N + 127) / 128;
@@ -546,12 +494,8 @@ bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, i
   DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
   {
     ProfScope ps(h, "gram_tc");
-    if (slices == 2)
-      DFTFE_LAUNCH(k_gram_tc<2>, (unsigned)(ns * npairs), gt::kThreads, gt::Cfg<2>::smem(), h->stream, A, lda, B,
-                   ldb, M, N, npairs, rows, part, err);
-    else
-      DFTFE_LAUNCH(k_gram_tc<3>, (unsigned)(ns * npairs), gt::kThreads, gt::Cfg<3>::smem(), h->stream, A, lda, B,
-                   ldb, M, N, npairs, rows, part, err);
+    DFTFE_LAUNCH(k_gram_tc, (unsigned)(ns * npairs), st::kThreads, st::smem_bytes(), h->stream, A, lda, B, ldb, M, N,
+                 npairs, rows, part, err);
   }
   DFTFE_LAUNCH(k_gram_tc_reduce, nblk_tc((int64_t)N * N), 256, 0, h->stream, part, (int)ns, dpart, nchunk, N, C);
   int herr = 0;
