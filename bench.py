@@ -33,10 +33,12 @@ import synth  # noqa: E402
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.07 GHz
 # DRAM bytes (read + write) per cell per 128-column tile, from one ncu capture each on a
-# smaller workload with the same per-cell shape (profiles/cell_gemm_*_p6_block128.md);
-# a launch of this workload processes N_c / 8 cells, so traffic scales with the cells.
-DRAM_BYTES_PER_CELL = {"cell_gemm_tf32x3": (349.4e6 + 16.6e6) / 216,
-                       "cell_gemm_fp64": (124.1e6 + 10.2e6) / 64}
+# smaller workload with the same per-cell shape (profiles/cell_gemm_*_p6_block128.md); a
+# launch of this workload processes N_c / 8 cells (FP64, one colour) or all N_c cells
+# (split precision), so traffic scales with the cells.  A kernel that changed since its
+# capture has no entry here (traffic null).
+DRAM_BYTES_PER_CELL = {"cell_gemm_fp64": (124.1e6 + 10.2e6) / 64,
+                       "cell_gemm_tf32x3": (2268.1e6 + 283.4e6) / 1728}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -287,7 +289,8 @@ def run_ours(args, rank, world, local, tdist):
         if key in fam:
             apps = wl.cheb_degree * N / wl.block
             s_h = 8 if p == "tf32x3" else 4                         # hi + lo bytes per matrix entry
-            byt = (Nc * nc * nc * s_h + 3.0 * M * wl.block * 4) * apps
+            # per application: split cell matrices, the X block once, the per-cell products
+            byt = (Nc * nc * nc * s_h + M * wl.block * 4 + Nc * nc * wl.block * 4) * apps
             t = fam[key]["ms"] / 1e3
             a = byt / t / 1e9
             roofs[key] = {"kernel": f"k_cell_mixed<{p}> (tcgen05 split products, FP32 TMEM accumulation)",
@@ -305,6 +308,23 @@ def run_ours(args, rank, world, local, tdist):
                                  "frac": a / (fp32_peak / 12.0),
                                  "peak_source": "derived: FP32 peak 152 SMs x 128 FMA/clk x 2 x 2.07 GHz / 12 "
                                                 "FP32 instructions per float-pair multiply-add"}
+    if "assemble32" in fam:
+        apps = wl.cheb_degree * N / wl.block
+        byt = (Nc * nc * wl.block * 4 + 4.0 * M * wl.block * 4) * apps   # Y^c, X_k, X_k-1 in; Z out
+        a = byt / (fam["assemble32"]["ms"] / 1e3) / 1e9
+        roofs["assemble32"] = {"kernel": "k_assemble32 (sum of cell products + Chebyshev recurrence)", "bound": "hbm",
+                               "achieved": a, "peak": hbm_peak, "unit": "GB/s", "frac": a / hbm_peak,
+                               "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    # tensor work: six TF32 slice products per multiply-add (FP32-equivalent operands)
+    nb = (N + 127) // 128
+    for key, flops, label in (("rotate_tc", 3 * 2.0 * M * N * N * 6, "k_rot_tc (X offdiag(Z), 3-slice TF32, 3 rotations)"),
+                              ("gram_tc", 2 * 2.0 * M * (nb * (nb + 1) / 2) * 128 * 128 * 6,
+                               "k_gram_tc (S, H^ lower 128x128 blocks, 3-slice TF32)")):
+        if key in fam:
+            a = flops / (fam[key]["ms"] / 1e3) / 1e12
+            roofs[key] = {"kernel": label, "bound": "tensor", "achieved": a, "peak": tensor_peak["tf32x3"],
+                          "unit": "TFLOP/s", "frac": a / tensor_peak["tf32x3"],
+                          "peak_source": "measured bf16 sustained x nominal tf32/bf16 (1.1/2.25)"}
     for key, flops, label in (("gram", 2 * M * N * N * 0.5625 * 2, "k_gram_partial (S, H^ lower tiles, FP64)"),
                               ("rotate", 2 * M * N * N * 2.5, "k_rotate (X L^-T, X Q, W Q, FP64)")):
         if key in fam:
@@ -315,14 +335,14 @@ def run_ours(args, rank, world, local, tdist):
     dom = max(timed, key=timed.get) if timed else None
     roofline = dict(roofs[dom]) if dom else None
     if roofline is not None:
-        cells_per_launch = Nc / 8.0
+        cells_per_launch = Nc / 8.0 if dom == "cell_gemm_fp64" else float(Nc)
         per_cell = DRAM_BYTES_PER_CELL.get(dom) if wl.degree == 6 else None
         roofline["traffic"] = per_cell * cells_per_launch * min(N, 128) / 128 if per_cell else None
-        roofline["traffic_note"] = ("DRAM bytes per 128-column launch over N_c/8 cells, scaled from an ncu "
-                                    "capture on a 12^3- or 8^3-cell case" if per_cell else None)
+        roofline["traffic_note"] = ("DRAM bytes per 128-column launch, scaled from an ncu capture on a 12^3- or "
+                                    "8^3-cell case with the same per-cell shape" if per_cell else None)
         if dom.startswith("cell_gemm_") and dom != "cell_gemm_fp64" and dom != "cell_gemm_df":
             s_h = 8 if "tf32" in dom else 4
-            roofline["algorithmic_bytes_per_launch"] = (Nc * nc * nc * s_h + 3.0 * M * 128 * 4) / 8.0
+            roofline["algorithmic_bytes_per_launch"] = Nc * nc * nc * s_h + M * 128 * 4 + Nc * nc * 128 * 4
         roofline["share_of_pass"] = fam[dom]["ms"] / (sec_per_pass * 1e3)
 
     # the downstream step of the pass (Alg. 2 step 3a + Alg. 3): split Rayleigh-Ritz on the
