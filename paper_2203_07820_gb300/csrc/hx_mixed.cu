@@ -20,7 +20,6 @@
 //   warps 2-5   B producers (coalesced gather + split of X^c, 2-stage ring, loads one
 //               chunk ahead)
 //   warps 6-9   epilogue (tcgen05.ld of the accumulators, stores of the rows of Y^c)
-//   warp 10     L2 prefetch of the next cell's X rows
 // Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its
 // own copies and MMAs (bounded), frees its tensor memory and returns.
 #include "internal.h"
@@ -35,8 +34,7 @@ namespace dftfe {
 
 namespace mx {
 
-constexpr int kPrefetchWarp = 10;
-constexpr int kThreads = 352;
+constexpr int kThreads = 320;
 constexpr int kStagesA = 4, kStagesB = 2;
 constexpr int kTile = 16384;                       // one 128-row x 128-byte operand tile
 constexpr int kStageBytes = 2 * kTile;             // hi + lo
@@ -61,7 +59,6 @@ struct Shared {
   uint64_t acc_full, acc_empty[kMaxMTiles], drain;   // acc_empty per 128-column accumulator
   uint32_t tmem;
   int abort;
-  int mma_cell;                                     // cell the MMA lane is working on
 };
 
 template <bool TF32>
@@ -170,7 +167,6 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     for (int t = 0; t < kMaxMTiles; ++t) mbar_init(&sh->acc_empty[t], 128);
     mbar_init(&sh->drain, 1);
     sh->abort = 0;
-    sh->mma_cell = -1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -212,7 +208,6 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
     if (lane == 0) {
       uint32_t ta = 0, tb = 0;
       for (int i = 0; i < my_cells && !*abort; ++i) {
-        *(volatile int*)&sh->mma_cell = i;
         for (int kc = 0; kc < nkc && !*abort; ++kc, ++tb) {
           const int sb = tb % kStagesB;
           if (!mbar_wait(&sh->b_full[sb], (tb / kStagesB) & 1, abort, err)) break;
@@ -288,29 +283,6 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
       }
 #pragma unroll
       for (int j = 0; j < KC; ++j) v[j] = vn[j];
-    }
-  } else if (warp == kPrefetchWarp) {
-    // ------------------------------------------------------------ L2 prefetch
-    {
-      // pull the X rows gathered by the B producers for the next cell into L2 while the
-      // current cell is computed, so the gather does not wait on HBM latency.  The MMA lane
-      // publishes the cell it is working on; prefetching runs one cell ahead of it.
-      const uint32_t xbytes = 4u * (uint32_t)min(128, (int)(ldx - col0));
-      long spins = 0;
-      for (int next = 0; next < my_cells && !*abort;) {
-        if (next > *(volatile int*)&sh->mma_cell + 1) {
-          if (++spins > kSpinLimit) break;
-          __nanosleep(256);
-          continue;
-        }
-        const int64_t cell = cell_of(next);
-        const int32_t* cm = map + cell * nc;
-        for (int k = lane; k < nc; k += 32) {
-          const int64_t g = cm[k];
-          asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(X + g * ldx + col0), "r"(xbytes) : "memory");
-        }
-        ++next;
-      }
     }
   } else {
     // ------------------------------------------------------------ epilogue
