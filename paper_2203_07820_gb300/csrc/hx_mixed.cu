@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh->tmem;
   const int my_cells = ncells > (int)blockIdx.x ? (ncells - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int last_rows8 = ((nc - 128 * (nmt - 1)) + 7) / 8 * 8;   // rows of the last M-tile, in atoms
 
   if (warp == 0) {
     // ------------------------------------------------------------ A producer
@@ -191,10 +192,17 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
             const int s = ta % kStagesA;
             if (!mbar_wait(&sh->a_empty[s], ((ta / kStagesA) & 1) ^ 1, abort, err)) break;
             const uint32_t full = smem_u32(&sh->a_full[s]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(kStageBytes) : "memory");
+            // only the 8-row atoms that hold matrix rows are streamed: the rows of the last
+            // M-tile beyond n_c keep stale data, which only reaches accumulator rows that the
+            // epilogue never stores (row m of a product depends on row m of A alone)
+            const uint32_t bytes = mt == nmt - 1 ? (uint32_t)last_rows8 * 128u : (uint32_t)kTile;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(2 * bytes) : "memory");
             const uint8_t* src = A + (((cell * nkc + kc) * nmt + mt) * 2) * (int64_t)kTile;
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         :: "r"(smem_u32(sA + s * kStageBytes)), "l"(src), "r"(kStageBytes), "r"(full) : "memory");
+                         :: "r"(smem_u32(sA + s * kStageBytes)), "l"(src), "r"(bytes), "r"(full) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_u32(sA + s * kStageBytes + kTile)), "l"(src + kTile), "r"(bytes), "r"(full)
+                         : "memory");
           }
       }
       // drain: every issued copy has landed before the CTA may exit
