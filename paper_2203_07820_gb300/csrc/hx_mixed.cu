@@ -405,45 +405,15 @@ __global__ void __launch_bounds__(256) k_nl_coef32_part(const float* __restrict_
 }
 
 __global__ void k_nl_coef32_reduce(const float* __restrict__ part, const double* __restrict__ hcoup, int nproj,
-                                   int ncol, float* __restrict__ P) {
+                                   int ncol, float* __restrict__ P, int ldP) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= (int64_t)nproj * ncol) return;
   const int a = (int)(t / ncol), col = (int)(t % ncol);
   float s = 0.0f;
   for (int k = 0; k < kNlSplits; ++k) s += part[((int64_t)a * kNlSplits + k) * ncol + col];
-  P[t] = (float)hcoup[a] * s;
+  P[(int64_t)a * ldP + col] = (float)hcoup[a] * s;
 }
 
-__global__ void __launch_bounds__(256) k_nl_add32(float* __restrict__ Z, int64_t ldz, int ncol,
-                                                  const int32_t* __restrict__ snode, const int64_t* __restrict__ srow,
-                                                  const int32_t* __restrict__ sproj, const double* __restrict__ sval,
-                                                  const float* __restrict__ P, int64_t nsup, float alpha) {
-  // one warp per support node and 128-column tile (blockIdx.y); lane l owns columns
-  // 4l..4l+3, so each node row is read and written as one contiguous 512-byte run
-  const int lane = threadIdx.x & 31;
-  const int64_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int c0 = blockIdx.y * 128 + 4 * lane;
-  if (s >= nsup || c0 >= ncol) return;
-  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int64_t t = srow[s]; t < srow[s + 1]; ++t) {
-    const float w = (float)sval[t];
-    const float* p = P + (int64_t)sproj[t] * ncol + c0;
-    acc.x = fmaf(w, p[0], acc.x);
-    if (c0 + 1 < ncol) acc.y = fmaf(w, p[1], acc.y);
-    if (c0 + 2 < ncol) acc.z = fmaf(w, p[2], acc.z);
-    if (c0 + 3 < ncol) acc.w = fmaf(w, p[3], acc.w);
-  }
-  float* z = Z + (int64_t)snode[s] * ldz + c0;
-  float4 o = *reinterpret_cast<float4*>(z);          // in bounds: ldz is a multiple of 32
-  o.x = fmaf(alpha, acc.x, o.x); o.y = fmaf(alpha, acc.y, o.y);
-  o.z = fmaf(alpha, acc.z, o.z); o.w = fmaf(alpha, acc.w, o.w);
-  if (c0 + 3 < ncol) {
-    *reinterpret_cast<float4*>(z) = o;
-  } else {
-    const float v[4] = {o.x, o.y, o.z, o.w};
-    for (int j = 0; c0 + j < ncol; ++j) z[j] = v[j];
-  }
-}
 
 static unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -475,15 +445,19 @@ static uint8_t* mixed_tiles(dftfe_ham h, bool tf32, int* nkc_out, int* nmt_out) 
   return A;
 }
 
-// Assembly of the per-cell products fused with the recurrence:
-//   Z[g] = s1 X[g] + s2 Xp[g] + alpha * sum_{slots (c, l) of node g} Y^c[l]
+// Assembly of the per-cell products fused with the recurrence and the nonlocal term:
+//   Z[g] = s1 X[g] + s2 Xp[g] + alpha (sum_{slots (c, l) of node g} Y^c[l] + sum_t w_t P[a_t])
 // one warp per node, lane l owns columns col0 + 4l .. +3 (float4); the slots of a node are
-// summed in increasing cell order, so the result is deterministic.
+// summed in increasing cell order, so the result is deterministic.  P (nproj x ncol, FP32)
+// (row stride ldP) holds h_a (C~^T X)_a; (a_t, w_t) are the node's projector entries (none off
+// the supports).
 __global__ void __launch_bounds__(256) k_assemble32(float* __restrict__ Z, int64_t ldz, const float* __restrict__ X,
                                                     int64_t ldx, const float* __restrict__ Xp, int64_t ldp,
                                                     const float* __restrict__ Yc, const int32_t* __restrict__ nptr,
-                                                    const int32_t* __restrict__ nslot, int64_t M, int col0, int ncol,
-                                                    float alpha, float s1, float s2) {
+                                                    const int32_t* __restrict__ nslot, const int64_t* __restrict__ nlptr,
+                                                    const int32_t* __restrict__ nlproj, const double* __restrict__ nlval,
+                                                    const float* __restrict__ P, int ldP, int64_t M, int col0,
+                                                    int ncol, float alpha, float s1, float s2) {
   const int lane = threadIdx.x & 31;
   const int64_t g = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int c = col0 + 4 * lane;
@@ -492,6 +466,15 @@ __global__ void __launch_bounds__(256) k_assemble32(float* __restrict__ Z, int64
   for (int t = nptr[g]; t < nptr[g + 1]; ++t) {
     const float4 y = __ldg(reinterpret_cast<const float4*>(Yc + (int64_t)nslot[t] * 128 + 4 * lane));
     acc.x += y.x; acc.y += y.y; acc.z += y.z; acc.w += y.w;
+  }
+  if (nlptr) {
+    for (int64_t t = nlptr[g]; t < nlptr[g + 1]; ++t) {
+      const float w = (float)nlval[t];
+      const float* pa = P + (int64_t)nlproj[t] * ldP + c;      // ldP % 4 == 0, c < ldP
+      const float4 pv = *reinterpret_cast<const float4*>(pa);
+      acc.x = fmaf(w, pv.x, acc.x); acc.y = fmaf(w, pv.y, acc.y);
+      acc.z = fmaf(w, pv.z, acc.z); acc.w = fmaf(w, pv.w, acc.w);
+    }
   }
   const float4 x = *reinterpret_cast<const float4*>(X + g * ldx + c);     // in bounds: ld % 32 == 0
   float4 o = make_float4(fmaf(alpha, acc.x, s1 * x.x), fmaf(alpha, acc.y, s1 * x.y),
@@ -549,6 +532,17 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
   float* Yc = (float*)ws_get(h, "mx_yc", sizeof(float) * (size_t)m->Nc * m->nc * 128);
   const size_t sh = mixed_smem();
   const unsigned grid = (unsigned)std::min<int64_t>(m->Nc, h->sm_count);
+  // nonlocal coefficients P = h (C~^T X) first: the assembly adds C~ P with the cell sums
+  float* P = nullptr;
+  const int ldP = (ncol + 3) / 4 * 4;
+  if (h->nproj > 0) {
+    P = (float*)ws_get(h, "nl_coef32", sizeof(float) * h->nproj * (size_t)ldP);
+    float* Pp = (float*)ws_get(h, "nl_coef32_part", sizeof(float) * h->nproj * (size_t)kNlSplits * ncol);
+    dim3 g1((unsigned)(h->nproj * kNlSplits), (unsigned)((ncol + 127) / 128));
+    DFTFE_LAUNCH(k_nl_coef32_part, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval, Pp);
+    DFTFE_LAUNCH(k_nl_coef32_reduce, nblk((int64_t)h->nproj * ncol), 256, 0, h->stream, Pp, h->d_h, h->nproj,
+                 ncol, P, ldP);
+  }
   for (int col0 = 0; col0 < ncol; col0 += 128) {
     {
       ProfScope ps(h, tf32 ? "cell_gemm_tf32x3" : "cell_gemm_bf16x3");
@@ -561,18 +555,7 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
     }
     ProfScope ps(h, "assemble32");
     DFTFE_LAUNCH(k_assemble32, nblk((m->M + 7) / 8 * 256), 256, 0, h->stream, Z, ldz, X, ldx, Xp, ldp, Yc, nptr, nslot,
-                 m->M, col0, ncol, alpha, s1, s2);
-  }
-  if (h->nproj > 0) {
-    float* P = (float*)ws_get(h, "nl_coef32", sizeof(float) * h->nproj * (size_t)ncol);
-    float* Pp = (float*)ws_get(h, "nl_coef32_part", sizeof(float) * h->nproj * (size_t)kNlSplits * ncol);
-    dim3 g1((unsigned)(h->nproj * kNlSplits), (unsigned)((ncol + 127) / 128));
-    DFTFE_LAUNCH(k_nl_coef32_part, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval, Pp);
-    DFTFE_LAUNCH(k_nl_coef32_reduce, nblk((int64_t)h->nproj * ncol), 256, 0, h->stream, Pp, h->d_h, h->nproj,
-                 ncol, P);
-    dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 127) / 128));
-    DFTFE_LAUNCH(k_nl_add32, g2, 256, 0, h->stream, Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj, h->d_sval, P,
-                 h->nsup, alpha);
+                 P ? h->d_nptr_all : nullptr, h->d_sproj, h->d_sval, P, ldP, m->M, col0, ncol, alpha, s1, s2);
   }
 }
 

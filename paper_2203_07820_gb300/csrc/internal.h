@@ -132,6 +132,7 @@ struct dftfe_ham_s {
   int64_t nsup = 0;
   int32_t* d_snode = nullptr; int64_t* d_srow = nullptr;
   int32_t* d_sproj = nullptr; double* d_sval = nullptr;
+  int64_t* d_nptr_all = nullptr;   // M + 1 offsets of every node's (sproj, sval) entries
   // workspace
   std::map<std::string, dftfe::DevBuf> ws;
   // profiling

@@ -197,8 +197,10 @@ static T* dev_upload(const std::vector<T>& v, cudaStream_t s) {
 static void free_nonlocal(dftfe_ham h) {
   cudaFree(h->d_h); cudaFree(h->d_prow); cudaFree(h->d_pnode); cudaFree(h->d_pval);
   cudaFree(h->d_snode); cudaFree(h->d_srow); cudaFree(h->d_sproj); cudaFree(h->d_sval);
+  cudaFree(h->d_nptr_all);
   h->d_h = nullptr; h->d_prow = nullptr; h->d_pnode = nullptr; h->d_pval = nullptr;
   h->d_snode = nullptr; h->d_srow = nullptr; h->d_sproj = nullptr; h->d_sval = nullptr;
+  h->d_nptr_all = nullptr;
   h->nproj = 0;
   h->nsup = 0;
 }
@@ -486,6 +488,13 @@ extern "C" dftfe_status dftfe_ham_set_nonlocal(dftfe_ham h, int nproj, const dou
                  h->d_mass, nnz);
   h->d_snode = dev_upload(snode, s);
   h->d_srow = dev_upload(srow, s);
+  {
+    // the same node-major entries indexed by every node (empty ranges off the supports)
+    std::vector<int64_t> nall(m->M + 1, 0);
+    for (size_t k = 0; k < snode.size(); ++k) nall[(size_t)snode[k] + 1] = srow[k + 1] - srow[k];
+    for (int64_t g = 0; g < m->M; ++g) nall[g + 1] += nall[g];
+    h->d_nptr_all = dev_upload(nall, s);
+  }
   h->d_sproj = dev_upload(sproj, s);
   int64_t* d_perm = dev_upload(order, s);
   DFTFE_CHECK_CUDA(cudaMalloc(&h->d_sval, sizeof(double) * std::max<int64_t>(nnz, 1)));
