@@ -264,6 +264,41 @@ dftfe_status dftfe_density(dftfe_ham ham, const double* Xo, int64_t ldo, int nco
 #define DFTFE_NOALLOC_MAX_COLS 512
 dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, int ncol, void* stream);
 
+/* ------------------------------------------ learned degree / bounds proposer */
+/* The network that proposes the Chebyshev degree and the unwanted-interval bounds of the
+ * next pass from the last passes' Ritz values, residuals and bounds (a learned replacement
+ * for the Lanczos bound estimate plus a fixed degree, which remain its fallback).  A
+ * three-layer perceptron, FP32:
+ *     h1 = tanh(W1 x + b1), h2 = tanh(W2 h1 + b2), y = W3 h2 + b3,
+ * parameters packed in one device vector: W1 (n_hidden x n_in, row-major), b1,
+ * W2 (n_hidden x n_hidden), b2, W3 (n_out x n_hidden), b3.  Sizes: 1 <= n_in <= 64,
+ * n_hidden in {32, 64, 96, 128}, 1 <= n_out <= 8.  All arrays are device memory, rows of X
+ * and Y are samples (row-major); work is enqueued on `stream` (NULL = legacy default stream).
+ * Nothing here comes from the paper, which fixes the degree from the bounds (Sec. 3.1). */
+
+/* Number of packed parameters, or -1 for non-positive sizes. */
+int64_t dftfe_mlp_param_count(int n_in, int n_hidden, int n_out);
+
+/* Y[n x n_out] = network(X[n x n_in]).  DFTFE_ERR_ARG for sizes out of range or null
+ * pointers (n = 0 is a no-op). */
+dftfe_status dftfe_mlp_forward(const float* params, int n_in, int n_hidden, int n_out, const float* X,
+                               int64_t n, float* Y, void* stream);
+
+/* Training objective L = (1/n) sum_s sum_k w_k (y_sk - t_sk)^2 over the n >= 1 rows of X with
+ * targets T[n x n_out] and per-output weights w[n_out] (NULL = all 1).  Writes L to *loss
+ * (device, may be NULL) and dL/dparams to grad (device, dftfe_mlp_param_count floats), summed
+ * in a fixed order (deterministic).  Uses a stream-ordered temporary of about
+ * 2 x SMs x param_count floats. */
+dftfe_status dftfe_mlp_loss_grad(const float* params, int n_in, int n_hidden, int n_out, const float* X,
+                                 const float* T, const float* w, int64_t n, float* loss, float* grad,
+                                 void* stream);
+
+/* One Adam step (Kingma & Ba 2015) at step number t >= 1 on `count` parameters: moment
+ * estimates m, v (device, zero before the first step) are updated in place, then
+ * params -= lr * mhat / (sqrt(vhat) + eps) with the bias-corrected moments. */
+dftfe_status dftfe_mlp_adam(float* params, const float* grad, float* m, float* v, int64_t count, int t,
+                            float lr, float beta1, float beta2, float eps, void* stream);
+
 /* ------------------------------------------------------------ instrumentation */
 
 /* Per-kernel timing with CUDA events recorded on the ham's stream around every

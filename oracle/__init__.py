@@ -18,6 +18,8 @@ It is a plain, slow, obviously-correct restatement of the paper's method
                   Schmidt, Rayleigh-Ritz, residuals, one pass
   density.py      spectrum-splitting Rayleigh-Ritz, Fermi level,      (Alg. 2 step 3a, Alg. 3)
                   electron density at quadrature points
+  mlp.py          the learned degree/bounds proposer's network:        (no counterpart in the paper)
+                  forward, loss gradient by the chain rule, Adam
 
 Every function is FP64.  Library primitives used as single steps: numpy
 matmul/einsum, numpy.linalg.cholesky/eigh, scipy triangular solve, scipy.sparse
@@ -27,7 +29,8 @@ Pins (tests/test_oracle_*.py) tie it to closed forms and invariants: GLL p=4
 closed form, quadrature exactness, Kronecker-sum spectrum of the free-electron
 operator, harmonic-oscillator levels, scalar Chebyshev identity on exact
 eigenvectors, nonlocal PSD/rank/normalisation, Courant-Fischer, convergence to a
-dense eigensolve.  No function here is "parity unpinned".
+dense eigensolve; for mlp.py, central finite differences, a closed-form linear special
+case and Adam's closed-form first step.  No function here is "parity unpinned".
 """
 from .basis import gll_rule, gauss_rule, lagrange_table, lagrange_deriv_table
 from .mesh import PeriodicMesh

@@ -75,6 +75,9 @@ _SIGS = {
     "dftfe_rayleigh_ritz_split": [_vp, _vp, _i64, _int, _int, _vp, _vp, _i64, _int],
     "dftfe_fermi_level": [_vp, _int, _int, _dbl, _dbl, _vp, C.POINTER(_dbl), _vp],
     "dftfe_density": [_vp, _vp, _i64, _int, _vp, _i64, _int, _vp, _vp],
+    "dftfe_mlp_forward": [_vp, _int, _int, _int, _vp, _i64, _vp, _vp],
+    "dftfe_mlp_loss_grad": [_vp, _int, _int, _int, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
+    "dftfe_mlp_adam": [_vp, _vp, _vp, _vp, _i64, _int, C.c_float, C.c_float, C.c_float, C.c_float, _vp],
     "dftfe_profile_enable": [_vp, _int],
     "dftfe_profile_query": [_vp, C.c_char_p, C.POINTER(_dbl), C.POINTER(_i64)],
 }
@@ -82,6 +85,8 @@ for _name, _args in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = C.c_int
+_lib.dftfe_mlp_param_count.argtypes = [_int, _int, _int]
+_lib.dftfe_mlp_param_count.restype = C.c_int64
 _lib.dftfe_launch_count.argtypes = []
 _lib.dftfe_launch_count.restype = C.c_int64
 _lib.dftfe_last_error.argtypes = []
@@ -251,6 +256,37 @@ def dftfe_rayleigh_ritz_split(ham, X, nfr, evals, Xfr, prec=DFTFE_FP64):
     px, ld = _dev(X, "X")
     pf, ldf = _dev(Xfr, "Xfr")
     _check(_lib.dftfe_rayleigh_ritz_split(ham, px, ld, X.shape[1], int(nfr), _vp(evals.data_ptr()), pf, ldf, prec))
+
+
+def _f32(t, name):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype.itemsize != 4 or not t.dtype.is_floating_point or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA float32 tensor")
+    return _vp(t.data_ptr())
+
+
+def dftfe_mlp_param_count(n_in, n_hidden, n_out):
+    return int(_lib.dftfe_mlp_param_count(int(n_in), int(n_hidden), int(n_out)))
+
+
+def dftfe_mlp_forward(params, shape, X, Y, stream=None):
+    n_in, n_h, n_out = shape
+    _check(_lib.dftfe_mlp_forward(_f32(params, "params"), n_in, n_h, n_out, _f32(X, "X"), X.shape[0],
+                                  _f32(Y, "Y"), _stream(stream)))
+
+
+def dftfe_mlp_loss_grad(params, shape, X, T, w, loss, grad, stream=None):
+    n_in, n_h, n_out = shape
+    _check(_lib.dftfe_mlp_loss_grad(_f32(params, "params"), n_in, n_h, n_out, _f32(X, "X"), _f32(T, "T"),
+                                    _f32(w, "w"), X.shape[0], _f32(loss, "loss"), _f32(grad, "grad"),
+                                    _stream(stream)))
+
+
+def dftfe_mlp_adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(_lib.dftfe_mlp_adam(_f32(params, "params"), _f32(grad, "grad"), _f32(m, "m"), _f32(v, "v"),
+                               params.numel(), int(t), float(lr), float(beta1), float(beta2), float(eps),
+                               _stream(stream)))
 
 
 def dftfe_fermi_level(evals_fr, n_oc, n_elec, kT, f_fr, stream=None):

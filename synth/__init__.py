@@ -205,3 +205,20 @@ def projector_csr(node_xyz, centres, width, cutoff, L):
     if not nodes:
         return np.zeros(1, np.int64), np.zeros(0, np.int64), np.zeros(0)
     return (np.asarray(rowptr, np.int64), np.concatenate(nodes), np.concatenate(vals))
+
+
+def atom_walk(seed, centres, steps, step_len=0.05):
+    """Positions of an SCF-like sequence: at every step each atom moves by `step_len` bohr in a
+    direction drawn uniformly on the sphere (seeded stream); returns steps + 1 arrays (the
+    first is `centres`).  Input generation only: the caller mixes the potentials."""
+    s = Stream(seed)
+    pos = [np.asarray(centres, dtype=np.float64).copy()]
+    for _ in range(steps):
+        nxt = pos[-1].copy()
+        for a in range(nxt.shape[0]):
+            z = 2.0 * s.uniform() - 1.0
+            phi = 2.0 * math.pi * s.uniform()
+            r = math.sqrt(max(0.0, 1.0 - z * z))
+            nxt[a] += step_len * np.array([r * math.cos(phi), r * math.sin(phi), z])
+        pos.append(nxt)
+    return pos
