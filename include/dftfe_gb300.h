@@ -264,6 +264,38 @@ dftfe_status dftfe_density(dftfe_ham ham, const double* Xo, int64_t ldo, int nco
 #define DFTFE_NOALLOC_MAX_COLS 512
 dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, int ncol, void* stream);
 
+/* ------------------------------------------------------------ batched passes */
+/* Several independent systems (Gamma point, FP64) of uneven mesh size, degree, state count
+ * and block size advanced by one ChFSI pass each with shared launches: per Chebyshev step one
+ * launch forms the recurrence terms of every system and one launch per colour runs the cell
+ * products of every system's cells of that colour; the nonlocal term, CholGS and
+ * Rayleigh-Ritz run per system.  Results are bit-identical to dftfe_chfsi_pass on each system
+ * alone (same operations in the same order).  No counterpart in the paper, which runs one
+ * system per job. */
+typedef struct dftfe_batch_s* dftfe_batch;
+
+typedef struct {
+  double* X;            /* device, M x ncol, row stride ld (updated in place) */
+  int64_t ld;
+  int ncol;             /* 1..2048, <= M */
+  int block;            /* filter block size, >= 1 */
+  int degree;           /* Chebyshev degree, >= 0 */
+  dftfe_bounds bounds;  /* in: filter bounds; out: updated as dftfe_chfsi_pass does */
+  double* evals;        /* device, ncol: Ritz values (ascending) */
+  double* resid;        /* device, ncol: residual norms */
+} dftfe_batch_item;
+
+/* Build a batch over nsys (1..4096) distinct Hamiltonians created on one stream; the batch
+ * keeps pointers to them (destroy the batch first).  Potentials may change between passes. */
+dftfe_status dftfe_batch_create(const dftfe_ham* hams, int nsys, dftfe_batch* out);
+
+/* One pass for every system; items[i] belongs to hams[i].  prec must be DFTFE_FP64.
+ * Errors as for dftfe_chfsi_pass (checked for all items before any work). */
+dftfe_status dftfe_batch_chfsi_pass(dftfe_batch batch, dftfe_batch_item* items, dftfe_precision prec);
+
+/* Synchronise the batch's stream and free it (NULL is a no-op). */
+dftfe_status dftfe_batch_destroy(dftfe_batch batch);
+
 /* ------------------------------------------ learned degree / bounds proposer */
 /* The network that proposes the Chebyshev degree and the unwanted-interval bounds of the
  * next pass from the last passes' Ritz values, residuals and bounds (a learned replacement

@@ -75,6 +75,9 @@ _SIGS = {
     "dftfe_rayleigh_ritz_split": [_vp, _vp, _i64, _int, _int, _vp, _vp, _i64, _int],
     "dftfe_fermi_level": [_vp, _int, _int, _dbl, _dbl, _vp, C.POINTER(_dbl), _vp],
     "dftfe_density": [_vp, _vp, _i64, _int, _vp, _i64, _int, _vp, _vp],
+    "dftfe_batch_create": [C.POINTER(_vp), _int, C.POINTER(_vp)],
+    "dftfe_batch_chfsi_pass": [_vp, _vp, _int],
+    "dftfe_batch_destroy": [_vp],
     "dftfe_mlp_forward": [_vp, _int, _int, _int, _vp, _i64, _vp, _vp],
     "dftfe_mlp_loss_grad": [_vp, _int, _int, _int, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "dftfe_mlp_adam": [_vp, _vp, _vp, _vp, _i64, _int, C.c_float, C.c_float, C.c_float, C.c_float, _vp],
@@ -256,6 +259,36 @@ def dftfe_rayleigh_ritz_split(ham, X, nfr, evals, Xfr, prec=DFTFE_FP64):
     px, ld = _dev(X, "X")
     pf, ldf = _dev(Xfr, "Xfr")
     _check(_lib.dftfe_rayleigh_ritz_split(ham, px, ld, X.shape[1], int(nfr), _vp(evals.data_ptr()), pf, ldf, prec))
+
+
+class BatchItem(C.Structure):
+    _fields_ = [("X", _vp), ("ld", _i64), ("ncol", _int), ("block", _int), ("degree", _int),
+                ("bounds", Bounds), ("evals", _vp), ("resid", _vp)]
+
+
+def dftfe_batch_create(hams):
+    arr = (_vp * len(hams))(*hams)
+    out = _vp()
+    _check(_lib.dftfe_batch_create(arr, len(hams), C.byref(out)))
+    return out
+
+
+def dftfe_batch_destroy(batch):
+    _check(_lib.dftfe_batch_destroy(batch))
+
+
+def dftfe_batch_chfsi_pass(batch, Xs, blocks, degrees, bounds, evals, resids, prec=DFTFE_FP64):
+    """One pass for every system of the batch; `bounds` (list of Bounds) are updated in place."""
+    n = len(Xs)
+    items = (BatchItem * n)()
+    for i in range(n):
+        px, ld = _dev(Xs[i], "X")
+        items[i] = BatchItem(px, ld, Xs[i].shape[1], int(blocks[i]), int(degrees[i]), bounds[i],
+                             _vp(evals[i].data_ptr()), _vp(resids[i].data_ptr()))
+    _check(_lib.dftfe_batch_chfsi_pass(batch, C.cast(items, _vp), prec))
+    for i in range(n):
+        bounds[i].a, bounds[i].b, bounds[i].a0 = items[i].bounds.a, items[i].bounds.b, items[i].bounds.a0
+    return bounds
 
 
 def _f32(t, name):

@@ -68,6 +68,29 @@ static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals,
   }
 }
 
+// The pass after the filter (Alg. 2 read as orthonormalise-first): CholGS, Rayleigh-Ritz,
+// residuals, bounds update a <- theta_N, a0 <- theta_1 (a0 kept NaN for the unscaled filter).
+void chfsi_pass_tail(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_bounds* inout, double* evals,
+                     double* resid, dftfe_precision prec) {
+  auto* m = h->mesh;
+  {
+    ProfScope ps(h, "pass_cholgs");
+    cholgs_impl(h, X, ld, ncol, prec != DFTFE_FP64);
+  }
+  double* W = (double*)ws_get(h, "W", sizeof(double) * (size_t)m->M * ncol);
+  {
+    ProfScope ps(h, "pass_rr");
+    rr_impl(h, X, ld, ncol, evals, W, ncol, prec);
+  }
+  residual_norms(h, X, ld, W, ncol, m->M, ncol, evals, resid, 0);
+  double ends[2];
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[0], evals, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[1], evals + ncol - 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  inout->a = ends[1];
+  if (!std::isnan(inout->a0)) inout->a0 = ends[0];
+}
+
 }  // namespace dftfe
 
 using namespace dftfe;
@@ -164,22 +187,7 @@ extern "C" dftfe_status dftfe_chfsi_pass(dftfe_ham h, double* X, int64_t ld, int
       else chebyshev_filter_mixed(h, X + j0, ld, nb, degree, *inout, prec == DFTFE_MIXED_TF32X3);
     }
   }
-  {
-    ProfScope ps(h, "pass_cholgs");
-    cholgs_impl(h, X, ld, ncol, prec != DFTFE_FP64);
-  }
-  double* W = (double*)ws_get(h, "W", sizeof(double) * (size_t)m->M * ncol);
-  {
-    ProfScope ps(h, "pass_rr");
-    rr_impl(h, X, ld, ncol, evals, W, ncol, prec);
-  }
-  residual_norms(h, X, ld, W, ncol, m->M, ncol, evals, resid, 0);
-  double ends[2];
-  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[0], evals, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[1], evals + ncol - 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
-  inout->a = ends[1];
-  if (!std::isnan(inout->a0)) inout->a0 = ends[0];
+  chfsi_pass_tail(h, X, ld, ncol, inout, evals, resid, prec);
   ABI_END
 }
 

@@ -1,0 +1,292 @@
+// Batched ChFSI passes (FP64, Gamma point): independent systems of uneven mesh size, degree,
+// state count and block size filtered with shared launches.  Per Chebyshev step one launch
+// forms s1 X_k + s2 X_{k-1} for every system, and one launch per colour runs the cell
+// products of every system's cells of that colour (a work list of (system, cell) pairs built
+// once); the nonlocal term is added per system.  The orthonormalisation and Rayleigh-Ritz
+// steps then run per system.  Each system's arithmetic, and its order, is that of a single
+// pass (the cell body is shared with the per-colour kernel), so the results are bit-identical
+// to passes run one system at a time; the gain is fewer, fuller launches for small systems.
+#include "internal.h"
+#include "cell_fp64.cuh"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <vector>
+
+struct dftfe_batch_s {
+  std::vector<dftfe_ham> hams;
+  cudaStream_t stream = nullptr;
+  int ncolours = 0;                         // most colours of any system
+  std::vector<int64_t> work_off;            // per colour: range in the work list
+  int32_t* d_wsys = nullptr;                // work list: system of each item
+  int32_t* d_wcell = nullptr;               // work list: cell of each item
+  int nc_max = 0;
+  void* d_steps = nullptr;                  // per-step system descriptors
+  size_t steps_bytes = 0;
+};
+
+namespace dftfe {
+
+namespace bt {
+struct SysStep {
+  const double* Hc;
+  const int32_t* map;
+  const double* X;
+  const double* Xp;
+  double* Z;
+  int64_t ldx, ldp, ldz, M;
+  int nc, ncol, active;
+  double alpha, s1, s2;
+};
+}  // namespace bt
+
+// Z = s1 X + s2 Xp for every active system (blockIdx.y = system); the same operations in the
+// same order as the single-system k_axpby_init
+__global__ void k_batch_axpby(const bt::SysStep* __restrict__ st) {
+  const bt::SysStep& d = st[blockIdx.y];
+  if (!d.active) return;
+  const int64_t n = d.M * d.ncol;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / d.ncol;
+    const int j = (int)(t - i * d.ncol);
+    double v = 0.0;
+    if (d.s1 != 0.0) v = d.s1 * d.X[i * d.ldx + j];
+    if (d.Xp) v += d.s2 * d.Xp[i * d.ldp + j];
+    d.Z[i * d.ldz + j] = v;
+  }
+}
+
+// one CTA per (work item of this colour, 32-column tile)
+__global__ void __launch_bounds__(256, 2) k_batch_cell(const bt::SysStep* __restrict__ st,
+                                                       const int32_t* __restrict__ wsys,
+                                                       const int32_t* __restrict__ wcell) {
+  extern __shared__ double smem[];
+  const bt::SysStep& d = st[wsys[blockIdx.x]];
+  if (!d.active || (int)blockIdx.y * 32 >= d.ncol) return;
+  cell_fp64_wide_body(d.Hc, d.map, wcell[blockIdx.x], d.nc, d.X, d.ldx, d.Z, d.ldz, d.ncol, d.alpha,
+                      (int)blockIdx.y, smem);
+}
+
+// Chebyshev coefficients of step k (1-based) for bounds b, as the single-system filter forms
+// them; sigma carries the scaled recurrence's state
+static void cheb_coef(const dftfe_bounds& b, int k, double& sigma, double& alpha, double& s1, double& s2) {
+  const double e = (b.b - b.a) / 2.0, c = (b.b + b.a) / 2.0;
+  const bool scaled = !std::isnan(b.a0);
+  s2 = 0.0;
+  if (k == 1) {
+    sigma = scaled ? e / (b.a0 - c) : 0.0;
+    alpha = scaled ? sigma / e : 1.0 / e;
+    s1 = -c * alpha;
+  } else if (scaled) {
+    const double sigma1 = e / (b.a0 - c), gamma = 2.0 / sigma1;
+    const double sigma2 = 1.0 / (gamma - sigma);
+    alpha = 2.0 * sigma2 / e;
+    s1 = -c * alpha;
+    s2 = -sigma * sigma2;
+    sigma = sigma2;
+  } else {
+    alpha = 2.0 / e;
+    s1 = -c * alpha;
+    s2 = -1.0;
+  }
+}
+
+static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
+  const int ns = (int)bt->hams.size();
+  int rounds = 0, maxdeg = 0;
+  for (int s = 0; s < ns; ++s) {
+    rounds = std::max(rounds, (items[s].ncol + items[s].block - 1) / items[s].block);
+    maxdeg = std::max(maxdeg, items[s].degree);
+  }
+  const size_t need = sizeof(bt::SysStep) * (size_t)std::max(maxdeg, 1) * ns;
+  if (need > bt->steps_bytes) {
+    if (bt->d_steps) DFTFE_CHECK_CUDA(cudaFree(bt->d_steps));
+    bt->d_steps = nullptr;
+    DFTFE_CHECK_CUDA(cudaMalloc(&bt->d_steps, need));
+    bt->steps_bytes = need;
+  }
+  bt::SysStep* dsteps = (bt::SysStep*)bt->d_steps;
+  const size_t sh = (size_t)bt->nc_max * 32 * sizeof(double) + bt->nc_max * sizeof(int32_t);
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_batch_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  for (int j = 0; j < rounds; ++j) {
+    // per system: block j of its columns, three rotating buffers, the step descriptors
+    std::vector<bt::SysStep> host((size_t)std::max(maxdeg, 1) * ns);
+    std::vector<int> cur(ns, 0), prev(ns, -1), nb(ns, 0), tiles(ns, 0);
+    std::vector<std::array<double*, 3>> buf(ns);
+    std::vector<std::array<int64_t, 3>> lds(ns);
+    int maxtiles = 0;
+    std::vector<int> alone;                       // blocks of at most 4 columns: narrow kernel
+    for (int s = 0; s < ns; ++s) {
+      dftfe_ham h = bt->hams[s];
+      nb[s] = std::min(items[s].block, items[s].ncol - j * items[s].block);
+      if (nb[s] <= 0 || items[s].degree <= 0) { nb[s] = 0; continue; }
+      if (nb[s] <= 4) {
+        alone.push_back(s);
+        nb[s] = 0;
+        continue;
+      }
+      double* w1 = (double*)ws_get(h, "cheb_w1", sizeof(double) * h->mesh->M * (size_t)nb[s]);
+      double* w2 = (double*)ws_get(h, "cheb_w2", sizeof(double) * h->mesh->M * (size_t)nb[s]);
+      buf[s] = {items[s].X + (int64_t)j * items[s].block, w1, w2};
+      lds[s] = {items[s].ld, nb[s], nb[s]};
+      tiles[s] = (nb[s] + 31) / 32;
+      maxtiles = std::max(maxtiles, tiles[s]);
+    }
+    std::vector<double> sigma(ns, 0.0);
+    for (int k = 1; k <= maxdeg; ++k)
+      for (int s = 0; s < ns; ++s) {
+        bt::SysStep& d = host[(size_t)(k - 1) * ns + s];
+        d = bt::SysStep{};
+        if (nb[s] == 0 || k > items[s].degree) continue;
+        dftfe_ham h = bt->hams[s];
+        int out = 0;
+        while (out == cur[s] || out == prev[s]) ++out;
+        double alpha, s1, s2;
+        cheb_coef(items[s].bounds, k, sigma[s], alpha, s1, s2);
+        d.Hc = h->d_Hc;
+        d.map = h->d_map;
+        d.X = buf[s][cur[s]];
+        d.ldx = lds[s][cur[s]];
+        d.Xp = prev[s] >= 0 ? buf[s][prev[s]] : nullptr;
+        d.ldp = prev[s] >= 0 ? lds[s][prev[s]] : 0;
+        d.Z = buf[s][out];
+        d.ldz = lds[s][out];
+        d.M = h->mesh->M;
+        d.nc = h->mesh->nc;
+        d.ncol = nb[s];
+        d.active = 1;
+        d.alpha = alpha;
+        d.s1 = s1;
+        d.s2 = s2;
+        prev[s] = cur[s];
+        cur[s] = out;
+      }
+    DFTFE_CHECK_CUDA(cudaMemcpyAsync(dsteps, host.data(), sizeof(bt::SysStep) * host.size(), cudaMemcpyHostToDevice,
+                                     bt->stream));
+    int64_t maxwork = 0;
+    for (int s = 0; s < ns; ++s) maxwork = std::max<int64_t>(maxwork, bt->hams[s]->mesh->M * nb[s]);
+    for (int k = 1; k <= maxdeg; ++k) {
+      const bt::SysStep* dk = dsteps + (size_t)(k - 1) * ns;
+      const unsigned gx = (unsigned)std::min<int64_t>((maxwork + 255) / 256, 4096);
+      DFTFE_LAUNCH(k_batch_axpby, dim3(std::max(gx, 1u), (unsigned)ns), 256, 0, bt->stream, dk);
+      for (int s = 0; s < ns; ++s) {
+        const bt::SysStep& d = host[(size_t)(k - 1) * ns + s];
+        if (d.active) nonlocal_add_fp64(bt->hams[s], d.X, d.ldx, d.Z, d.ldz, d.ncol, d.alpha);
+      }
+      for (int c = 0; c < bt->ncolours; ++c) {
+        const int64_t n = bt->work_off[c + 1] - bt->work_off[c];
+        if (n == 0 || maxtiles == 0) continue;
+        ProfScope ps(bt->hams[0], "batch_cell");
+        DFTFE_LAUNCH(k_batch_cell, dim3((unsigned)n, (unsigned)maxtiles), 256, sh, bt->stream, dk,
+                     bt->d_wsys + bt->work_off[c], bt->d_wcell + bt->work_off[c]);
+      }
+    }
+    for (int s = 0; s < ns; ++s)
+      if (nb[s] > 0 && cur[s] != 0)
+        copy_block(bt->stream, buf[s][cur[s]], lds[s][cur[s]], buf[s][0], lds[s][0], bt->hams[s]->mesh->M, nb[s]);
+    for (int s : alone) {
+      const int n = std::min(items[s].block, items[s].ncol - j * items[s].block);
+      chebyshev_filter(bt->hams[s], items[s].X + (int64_t)j * items[s].block, items[s].ld, n, items[s].degree,
+                       items[s].bounds);
+    }
+    // the host descriptors must outlive the copy above: wait before they go out of scope
+    DFTFE_CHECK_CUDA(cudaStreamSynchronize(bt->stream));
+  }
+}
+
+}  // namespace dftfe
+
+using namespace dftfe;
+
+extern "C" dftfe_status dftfe_batch_create(const dftfe_ham* hams, int nsys, dftfe_batch* out) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(hams && out && nsys >= 1 && nsys <= 4096, "need 1..4096 Hamiltonians");
+  cudaStream_t s = hams[0] ? hams[0]->stream : nullptr;
+  for (int i = 0; i < nsys; ++i) {
+    DFTFE_REQUIRE(hams[i], "null Hamiltonian");
+    DFTFE_REQUIRE(hams[i]->stream == s, "all Hamiltonians of a batch must use one stream");
+    for (int j = 0; j < i; ++j) DFTFE_REQUIRE(hams[j] != hams[i], "a Hamiltonian appears twice");
+  }
+  auto* b = new dftfe_batch_s();
+  try {
+    b->hams.assign(hams, hams + nsys);
+    b->stream = s;
+    for (auto h : b->hams) {
+      b->ncolours = std::max(b->ncolours, h->ncolours);
+      b->nc_max = std::max(b->nc_max, h->mesh->nc);
+    }
+    // work list: colour by colour, the cells of every system with that colour
+    std::vector<int32_t> wsys, wcell;
+    b->work_off.assign(1, 0);
+    std::vector<std::vector<int32_t>> cells(nsys);
+    for (int i = 0; i < nsys; ++i) {
+      auto h = b->hams[i];
+      cells[i].resize(h->colour_off.back());
+      if (!cells[i].empty())
+        DFTFE_CHECK_CUDA(cudaMemcpy(cells[i].data(), h->d_colour_cells, sizeof(int32_t) * cells[i].size(),
+                                    cudaMemcpyDeviceToHost));
+    }
+    for (int c = 0; c < b->ncolours; ++c) {
+      for (int i = 0; i < nsys; ++i) {
+        auto h = b->hams[i];
+        if (c >= h->ncolours) continue;
+        for (int64_t t = h->colour_off[c]; t < h->colour_off[c + 1]; ++t) {
+          wsys.push_back(i);
+          wcell.push_back(cells[i][t]);
+        }
+      }
+      b->work_off.push_back((int64_t)wsys.size());
+    }
+    DFTFE_CHECK_CUDA(cudaMalloc(&b->d_wsys, sizeof(int32_t) * std::max<size_t>(wsys.size(), 1)));
+    DFTFE_CHECK_CUDA(cudaMalloc(&b->d_wcell, sizeof(int32_t) * std::max<size_t>(wcell.size(), 1)));
+    if (!wsys.empty()) {
+      DFTFE_CHECK_CUDA(cudaMemcpy(b->d_wsys, wsys.data(), sizeof(int32_t) * wsys.size(), cudaMemcpyHostToDevice));
+      DFTFE_CHECK_CUDA(cudaMemcpy(b->d_wcell, wcell.data(), sizeof(int32_t) * wcell.size(), cudaMemcpyHostToDevice));
+    }
+  } catch (...) {
+    cudaFree(b->d_wsys);
+    cudaFree(b->d_wcell);
+    delete b;
+    throw;
+  }
+  *out = b;
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_batch_destroy(dftfe_batch b) {
+  ABI_BEGIN
+  if (!b) return DFTFE_OK;
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(b->stream));
+  cudaFree(b->d_wsys);
+  cudaFree(b->d_wcell);
+  cudaFree(b->d_steps);
+  delete b;
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_batch_chfsi_pass(dftfe_batch b, dftfe_batch_item* items, dftfe_precision prec) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(b && items, "null argument");
+  DFTFE_REQUIRE(prec == DFTFE_FP64, "batched passes are FP64");
+  const int ns = (int)b->hams.size();
+  for (int s = 0; s < ns; ++s) {
+    const dftfe_batch_item& it = items[s];
+    dftfe_ham h = b->hams[s];
+    DFTFE_REQUIRE(it.X && it.evals && it.resid, "null array in a batch item");
+    DFTFE_REQUIRE(it.ncol >= 1 && it.ncol <= 2048 && it.ld >= it.ncol && it.block >= 1 && it.degree >= 0,
+                  "bad sizes in a batch item");
+    DFTFE_REQUIRE(it.ncol <= h->mesh->M, "more columns than DoFs");
+    DFTFE_REQUIRE(it.bounds.b > it.bounds.a, "need b > a");
+    DFTFE_REQUIRE(std::isnan(it.bounds.a0) || it.bounds.a0 < it.bounds.a, "need a0 < a for the scaled filter");
+    if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  }
+  {
+    ProfScope ps(b->hams[0], "batch_filter");
+    batch_filter(b, items);
+  }
+  for (int s = 0; s < ns; ++s)
+    chfsi_pass_tail(b->hams[s], items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
+                    items[s].resid, prec);
+  ABI_END
+}

@@ -12,6 +12,7 @@
 // The recurrence (Eq. chebyfilter) is fused: the output is initialised to
 // s1 X_k + s2 X_{k-1} and the local and nonlocal parts accumulate alpha H~ X_k on top.
 #include "internal.h"
+#include "cell_fp64.cuh"
 
 #include <cmath>
 
@@ -83,55 +84,14 @@ __global__ void __launch_bounds__(256) k_nl_add(double* __restrict__ Z, int64_t 
   Z[(int64_t)snode[s] * ldz + col] += alpha * acc;
 }
 
-// Local part, wide form: one CTA = one cell x 32 columns, 8 warps; each warp owns rows
-// r0..r0+7 of H~^c in turn (lanes = columns).  H~^c rows are read as warp-uniform loads.
-constexpr int CW_ROWS = 8;
+// Local part, wide form: one CTA = one cell x 32 columns (the body is shared with the batched
+// kernel, see cell_fp64.cuh).
 __global__ void __launch_bounds__(256, 2) k_cell_fp64_wide(
     const double* __restrict__ Hc, const int32_t* __restrict__ map,
     const int32_t* __restrict__ cells, int nc, const double* __restrict__ X, int64_t ldx,
     double* __restrict__ Z, int64_t ldz, int ncol, double alpha) {
   extern __shared__ double smem[];
-  double* xs = smem;                          // nc x 32
-  int32_t* sm = (int32_t*)(smem + nc * 32);   // nc
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t cell = cells[blockIdx.x];
-  const int col = blockIdx.y * 32 + lane;
-  const bool colok = col < ncol;
-  const int32_t* m = map + cell * nc;
-  for (int k = threadIdx.x; k < nc; k += 256) sm[k] = m[k];
-  __syncthreads();
-  for (int k = warp; k < nc; k += 8) xs[k * 32 + lane] = colok ? X[(int64_t)sm[k] * ldx + col] : 0.0;
-  __syncthreads();
-  const double* H = Hc + cell * (int64_t)nc * nc;
-  for (int r0 = warp * CW_ROWS; r0 < nc; r0 += 8 * CW_ROWS) {
-    const int nr = min(CW_ROWS, nc - r0);
-    double acc[CW_ROWS];
-#pragma unroll
-    for (int i = 0; i < CW_ROWS; ++i) acc[i] = 0.0;
-    const double* Hr = H + (int64_t)r0 * nc;
-    if (nr == CW_ROWS) {
-      for (int k = 0; k < nc; ++k) {
-        const double x = xs[k * 32 + lane];
-#pragma unroll
-        for (int i = 0; i < CW_ROWS; ++i) acc[i] = fma(__ldg(Hr + (int64_t)i * nc + k), x, acc[i]);
-      }
-    } else {
-      for (int k = 0; k < nc; ++k) {
-        const double x = xs[k * 32 + lane];
-#pragma unroll
-        for (int i = 0; i < CW_ROWS; ++i)
-          if (i < nr) acc[i] = fma(__ldg(Hr + (int64_t)i * nc + k), x, acc[i]);
-      }
-    }
-    if (colok) {
-#pragma unroll
-      for (int i = 0; i < CW_ROWS; ++i)
-        if (i < nr) {
-          double* z = Z + (int64_t)sm[r0 + i] * ldz + col;
-          *z += alpha * acc[i];
-        }
-    }
-  }
+  cell_fp64_wide_body(Hc, map, cells[blockIdx.x], nc, X, ldx, Z, ldz, ncol, alpha, (int)blockIdx.y, smem);
 }
 
 // Local part, narrow form (ncol <= 4): one CTA = one cell; each warp reduces whole rows
@@ -219,6 +179,17 @@ static void set_smem_attrs() {
   g_attr_set = true;
 }
 
+// Z += alpha H~_nl X (FP64), nothing without projectors
+void nonlocal_add_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol, double alpha) {
+  if (h->nproj <= 0) return;
+  double* P = (double*)ws_get(h, "nl_coef", sizeof(double) * h->nproj * (size_t)ncol);
+  dim3 g1((unsigned)h->nproj, (unsigned)((ncol + 31) / 32));
+  DFTFE_LAUNCH(k_nl_coef, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval, h->d_h, P);
+  dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
+  DFTFE_LAUNCH(k_nl_add, g2, 256, 0, h->stream, Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj, h->d_sval, P,
+               h->nsup, alpha);
+}
+
 void apply_combo(dftfe_ham h, const double* X, int64_t ldx, const double* Xprev, int64_t ldp,
                  double* Z, int64_t ldz, int ncol, double alpha, double s1, double s2) {
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential before applying H");
@@ -227,15 +198,7 @@ void apply_combo(dftfe_ham h, const double* X, int64_t ldx, const double* Xprev,
   set_smem_attrs();
   DFTFE_LAUNCH(k_axpby_init, nblk(m->M * ncol), 256, 0, h->stream, Z, ldz, X, ldx, Xprev, ldp, m->M,
                ncol, s1, s2);
-  if (h->nproj > 0) {
-    double* P = (double*)ws_get(h, "nl_coef", sizeof(double) * h->nproj * (size_t)ncol);
-    dim3 g1((unsigned)h->nproj, (unsigned)((ncol + 31) / 32));
-    DFTFE_LAUNCH(k_nl_coef, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, h->d_pval,
-                 h->d_h, P);
-    dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
-    DFTFE_LAUNCH(k_nl_add, g2, 256, 0, h->stream, Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj,
-                 h->d_sval, P, h->nsup, alpha);
-  }
+  nonlocal_add_fp64(h, X, ldx, Z, ldz, ncol, alpha);
   local_part(h, X, ldx, Z, ldz, ncol, alpha);
 }
 

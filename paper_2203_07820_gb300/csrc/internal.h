@@ -177,6 +177,11 @@ void rotate_inplace_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, 
 // X <- X Z with the offdiagonal of Z as FP32-equivalent tensor-core products and its
 // diagonal in FP64; false when not applicable
 bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper);
+// the pass after its filter: CholGS, Rayleigh-Ritz, residuals, bounds update
+void chfsi_pass_tail(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_bounds* inout, double* evals,
+                     double* resid, dftfe_precision prec);
+// Z += alpha H~_nl X in FP64 (no-op without projectors)
+void nonlocal_add_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol, double alpha);
 // C = A^T B (both triangles) with FP32-equivalent tensor-core off-diagonal entries and the
 // FP64 diagonal from column-dot partials dpart[nchunk][N]; false when not applicable
 bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,

@@ -1,0 +1,135 @@
+"""Batched passes over independent systems of uneven mesh size, degree, state count and block
+size: every system's result must be bit-identical to a pass of that system alone (same
+operations in the same order), over two consecutive passes; a timing comparison on sixteen
+small systems is printed."""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from systems import gpu_system, small_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# (seed, cells, p, L, nonlocal, states, block, degree, scaled)
+SYSTEMS = [
+    (0, (3, 3, 3), 4, 6.0, True, 20, 8, 9, True),      # last block of 4: narrow kernel alone
+    (1, (4, 3, 2), 4, 8.0, False, 24, 24, 12, False),
+    (2, (2, 2, 3), 6, 7.0, True, 37, 16, 7, True),
+    (3, (4, 4, 4), 3, 8.0, False, 16, 7, 10, True),
+    (4, (2, 3, 2), 5, 6.0, True, 30, 30, 0, True),      # degree 0: no filter
+]
+
+
+def _make(dg, spec):
+    seed, n, p, L, nl, N, block, deg, scaled = spec
+    c = small_case(seed, n=n, p=p, L=L, nl=nl)
+    mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    M = dg.dftfe_mesh_info(mesh)[0]
+    X = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    dg.dftfe_random_uniform(X, 100 + seed)
+    bd = dg.dftfe_spectrum_bounds(ham, 20, 7 + seed, N)
+    if not scaled:
+        bd = dg.make_bounds(bd.a, bd.b)
+    return mesh, ham, X, bd, block, deg
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_07820_gb300 as dg
+    return dg
+
+
+def test_batched_passes_are_bit_identical_to_single_passes(dg):
+    made = [_make(dg, s) for s in SYSTEMS]
+    hams = [m[1] for m in made]
+    batch = dg.dftfe_batch_create(hams)
+    try:
+        Xb = [m[2].clone() for m in made]
+        Xs = [m[2].clone() for m in made]
+        bb = [dg.make_bounds(m[3].a, m[3].b, m[3].a0) for m in made]
+        bs = [dg.make_bounds(m[3].a, m[3].b, m[3].a0) for m in made]
+        evb = [torch.empty(x.shape[1], dtype=torch.float64, device="cuda") for x in Xb]
+        rsb = [torch.empty_like(e) for e in evb]
+        evs = [torch.empty_like(e) for e in evb]
+        rss = [torch.empty_like(e) for e in evb]
+        blocks = [m[4] for m in made]
+        degs = [m[5] for m in made]
+        for _ in range(2):
+            dg.dftfe_batch_chfsi_pass(batch, Xb, blocks, degs, bb, evb, rsb)
+            for i, (mesh, ham, _, _, block, deg) in enumerate(made):
+                dg.dftfe_chfsi_pass(ham, Xs[i], block, deg, bs[i], evs[i], rss[i])
+            torch.cuda.synchronize()
+            for i in range(len(made)):
+                assert torch.equal(Xb[i], Xs[i]), i
+                assert torch.equal(evb[i], evs[i]) and torch.equal(rsb[i], rss[i]), i
+                for f in ("a", "b", "a0"):
+                    x, y = getattr(bb[i], f), getattr(bs[i], f)
+                    assert x == y or (math.isnan(x) and math.isnan(y)), (i, f)
+    finally:
+        dg.dftfe_batch_destroy(batch)
+        for mesh, ham, *_ in made:
+            dg.dftfe_ham_destroy(ham)
+            dg.dftfe_mesh_destroy(mesh)
+
+
+def test_batch_rejects_bad_input(dg):
+    spec = SYSTEMS[1]
+    mesh, ham, X, bd, block, deg = _make(dg, spec)
+    try:
+        with pytest.raises(dg.DftfeError):
+            dg.dftfe_batch_create([ham, ham])                      # duplicate
+        batch = dg.dftfe_batch_create([ham])
+        ev = torch.empty(X.shape[1], dtype=torch.float64, device="cuda")
+        rs = torch.empty_like(ev)
+        with pytest.raises(dg.DftfeError):
+            dg.dftfe_batch_chfsi_pass(batch, [X], [block], [deg], [dg.make_bounds(bd.b, bd.a)], [ev], [rs])
+        with pytest.raises(dg.DftfeError):
+            dg.dftfe_batch_chfsi_pass(batch, [X], [block], [deg], [bd], [ev], [rs], prec=2)
+        dg.dftfe_batch_destroy(batch)
+    finally:
+        dg.dftfe_ham_destroy(ham)
+        dg.dftfe_mesh_destroy(mesh)
+
+
+def test_batch_of_sixteen_small_systems_timing(dg, capsys):
+    specs = []
+    for i in range(16):
+        n = (3 + i % 3, 3 + (i // 3) % 3, 3 + (i // 9) % 2)
+        specs.append((i, n, 4 + i % 3, 6.0 + n[0], i % 2 == 0, 16 + 8 * (i % 4), 16, 20 + 4 * (i % 6), True))
+    made = [_make(dg, s) for s in specs]
+    batch = dg.dftfe_batch_create([m[1] for m in made])
+    try:
+        def run(batched):
+            Xs = [m[2].clone() for m in made]
+            bds = [dg.make_bounds(m[3].a, m[3].b, m[3].a0) for m in made]
+            evs = [torch.empty(x.shape[1], dtype=torch.float64, device="cuda") for x in Xs]
+            rss = [torch.empty_like(e) for e in evs]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if batched:
+                dg.dftfe_batch_chfsi_pass(batch, Xs, [m[4] for m in made], [m[5] for m in made], bds, evs, rss)
+            else:
+                for i, m in enumerate(made):
+                    dg.dftfe_chfsi_pass(m[1], Xs[i], m[4], m[5], bds[i], evs[i], rss[i])
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, Xs
+        run(True), run(False)                                   # warm-up
+        tb, xb = run(True)
+        ts, xs = run(False)
+        assert all(torch.equal(a, b) for a, b in zip(xb, xs))
+        with capsys.disabled():
+            print(f"\n16 systems ({sum(m[2].shape[0] for m in made)} DoFs in all): batched pass {tb * 1e3:.1f} ms, "
+                  f"one by one {ts * 1e3:.1f} ms")
+    finally:
+        dg.dftfe_batch_destroy(batch)
+        for mesh, ham, *_ in made:
+            dg.dftfe_ham_destroy(ham)
+            dg.dftfe_mesh_destroy(mesh)
