@@ -57,15 +57,16 @@ __global__ void k_batch_axpby(const bt::SysStep* __restrict__ st) {
   }
 }
 
-// one CTA per (work item of this colour, 32-column tile)
+// one CTA per (work item of this colour, 32-column tile, range of 64-row groups)
 __global__ void __launch_bounds__(256, 2) k_batch_cell(const bt::SysStep* __restrict__ st,
                                                        const int32_t* __restrict__ wsys,
-                                                       const int32_t* __restrict__ wcell) {
+                                                       const int32_t* __restrict__ wcell, int rows_per_split) {
   extern __shared__ double smem[];
   const bt::SysStep& d = st[wsys[blockIdx.x]];
-  if (!d.active || (int)blockIdx.y * 32 >= d.ncol) return;
+  const int rbeg = (int)blockIdx.z * rows_per_split;
+  if (!d.active || (int)blockIdx.y * 32 >= d.ncol || rbeg >= d.nc) return;
   cell_fp64_wide_body(d.Hc, d.map, wcell[blockIdx.x], d.nc, d.X, d.ldx, d.Z, d.ldz, d.ncol, d.alpha,
-                      (int)blockIdx.y, smem);
+                      (int)blockIdx.y, rbeg, min(d.nc, rbeg + rows_per_split), smem);
 }
 
 // Chebyshev coefficients of step k (1-based) for bounds b, as the single-system filter forms
@@ -178,8 +179,10 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
         const int64_t n = bt->work_off[c + 1] - bt->work_off[c];
         if (n == 0 || maxtiles == 0) continue;
         ProfScope ps(bt->hams[0], "batch_cell");
-        DFTFE_LAUNCH(k_batch_cell, dim3((unsigned)n, (unsigned)maxtiles), 256, sh, bt->stream, dk,
-                     bt->d_wsys + bt->work_off[c], bt->d_wcell + bt->work_off[c]);
+        const int splits = fp64_row_splits(bt->hams[0], n * maxtiles, bt->nc_max);
+        const int rows = ((bt->nc_max + splits - 1) / splits + 63) / 64 * 64;
+        DFTFE_LAUNCH(k_batch_cell, dim3((unsigned)n, (unsigned)maxtiles, (unsigned)((bt->nc_max + rows - 1) / rows)), 256,
+                     sh, bt->stream, dk, bt->d_wsys + bt->work_off[c], bt->d_wcell + bt->work_off[c], rows);
       }
     }
     for (int s = 0; s < ns; ++s)

@@ -89,9 +89,12 @@ __global__ void __launch_bounds__(256) k_nl_add(double* __restrict__ Z, int64_t 
 __global__ void __launch_bounds__(256, 2) k_cell_fp64_wide(
     const double* __restrict__ Hc, const int32_t* __restrict__ map,
     const int32_t* __restrict__ cells, int nc, const double* __restrict__ X, int64_t ldx,
-    double* __restrict__ Z, int64_t ldz, int ncol, double alpha) {
+    double* __restrict__ Z, int64_t ldz, int ncol, double alpha, int rows_per_split) {
   extern __shared__ double smem[];
-  cell_fp64_wide_body(Hc, map, cells[blockIdx.x], nc, X, ldx, Z, ldz, ncol, alpha, (int)blockIdx.y, smem);
+  // blockIdx.z: a range of rows_per_split rows of the cell (a multiple of 64)
+  const int rbeg = (int)blockIdx.z * rows_per_split;
+  cell_fp64_wide_body(Hc, map, cells[blockIdx.x], nc, X, ldx, Z, ldz, ncol, alpha, (int)blockIdx.y, rbeg,
+                      min(nc, rbeg + rows_per_split), smem);
 }
 
 // Local part, narrow form (ncol <= 4): one CTA = one cell; each warp reduces whole rows
@@ -143,6 +146,14 @@ void copy_block(cudaStream_t s, const double* src, int64_t lds, double* dst, int
   DFTFE_LAUNCH(k_copy_block, nblk(rows * ncol), 256, 0, s, src, lds, dst, ldd, rows, ncol);
 }
 
+// Row splits of a cell for the FP64 wide kernel: enough CTAs for two per SM when a colour
+// holds few cells (the FP64 pipe of one SM needs long to finish a whole cell), at most one
+// split per 64 rows.
+int fp64_row_splits(dftfe_ham h, int64_t ctas, int nc) {
+  const int64_t want = (2LL * h->sm_count + ctas - 1) / std::max<int64_t>(ctas, 1);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (nc + 63) / 64));
+}
+
 static void local_part(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol,
                        double alpha) {
   auto* m = h->mesh;
@@ -162,9 +173,12 @@ static void local_part(dftfe_ham h, const double* X, int64_t ldx, double* Z, int
                    nc, X, ldx, Z, ldz, ncol, alpha);
     } else {
       size_t sh = (size_t)nc * 32 * sizeof(double) + nc * sizeof(int32_t);
-      dim3 grid((unsigned)n, (unsigned)((ncol + 31) / 32));
+      const int tiles = (ncol + 31) / 32;
+      const int splits = fp64_row_splits(h, n * tiles, nc);
+      const int rows = ((nc + splits - 1) / splits + 63) / 64 * 64;
+      dim3 grid((unsigned)n, (unsigned)tiles, (unsigned)((nc + rows - 1) / rows));
       DFTFE_LAUNCH(k_cell_fp64_wide, grid, 256, sh, h->stream, h->d_Hc, h->d_map, cells, nc, X, ldx, Z,
-                   ldz, ncol, alpha);
+                   ldz, ncol, alpha, rows);
     }
   }
 }

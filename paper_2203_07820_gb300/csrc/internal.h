@@ -182,6 +182,8 @@ void chfsi_pass_tail(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_bounds*
                      double* resid, dftfe_precision prec);
 // Z += alpha H~_nl X in FP64 (no-op without projectors)
 void nonlocal_add_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol, double alpha);
+// row splits of a cell for the FP64 wide cell kernel given the CTAs of one launch
+int fp64_row_splits(dftfe_ham h, int64_t ctas, int nc);
 // C = A^T B (both triangles) with FP32-equivalent tensor-core off-diagonal entries and the
 // FP64 diagonal from column-dot partials dpart[nchunk][N]; false when not applicable
 bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M, int N,
