@@ -804,11 +804,26 @@ __global__ void __launch_bounds__(256, 1) k_cell_df_tiled(const float2* __restri
   const int32_t* cm = map + cell * nc;
   for (int k = threadIdx.x; k < nc; k += 256) sm[k] = cm[k];
   __syncthreads();
-  for (int k = warp; k < nc; k += 8) {
+  {
+    // eight rows per warp in flight; the pair split keeps the FP64 pipe to one subtraction
+    // (the narrowing and widening are integer operations)
     const int col = col0 + lane;
-    const double xd = col < ncol ? X[(int64_t)sm[k] * ldx + col] : 0.0;
-    const float hi = __double2float_rn(xd);
-    xs[k * 32 + lane] = make_float2(hi, __double2float_rn(xd - (double)hi));
+    for (int k0 = warp; k0 < nc; k0 += 64) {
+      double xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + 8 * u;
+        xv[u] = (k < nc && col < ncol) ? X[(int64_t)sm[k] * ldx + col] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + 8 * u;
+        if (k < nc) {
+          const float hi = tc::narrow_f64(xv[u]);
+          xs[k * 32 + lane] = make_float2(hi, tc::narrow_f64(xv[u] - tc::widen_f32(hi)));
+        }
+      }
+    }
   }
   __syncthreads();
   float ah[TM][4], al[TM][4];
