@@ -37,20 +37,6 @@ def _start(dg, wl, seed):
     return X
 
 
-def test_features_and_decode_are_consistent(env):
-    dg, degree, wl, mesh, ham, qxyz = env
-    ev = np.linspace(-1.0, 0.5, 32)
-    r = degree.Record(ev, np.full(32, 1e-3), 0.5, 100.0, 40, False)
-    f = degree.features([r], True)
-    assert f.shape == (degree.N_IN,) and f[-1] == 1.0 and np.isclose(f[0], -0.75)
-    m, a, b, est = degree.decode(np.array([0.0, 0.0, 0.0]), r, 100.0)
-    assert m == 16 and a == ev[-1] and np.isclose(est, 100.0) and np.isclose(b, 101.0)
-    m, a, b, est = degree.decode(np.array([5.0, -3.0, -50.0]), r, 100.0)
-    assert m == degree.DEG_MAX and a == ev[-1] and b >= a + (ev[-1] - ev[0])   # clamps
-    m, a, b, est = degree.decode(np.array([-5.0, 3.0, 50.0]), r, 100.0)
-    assert m == degree.DEG_MIN and np.isclose(a, ev[-1] + 0.02 * 1.5) and np.isclose(est, 100.0 * np.exp(0.02))
-
-
 def test_learned_proposer_against_the_standard_rule(env, capsys):
     """Both controllers meet the tolerance at every step of held-out sequences; the proposer
     replaces the Lanczos run at each potential change and stays within 25 % of the standard
