@@ -38,7 +38,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.
 # (split precision), so traffic scales with the cells.  A kernel that changed since its
 # capture has no entry here (traffic null).
 DRAM_BYTES_PER_CELL = {"cell_gemm_fp64": (124.1e6 + 10.2e6) / 64,
-                       "cell_gemm_tf32x3": (2268.1e6 + 283.4e6) / 1728}
+                       "cell_gemm_tf32x3": (1877.1e6 + 279.3e6) / 1728}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
