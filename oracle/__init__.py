@@ -20,6 +20,9 @@ It is a plain, slow, obviously-correct restatement of the paper's method
                   electron density at quadrature points
   mlp.py          the learned degree/bounds proposer's network:        (no counterpart in the paper)
                   forward, loss gradient by the chain rule, Adam
+  kpoint.py       Bloch k-point Hamiltonian H~^k (complex cell terms    (Sec. 2, Eq. bloch and the
+                  -i k.G^c + 1/2|k|^2 M^c, phased projectors) and the    reduced equation after it)
+                  complex CholGS / Rayleigh-Ritz / residuals / pass
 
 Every function is FP64.  Library primitives used as single steps: numpy
 matmul/einsum, numpy.linalg.cholesky/eigh, scipy triangular solve, scipy.sparse
@@ -30,7 +33,9 @@ closed form, quadrature exactness, Kronecker-sum spectrum of the free-electron
 operator, harmonic-oscillator levels, scalar Chebyshev identity on exact
 eigenvectors, nonlocal PSD/rank/normalisation, Courant-Fischer, convergence to a
 dense eigensolve; for mlp.py, central finite differences, a closed-form linear special
-case and Adam's closed-form first step.  No function here is "parity unpinned".
+case and Adam's closed-form first step; for kpoint.py, the Kronecker sum of 1D Bloch
+operators, the free-electron closed form 1/2|k+G|^2 and Bloch folding of a doubled
+supercell.  No function here is "parity unpinned".
 """
 from .basis import gll_rule, gauss_rule, lagrange_table, lagrange_deriv_table
 from .mesh import PeriodicMesh

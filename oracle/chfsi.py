@@ -30,7 +30,9 @@ class Bounds:
 
 
 def chebyshev_filter(apply, X, degree, bounds):
-    X = np.array(X, dtype=np.float64, copy=True)
+    # real blocks stay float64; complex (Bloch) blocks stay complex128, the coefficients
+    # are real either way
+    X = np.array(X, dtype=np.result_type(np.asarray(X).dtype, np.float64), copy=True)
     if degree <= 0:
         return X
     e = (bounds.b - bounds.a) / 2.0

@@ -159,9 +159,13 @@ def gaussian_wells(points, centres, depth, width, L):
     pts = np.asarray(points, dtype=np.float64)
     v = np.zeros(pts.shape[0])
     rcut = 8.0 * width
-    # after the minimum-image wrap every other image is at least L/2 away
-    k = 0 if rcut <= 0.5 * L else int(math.ceil((rcut + 0.5 * L) / L))
-    shifts = [(i, j, l) for i in range(-k, k + 1) for j in range(-k, k + 1) for l in range(-k, k + 1)]
+    # after the minimum-image wrap every other image is at least L/2 away (L: scalar or
+    # one length per axis)
+    Lv = np.broadcast_to(np.asarray(L, np.float64), (3,))
+    k = [0 if rcut <= 0.5 * Ld else int(math.ceil((rcut + 0.5 * Ld) / Ld)) for Ld in Lv]
+    shifts = [(i, j, l) for i in range(-k[0], k[0] + 1) for j in range(-k[1], k[1] + 1)
+              for l in range(-k[2], k[2] + 1)]
+    L = np.asarray(L, np.float64)
     for R in centres:
         d0 = _wrap(pts - R, L)
         for sh in shifts:
@@ -185,13 +189,15 @@ def projector_csr(node_xyz, centres, width, cutoff, L):
       chi_s  = g(r) / (pi w^2)^(3/4),
       chi_pm = (x_m / w) g(r) / sqrt((pi w^2)^(3/2) / 2),   g = exp(-r^2 / (2 w^2)),
     each normalised analytically over R^3 and cut off hard at r < cutoff
-    (minimum-image displacement). Returns (rowptr int64, node int64, chi f64).
+    (minimum-image displacement; L a scalar or one length per axis).
+    Returns (rowptr int64, node int64, chi f64).
     """
     xyz = np.asarray(node_xyz, np.float64)
     n_s = (math.pi * width * width) ** 0.75
     n_p = math.sqrt(0.5 * (math.pi * width * width) ** 1.5)
     rowptr = [0]
     nodes, vals = [], []
+    L = np.asarray(L, np.float64)
     for R in centres:
         d = _wrap(xyz - np.asarray(R), L)
         r2 = np.einsum("ij,ij->i", d, d)
@@ -205,6 +211,19 @@ def projector_csr(node_xyz, centres, width, cutoff, L):
     if not nodes:
         return np.zeros(1, np.int64), np.zeros(0, np.int64), np.zeros(0)
     return (np.asarray(rowptr, np.int64), np.concatenate(nodes), np.concatenate(vals))
+
+
+def projector_disp(node_xyz, centres, cutoff, L):
+    """Minimum-image displacement x_node - R_atom (nnz x 3) of every entry of
+    projector_csr(node_xyz, centres, ..., cutoff, L), in the same order."""
+    xyz = np.asarray(node_xyz, np.float64)
+    L = np.asarray(L, np.float64)
+    out = []
+    for R in centres:
+        d = _wrap(xyz - np.asarray(R), L)
+        idx = np.nonzero(np.einsum("ij,ij->i", d, d) < cutoff * cutoff)[0]
+        out.extend([d[idx]] * 4)
+    return np.concatenate(out) if out else np.zeros((0, 3))
 
 
 def atom_walk(seed, centres, steps, step_len=0.05):
