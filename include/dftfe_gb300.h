@@ -264,6 +264,69 @@ dftfe_status dftfe_density(dftfe_ham ham, const double* Xo, int64_t ldo, int nco
 #define DFTFE_NOALLOC_MAX_COLS 512
 dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, int ncol, void* stream);
 
+/* -------------------------------------------------------------- Bloch k-points */
+/* The periodic part u of a Bloch state psi = e^{ik.x} u (Sec. 2, Eq. bloch) solves the reduced
+ * equation after Eq. bloch.  Discretised with the same basis and quadratures as at the Gamma
+ * point, its Loewdin form is
+ *   H~^k = H~_loc + 1/2 |k|^2 - i sum_d k_d G~_d + C~^k diag(h) C~^k^H,
+ * G~_d = M^-1/2 G_d M^-1/2 with G_d,jl = int N_j dN_l/dx_d by GLL quadrature on the nodes, and
+ * C~^k_ja = M_jj^1/2 chi_a(x_j) e^{-ik.d_ja} with d_ja = x_j - R_a the minimum-image
+ * displacement (the Bloch sum of the projector; projectors cut off within half the box).
+ * The _z calls act on COMPLEX blocks: complex128, DoF-major, element (i, j) of an M x ncol
+ * block at X[2 (i ld + j)] (real part) and X[2 (i ld + j) + 1] (imaginary part), ld >= ncol
+ * counted in complex elements (the layout of C99 double complex and torch.complex128),
+ * DEVICE memory owned by the caller.  Arithmetic is FP64 throughout.  The Gamma-point calls
+ * of the same ham are unaffected.  The complex Rayleigh-Ritz multiplies each eigenvector
+ * column of the subspace problem by the phase that makes its largest-|.| entry real and
+ * positive (for deterministic output).  Every _z call other than dftfe_ham_set_kpoint returns
+ * DFTFE_ERR_STATE before the first dftfe_ham_set_kpoint, and after a dftfe_ham_set_nonlocal
+ * that came later than the last dftfe_ham_set_kpoint. */
+
+/* Set the wave vector k (HOST, 3 doubles, bohr^-1) of the _z calls.  disp: HOST nnz x 3
+ * displacements d_e = x_node(e) - R_atom (minimum image) of the entries e of the CSR passed to
+ * the last dftfe_ham_set_nonlocal, in its order; NULL only when no projectors are set.
+ * Non-finite k or displacements: DFTFE_ERR_ARG.  Synchronises the stream. */
+dftfe_status dftfe_ham_set_kpoint(dftfe_ham ham, const double* k, const double* disp);
+
+/* Y = H~^k X for complex M x ncol blocks (X, Y DEVICE, not overlapping). */
+dftfe_status dftfe_ham_apply_z(dftfe_ham ham, const double* X, int64_t ldx, double* Y,
+                               int64_t ldy, int ncol);
+
+/* dftfe_lanczos on the real 2M x 2M form of H~^k (the same spectrum, each eigenvalue
+ * twice), acting on the real view of one complex vector: v0 DEVICE, 2M doubles (M complex),
+ * or NULL for dftfe_random_uniform(seed) over 2M values.  HOST out3 as in dftfe_lanczos. */
+dftfe_status dftfe_lanczos_z(dftfe_ham ham, int k, const double* v0, uint64_t seed,
+                             double* out3);
+
+/* dftfe_spectrum_bounds from dftfe_lanczos_z.  Host out. */
+dftfe_status dftfe_spectrum_bounds_z(dftfe_ham ham, int k, uint64_t seed, int nstates,
+                                     dftfe_bounds* out);
+
+/* dftfe_chebyshev_filter (FP64) on a complex block with H~^k. */
+dftfe_status dftfe_chebyshev_filter_z(dftfe_ham ham, double* X, int64_t ld, int ncol,
+                                      int degree, const dftfe_bounds* bounds);
+
+/* Cholesky-Gram-Schmidt on a complex block: S = X^H X, S = L L^H, X <- X L^-H
+ * (1 <= ncol <= 1024).  DFTFE_ERR_NOT_SPD as dftfe_cholgs.  Synchronises the stream. */
+dftfe_status dftfe_cholgs_z(dftfe_ham ham, double* X, int64_t ld, int ncol);
+
+/* Rayleigh-Ritz on an orthonormal complex block: W = H~^k X, H^ = X^H W (lower triangle,
+ * Hermitian), H^ = Q Theta Q^H (Theta ascending, phases as above), X <- X Q.  evals: DEVICE
+ * ncol doubles.  HX: DEVICE complex M x ncol (ldhx) receiving W Q, or NULL.  1 <= ncol <=
+ * 1024.  Synchronises the stream. */
+dftfe_status dftfe_rayleigh_ritz_z(dftfe_ham ham, double* X, int64_t ld, int ncol,
+                                   double* evals, double* HX, int64_t ldhx);
+
+/* Residual norms ||w_i - theta_i x_i||_2 of complex columns (X, HX complex with ld;
+ * evals, resid DEVICE ncol doubles). */
+dftfe_status dftfe_residuals_z(dftfe_ham ham, const double* X, const double* HX, int64_t ld,
+                               int ncol, const double* evals, double* resid);
+
+/* One ChFSI pass on a complex block at the ham's k-point, as dftfe_chfsi_pass with FP64
+ * arithmetic (1 <= ncol <= 1024).  Synchronises the stream. */
+dftfe_status dftfe_chfsi_pass_z(dftfe_ham ham, double* X, int64_t ld, int ncol, int block,
+                                int degree, dftfe_bounds* inout, double* evals, double* resid);
+
 /* ------------------------------------------------------------ batched passes */
 /* Several independent systems (Gamma point, FP64) of uneven mesh size, degree, state count
  * and block size advanced by one ChFSI pass each with shared launches: per Chebyshev step one

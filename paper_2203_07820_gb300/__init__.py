@@ -81,6 +81,15 @@ _SIGS = {
     "dftfe_mlp_forward": [_vp, _int, _int, _int, _vp, _i64, _vp, _vp],
     "dftfe_mlp_loss_grad": [_vp, _int, _int, _int, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "dftfe_mlp_adam": [_vp, _vp, _vp, _vp, _i64, _int, C.c_float, C.c_float, C.c_float, C.c_float, _vp],
+    "dftfe_ham_set_kpoint": [_vp, _vp, _vp],
+    "dftfe_ham_apply_z": [_vp, _vp, _i64, _vp, _i64, _int],
+    "dftfe_lanczos_z": [_vp, _int, _vp, C.c_uint64, _vp],
+    "dftfe_spectrum_bounds_z": [_vp, _int, C.c_uint64, _int, C.POINTER(Bounds)],
+    "dftfe_chebyshev_filter_z": [_vp, _vp, _i64, _int, _int, C.POINTER(Bounds)],
+    "dftfe_cholgs_z": [_vp, _vp, _i64, _int],
+    "dftfe_rayleigh_ritz_z": [_vp, _vp, _i64, _int, _vp, _vp, _i64],
+    "dftfe_residuals_z": [_vp, _vp, _vp, _i64, _int, _vp, _vp],
+    "dftfe_chfsi_pass_z": [_vp, _vp, _i64, _int, _int, _int, C.POINTER(Bounds), _vp, _vp],
     "dftfe_profile_enable": [_vp, _int],
     "dftfe_profile_query": [_vp, C.c_char_p, C.POINTER(_dbl), C.POINTER(_i64)],
 }
@@ -259,6 +268,83 @@ def dftfe_rayleigh_ritz_split(ham, X, nfr, evals, Xfr, prec=DFTFE_FP64):
     px, ld = _dev(X, "X")
     pf, ldf = _dev(Xfr, "Xfr")
     _check(_lib.dftfe_rayleigh_ritz_split(ham, px, ld, X.shape[1], int(nfr), _vp(evals.data_ptr()), pf, ldf, prec))
+
+
+# ------------------------------------------------------------ Bloch k-points
+def _zdev(t, name="array"):
+    """Pointer and leading dimension (complex elements) of a CUDA complex128 tensor with unit
+    column stride."""
+    if t is None:
+        return None, 0
+    import torch
+    if not t.is_cuda or t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be a CUDA complex128 tensor")
+    if t.dim() == 1:
+        return _vp(t.data_ptr()), 1
+    if t.dim() != 2 or (t.stride(1) != 1 and t.shape[1] > 1):
+        raise ValueError(f"{name} must be 2-D with unit column stride")
+    return _vp(t.data_ptr()), t.stride(0)
+
+
+def dftfe_ham_set_kpoint(ham, k, disp=None):
+    """k: 3 floats (bohr^-1); disp: host nnz x 3 displacements of the projector CSR entries."""
+    kk, pk = _host(np.asarray(k, np.float64).reshape(3), np.float64)
+    if disp is None:
+        _check(_lib.dftfe_ham_set_kpoint(ham, pk, None))
+    else:
+        dd, pd = _host(np.asarray(disp, np.float64).reshape(-1, 3), np.float64)
+        _check(_lib.dftfe_ham_set_kpoint(ham, pk, pd))
+
+
+def dftfe_ham_apply_z(ham, X, Y):
+    px, ldx = _zdev(X, "X")
+    py, ldy = _zdev(Y, "Y")
+    ncol = 1 if X.dim() == 1 else X.shape[1]
+    _check(_lib.dftfe_ham_apply_z(ham, px, ldx, py, ldy, ncol))
+
+
+def dftfe_lanczos_z(ham, k, v0=None, seed=0):
+    out = (C.c_double * 3)()
+    pv = None if v0 is None else _vp(v0.data_ptr())
+    _check(_lib.dftfe_lanczos_z(ham, int(k), pv, C.c_uint64(seed), C.cast(out, _vp)))
+    return out[0], out[1], out[2]
+
+
+def dftfe_spectrum_bounds_z(ham, k, seed, nstates):
+    b = Bounds()
+    _check(_lib.dftfe_spectrum_bounds_z(ham, int(k), C.c_uint64(seed), int(nstates), C.byref(b)))
+    return b
+
+
+def dftfe_chebyshev_filter_z(ham, X, degree, bounds):
+    px, ld = _zdev(X, "X")
+    _check(_lib.dftfe_chebyshev_filter_z(ham, px, ld, X.shape[1], int(degree), C.byref(bounds)))
+
+
+def dftfe_cholgs_z(ham, X):
+    px, ld = _zdev(X, "X")
+    _check(_lib.dftfe_cholgs_z(ham, px, ld, X.shape[1]))
+
+
+def dftfe_rayleigh_ritz_z(ham, X, evals, HX=None):
+    px, ld = _zdev(X, "X")
+    ph, ldh = _zdev(HX, "HX")
+    _check(_lib.dftfe_rayleigh_ritz_z(ham, px, ld, X.shape[1], _vp(evals.data_ptr()), ph, ldh))
+
+
+def dftfe_residuals_z(ham, X, HX, evals, resid):
+    px, ld = _zdev(X, "X")
+    ph, ldh = _zdev(HX, "HX")
+    if ldh != ld:
+        raise ValueError("X and HX must share the leading dimension")
+    _check(_lib.dftfe_residuals_z(ham, px, ph, ld, X.shape[1], _vp(evals.data_ptr()), _vp(resid.data_ptr())))
+
+
+def dftfe_chfsi_pass_z(ham, X, block, degree, bounds, evals, resid):
+    px, ld = _zdev(X, "X")
+    _check(_lib.dftfe_chfsi_pass_z(ham, px, ld, X.shape[1], int(block), int(degree), C.byref(bounds),
+                                   _vp(evals.data_ptr()), _vp(resid.data_ptr())))
+    return bounds
 
 
 class BatchItem(C.Structure):

@@ -7,11 +7,12 @@
 //  potrf        S = L L^T, left-looking, one CTA (Alg. 2 step 2a).
 //  trtri        Z = L^-T, one thread per column of L^-1 (forward substitution).
 //  rotate       X <- X Z in place, row panels staged in shared memory (steps 3a/3b).
-//  syevd        H^ = Q Theta Q^T: Householder tridiagonalisation, accumulation of Q,
-//               implicit-shift QL on the tridiagonal (Bowdler, Martin, Reinsch,
-//               Wilkinson, Numer. Math. 11, 1968) with the rotations replayed on Q,
-//               then ascending sort and the sign convention (step 2b-c).
-//  residuals    ||W_i - theta_i X_i|| or the generalised form (a13).
+//  syevd        H^ = Q Theta Q^T: parallel cyclic Jacobi in one cooperative launch, then
+//               ascending sort and the sign convention (step 2b-c); syevd_z is the
+//               Hermitian form for Bloch k-points.
+//  tridiag_ql   implicit-shift QL on a tridiagonal (Bowdler, Martin, Reinsch, Wilkinson,
+//               Numer. Math. 11, 1968), for the Lanczos bound.
+//  residuals    ||W_i - theta_i X_i|| or the generalised form (a13), real or complex.
 #include "internal.h"
 
 #include <cmath>
@@ -476,6 +477,152 @@ __global__ void __launch_bounds__(256) k_jacobi(double* __restrict__ A, double* 
   }
 }
 
+// complex helpers for the Hermitian Jacobi
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zlin(double a, double2 x, double b, double2 y) {   // a x + b y
+  return make_double2(a * x.x + b * y.x, a * x.y + b * y.y);
+}
+
+// Hermitian form of k_jacobi: A (N x N complex, lower triangle read) -> VT (row p = column p
+// of V, not conjugated) and d.  A rotation of the pair (p, q) first makes a_pq real and
+// non-negative with the diagonal unitary D = diag(1, conj(w)), w = a_pq / |a_pq| (row q of A
+// times w, column q times conj(w)), then applies k_jacobi's real symmetric rotation R to the
+// resulting real 2 x 2 problem: J = D R, A <- J^H A J, V <- V J.  Same pairing, barriers,
+// convergence test and work split as k_jacobi.  Dynamic shared memory: 4 doubles, one
+// complex and 2 ints per pair.
+__global__ void __launch_bounds__(256) k_jacobi_z(double2* __restrict__ A, double2* __restrict__ VT,
+                                                  double* __restrict__ d, int N, int max_sweeps,
+                                                  const double* __restrict__ anorm_p, jac::Barrier* bar,
+                                                  int* status) {
+  extern __shared__ double jsm[];
+  const int Ne = N + (N & 1), NP = Ne / 2, m = Ne - 1;
+  double* cs = jsm;
+  double* sn = cs + NP;
+  double* tn = sn + NP;
+  double* mg = tn + NP;
+  double2* om = reinterpret_cast<double2*>(mg + NP);   // 4 NP doubles in: 16-byte aligned
+  int* pp = reinterpret_cast<int*>(om + NP);
+  int* qq = pp + NP;
+  __shared__ int rotated;
+  const double anorm = *anorm_p;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gthreads = (int64_t)gridDim.x * blockDim.x;
+  // full Hermitian copy from the lower triangle (real diagonal), VT = I
+  for (int64_t w = gtid; w < (int64_t)N * N; w += gthreads) {
+    const int i = (int)(w / N), j = (int)(w % N);
+    if (i < j) A[w] = zconj(A[(int64_t)j * N + i]);
+    else if (i == j) A[w].y = 0.0;
+    VT[w] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (!jac::grid_barrier(bar, status)) return;
+  bool converged = false;
+  unsigned int round = 0;
+  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+      for (int P = threadIdx.x; P < NP; P += blockDim.x) {
+        int p, q;
+        jac::pairing(k, P, Ne, p, q);
+        double c = 1.0, s = 0.0, t = 0.0, mag = 0.0;
+        double2 w = make_double2(1.0, 0.0);
+        if (q < N) {
+          const double2 apq = A[(int64_t)p * N + q];
+          mag = hypot(apq.x, apq.y);
+          const double app = A[(int64_t)p * N + p].x, aqq = A[(int64_t)q * N + q].x;
+          const double small = fmax(1e-15 * sqrt(fabs(app) * fabs(aqq)), 1e-18 * anorm);
+          if (mag > small) {
+            const double tau = (aqq - app) / (2.0 * mag);
+            t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(fma(tau, tau, 1.0)));
+            c = 1.0 / sqrt(fma(t, t, 1.0));
+            s = t * c;
+            w = make_double2(apq.x / mag, apq.y / mag);
+            rotated = 1;
+          }
+        }
+        cs[P] = c;
+        sn[P] = s;
+        tn[P] = t;
+        mg[P] = mag;
+        om[P] = w;
+        pp[P] = p;
+        qq[P] = q;
+      }
+      jac::arrive_read(bar);
+      ++round;
+      // A <- J^H A J on the off-diagonal 2 x 2 blocks (row pair P, column pair R)
+      for (int64_t wi = gtid; wi < (int64_t)NP * NP; wi += gthreads) {
+        const int P = (int)(wi / NP), R = (int)(wi % NP);
+        const double c = cs[P], s = sn[P], c2 = cs[R], s2 = sn[R];
+        if ((s == 0.0 && s2 == 0.0) || P == R) continue;
+        const int p = pp[P], q = qq[P], p2 = pp[R], q2 = qq[R];
+        const bool hq = q < N, hq2 = q2 < N;
+        double2* rp = A + (int64_t)p * N;
+        double2* rq = A + (int64_t)(hq ? q : p) * N;
+        const double2 z0 = make_double2(0.0, 0.0);
+        const double2 x00 = rp[p2], x01 = hq2 ? rp[q2] : z0;
+        const double2 x10 = hq ? rq[p2] : z0, x11 = hq && hq2 ? rq[q2] : z0;
+        const double2 wP = om[P], wRc = zconj(om[R]);
+        const double2 y10 = zmul(wP, x10), y11 = zmul(wP, x11);          // row q times w_P
+        const double2 t00 = zlin(c, x00, -s, y10), t01 = zlin(c, x01, -s, y11);
+        const double2 t10 = zlin(s, x00, c, y10), t11 = zlin(s, x01, c, y11);
+        const double2 u01 = zmul(wRc, t01), u11 = zmul(wRc, t11);         // column q2 times conj(w_R)
+        rp[p2] = zlin(c2, t00, -s2, u01);
+        if (hq2) rp[q2] = zlin(s2, t00, c2, u01);
+        if (hq) rq[p2] = zlin(c2, t10, -s2, u11);
+        if (hq && hq2) rq[q2] = zlin(s2, t10, c2, u11);
+      }
+      if (!jac::wait_reads(bar, round * gridDim.x, status)) return;
+      for (int64_t P = gtid; P < NP; P += gthreads) {
+        if (sn[P] == 0.0) continue;
+        double2* rp = A + (int64_t)pp[P] * N;
+        double2* rq = A + (int64_t)qq[P] * N;
+        const int p = pp[P], q = qq[P];
+        const double tm = tn[P] * mg[P];
+        rp[p].x -= tm;
+        rq[q].x += tm;
+        rp[q] = make_double2(0.0, 0.0);
+        rq[p] = make_double2(0.0, 0.0);
+      }
+      // V <- V J on the rows of VT
+      for (int64_t wi = gtid; wi < (int64_t)NP * N; wi += gthreads) {
+        const int P = (int)(wi / N), i = (int)(wi % N);
+        const double s = sn[P];
+        if (s == 0.0 || qq[P] >= N) continue;
+        const double c = cs[P];
+        double2* vp = VT + (int64_t)pp[P] * N + i;
+        double2* vq = VT + (int64_t)qq[P] * N + i;
+        const double2 a = *vp, b = zmul(zconj(om[P]), *vq);
+        *vp = zlin(c, a, -s, b);
+        *vq = zlin(s, a, c, b);
+      }
+      if (!jac::grid_barrier(bar, status)) return;
+    }
+    converged = rotated == 0;
+    __syncthreads();
+  }
+  if (blockIdx.x == 0) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) d[i] = A[(int64_t)i * N + i].x;
+    if (threadIdx.x == 0 && !converged) atomicCAS(status, 0, (int)DFTFE_ERR_NOCONV);
+  }
+}
+
+// Frobenius norm of a Hermitian matrix from its lower triangle (complex, interleaved)
+__global__ void k_fro_norm_z(const double2* __restrict__ A, int N, double* out) {
+  __shared__ double red[9];
+  double s = 0.0;
+  for (int64_t w = threadIdx.x; w < (int64_t)N * N; w += blockDim.x) {
+    const int i = (int)(w / N), j = (int)(w % N);
+    const double a2 = A[w].x * A[w].x + A[w].y * A[w].y;
+    if (i >= j) s += i > j ? 2.0 * a2 : a2;
+  }
+  s = block_sum<256>(s, red);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
 __global__ void k_fro_norm(const double* __restrict__ A, int N, double* out) {
   __shared__ double red[9];
   double s = 0.0;
@@ -685,26 +832,98 @@ void syevd(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_statu
   DFTFE_LAUNCH(k_sign_copy, N, 256, 0, s, VT, perm, N, Q);
 }
 
+// complex eigenvectors (rows of VT) -> columns of Q in ascending order, each multiplied by
+// the phase that makes its largest-|.| entry (first on ties) real and positive
+__global__ void __launch_bounds__(256) k_phase_copy_z(const double2* __restrict__ VT, const int* perm, int N,
+                                                      double2* __restrict__ Q) {
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  const int c = blockIdx.x;
+  const int src = perm[c];
+  double best = -1.0;
+  int bidx = N;
+  for (int r = threadIdx.x; r < N; r += 256) {
+    const double2 v = VT[(int64_t)src * N + r];
+    const double a = hypot(v.x, v.y);
+    if (a > best || (a == best && r < bidx)) { best = a; bidx = r; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double o = bv[threadIdx.x + s];
+      const int oi = bi[threadIdx.x + s];
+      if (o > bv[threadIdx.x] || (o == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = o;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const double2 pv = VT[(int64_t)src * N + bi[0]];
+  const double a = bv[0];
+  const double2 ph = a > 0.0 ? make_double2(pv.x / a, -pv.y / a) : make_double2(1.0, 0.0);
+  for (int r = threadIdx.x; r < N; r += 256) Q[(int64_t)r * N + c] = zmul(ph, VT[(int64_t)src * N + r]);
+}
+
+void syevd_z(dftfe_ham h, double* Ad, int N, double* evals, double* Qd, int* d_status) {
+  cudaStream_t s = h->stream;
+  ProfScope ps(h, "syevd_z");
+  double2* A = reinterpret_cast<double2*>(Ad);
+  double2* Q = reinterpret_cast<double2*>(Qd);
+  const int NP = (N + (N & 1)) / 2;
+  double2* VT = (double2*)ws_get(h, "eigz_V", sizeof(double2) * (size_t)N * N);
+  double* vec = (double*)ws_get(h, "eig_vec", sizeof(double) * (size_t)N + 64);
+  double* d = vec;
+  double* anorm = vec + N;
+  jac::Barrier* bar = (jac::Barrier*)ws_get(h, "eig_bar", sizeof(jac::Barrier));
+  int* perm = (int*)ws_get(h, "eig_perm", sizeof(int) * (size_t)N);
+  const size_t sh = (size_t)NP * (6 * sizeof(double) + 2 * sizeof(int));
+  static bool attr = false;
+  if (!attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_jacobi_z, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    attr = true;
+  }
+  if (sh > 64 * 1024) throw Error(DFTFE_ERR_ARG, "dense eigensolver: N too large");
+  int per_sm = 0;
+  DFTFE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_z, 256, sh));
+  if (per_sm < 1) throw Error(DFTFE_ERR_CUDA, "dense eigensolver: kernel does not fit on an SM");
+  const int want = (int)std::min<int64_t>(h->sm_count, ((int64_t)NP * N + 255) / 256);
+  int grid = std::max(1, want);
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(jac::Barrier), s));
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+  DFTFE_LAUNCH(k_fro_norm_z, 1, 256, 0, s, A, N, anorm);
+  int maxs = 60;
+  void* args[] = {&A, &VT, &d, &N, &maxs, &anorm, &bar, &d_status};
+  DFTFE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_z, dim3(grid), dim3(256), args, sh, s));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  DFTFE_LAUNCH(k_rank, nblk(N, 128), 128, 0, s, d, N, perm, evals);
+  DFTFE_LAUNCH(k_phase_copy_z, N, 256, 0, s, VT, perm, N, Q);
+}
+
 // ----------------------------------------------------------------- residuals
+// cw doubles per column: 1 (real) or 2 (complex, real and imaginary parts interleaved)
 __global__ void k_resid_partial(const double* __restrict__ X, int64_t ldx, const double* __restrict__ W,
                                 int64_t ldw, int64_t M, int ncol, const double* __restrict__ evals,
-                                const double* __restrict__ mass, int kind, int64_t rows,
+                                const double* __restrict__ mass, int kind, int64_t rows, int cw,
                                 double* __restrict__ part) {
   const int64_t i0 = (int64_t)blockIdx.x * rows;
   const int64_t i1 = min(M, i0 + rows);
   for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
     const double th = evals[c];
     double num = 0.0, den = 0.0;
-    for (int64_t i = i0; i < i1; ++i) {
-      const double x = X[i * ldx + c];
-      const double r = W[i * ldw + c] - th * x;
-      if (kind == 0) num = fma(r, r, num);
-      else {
-        const double m = mass[i];
-        num = fma(m * r, r, num);
-        den = fma(x / m, x, den);
+    for (int64_t i = i0; i < i1; ++i)
+      for (int u = 0; u < cw; ++u) {
+        const double x = X[i * ldx + c * cw + u];
+        const double r = W[i * ldw + c * cw + u] - th * x;
+        if (kind == 0) num = fma(r, r, num);
+        else {
+          const double m = mass[i];
+          num = fma(m * r, r, num);
+          den = fma(x / m, x, den);
+        }
       }
-    }
     part[((int64_t)blockIdx.x * ncol + c) * 2] = num;
     part[((int64_t)blockIdx.x * ncol + c) * 2 + 1] = den;
   }
@@ -723,13 +942,13 @@ __global__ void k_resid_final(const double* __restrict__ part, int nchunk, int n
 }
 
 void residual_norms(dftfe_ham h, const double* X, int64_t ldx, const double* W, int64_t ldw, int64_t M,
-                     int ncol, const double* evals, double* resid, int kind) {
+                     int ncol, const double* evals, double* resid, int kind, int cw) {
   if (ncol <= 0) return;
   const int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>(h->sm_count * 4, M / 64));
   const int64_t rows = (M + nchunk - 1) / nchunk;
   double* part = (double*)ws_get(h, "resid_part", sizeof(double) * 2 * (size_t)nchunk * ncol);
   DFTFE_LAUNCH(k_resid_partial, nchunk, 256, 0, h->stream, X, ldx, W, ldw, M, ncol, evals, h->d_mass,
-               kind, rows, part);
+               kind, rows, cw, part);
   DFTFE_LAUNCH(k_resid_final, nblk(ncol, 128), 128, 0, h->stream, part, nchunk, ncol, kind, resid);
 }
 
@@ -827,9 +1046,11 @@ __global__ void k_lz_bound(const double* d, const double* Z, const double* beta,
   out3[2] = d[imax] + fabs(beta[k - 1]) * fabs(Z[(int64_t)(k - 1) * k + imax]);
 }
 
-void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3) {
+void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3, bool cplx) {
   auto* m = h->mesh;
-  const int64_t M = m->M;
+  // vector length: M, or 2M for the real view of a complex vector (the dot products below are
+  // then those of the real 2M x 2M form of H~^k, which has H~^k's spectrum, each value twice)
+  const int64_t M = cplx ? 2 * m->M : m->M;
   cudaStream_t s = h->stream;
   double* Vm = (double*)ws_get(h, "lz_V", sizeof(double) * (size_t)(k + 1) * M);
   double* w = (double*)ws_get(h, "lz_w", sizeof(double) * (size_t)M);
@@ -851,7 +1072,8 @@ void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3) 
   DFTFE_LAUNCH(k_lz_scale, nblk(M), 256, 0, s, Vm, w, nrm, M);
   for (int j = 0; j < k; ++j) {
     double* vj = Vm + (int64_t)j * M;
-    apply_combo(h, vj, 1, nullptr, 0, w, 1, 1, 1.0, 0.0, 0.0);
+    if (cplx) apply_combo_z(h, vj, 1, nullptr, 0, w, 1, 1, 1.0, 0.0, 0.0);
+    else apply_combo(h, vj, 1, nullptr, 0, w, 1, 1, 1.0, 0.0, 0.0);
     DFTFE_LAUNCH(k_multidot_partial, LZ_G, 256, 0, s, vj, 1, w, M, part);
     DFTFE_LAUNCH(k_multidot_final, 1, 32, 0, s, part, 1, LZ_G, alpha + j, 0);
     DFTFE_LAUNCH(k_lz_three_term, nblk(M), 256, 0, s, w, vj, j > 0 ? vj - M : nullptr, alpha + j,

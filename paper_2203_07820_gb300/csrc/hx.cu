@@ -146,6 +146,16 @@ void copy_block(cudaStream_t s, const double* src, int64_t lds, double* dst, int
   DFTFE_LAUNCH(k_copy_block, nblk(rows * ncol), 256, 0, s, src, lds, dst, ldd, rows, ncol);
 }
 
+static bool g_attr_set = false;
+static void set_smem_attrs() {
+  if (g_attr_set) return;
+  const int big = 200 * 1024;
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_fp64_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_fp64_narrow<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_fp64_narrow<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  g_attr_set = true;
+}
+
 // Row splits of a cell for the FP64 wide kernel: enough CTAs for two per SM when a colour
 // holds few cells (the FP64 pipe of one SM needs long to finish a whole cell), at most one
 // split per 64 rows.
@@ -154,9 +164,10 @@ int fp64_row_splits(dftfe_ham h, int64_t ctas, int nc) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (nc + 63) / 64));
 }
 
-static void local_part(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol,
-                       double alpha) {
+void local_part_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol,
+                     double alpha) {
   auto* m = h->mesh;
+  set_smem_attrs();
   const int nc = m->nc;
   for (int c = 0; c < h->ncolours; ++c) {
     const int64_t n = h->colour_off[c + 1] - h->colour_off[c];
@@ -183,16 +194,6 @@ static void local_part(dftfe_ham h, const double* X, int64_t ldx, double* Z, int
   }
 }
 
-static bool g_attr_set = false;
-static void set_smem_attrs() {
-  if (g_attr_set) return;
-  const int big = 200 * 1024;
-  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_fp64_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_fp64_narrow<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_fp64_narrow<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-  g_attr_set = true;
-}
-
 // Z += alpha H~_nl X (FP64), nothing without projectors
 void nonlocal_add_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol, double alpha) {
   if (h->nproj <= 0) return;
@@ -213,7 +214,7 @@ void apply_combo(dftfe_ham h, const double* X, int64_t ldx, const double* Xprev,
   DFTFE_LAUNCH(k_axpby_init, nblk(m->M * ncol), 256, 0, h->stream, Z, ldz, X, ldx, Xprev, ldp, m->M,
                ncol, s1, s2);
   nonlocal_add_fp64(h, X, ldx, Z, ldz, ncol, alpha);
-  local_part(h, X, ldx, Z, ldz, ncol, alpha);
+  local_part_fp64(h, X, ldx, Z, ldz, ncol, alpha);
 }
 
 void apply_nonlocal_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {

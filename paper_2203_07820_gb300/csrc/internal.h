@@ -133,6 +133,15 @@ struct dftfe_ham_s {
   int32_t* d_snode = nullptr; int64_t* d_srow = nullptr;
   int32_t* d_sproj = nullptr; double* d_sval = nullptr;
   int64_t* d_nptr_all = nullptr;   // M + 1 offsets of every node's (sproj, sval) entries
+  int64_t nnz = 0;                 // projector CSR entries
+  int64_t* d_sperm = nullptr;      // node-major entry t = projector-major entry d_sperm[t]
+  // Bloch k-point (complex entry points)
+  bool has_kpoint = false;
+  bool kpoint_nl = false;          // d_pval_z / d_sval_z hold the current projectors
+  double kvec[3] = {0.0, 0.0, 0.0};
+  double* d_ktab = nullptr;        // 3 x p x (2p+1): k_d G~1_d stencil per axis (see kpoint.cu)
+  double* d_pval_z = nullptr;      // nnz complex, projector-major: M^1/2 chi e^{-ik.d}
+  double* d_sval_z = nullptr;      // the same values node-major
   // workspace
   std::map<std::string, dftfe::DevBuf> ws;
   // profiling
@@ -199,10 +208,23 @@ void rotate_inplace(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const 
                     bool upper);
 void syevd(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_status);
 void tridiag_ql(cudaStream_t s, double* d, double* e, double* Z, int N, int* d_status);
+// cw = 2: complex columns (interleaved real and imaginary parts, ld in doubles), one
+// residual per complex column
 void residual_norms(dftfe_ham h, const double* X, int64_t ldx, const double* W, int64_t ldw,
-                    int64_t M, int ncol, const double* evals, double* resid, int kind);
+                    int64_t M, int ncol, const double* evals, double* resid, int kind, int cw = 1);
 void random_uniform(cudaStream_t s, double* out, int64_t n, uint64_t seed, int64_t offset);
-void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3);
+// cplx: Lanczos on the real 2M x 2M form of H~^k (vectors are the real views of complex ones)
+void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3, bool cplx = false);
+// Hermitian A (N x N complex interleaved, lower triangle read) = Q Theta Q^H; Q row-major
+// complex, columns ascending, each column's largest-|.| entry made real and positive
+void syevd_z(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_status);
+
+// hx.cu: Z += alpha H~_loc X over all colours (FP64 cell products), ncol real columns
+void local_part_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol, double alpha);
+
+// kpoint.cu: Z = alpha H~^k X + s1 X + s2 Xp on complex blocks (ld in complex elements)
+void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, int64_t ldp, double* Z,
+                   int64_t ldz, int ncol, double alpha, double s1, double s2);
 
 }  // namespace dftfe
 

@@ -197,12 +197,14 @@ static T* dev_upload(const std::vector<T>& v, cudaStream_t s) {
 static void free_nonlocal(dftfe_ham h) {
   cudaFree(h->d_h); cudaFree(h->d_prow); cudaFree(h->d_pnode); cudaFree(h->d_pval);
   cudaFree(h->d_snode); cudaFree(h->d_srow); cudaFree(h->d_sproj); cudaFree(h->d_sval);
-  cudaFree(h->d_nptr_all);
+  cudaFree(h->d_nptr_all); cudaFree(h->d_sperm); cudaFree(h->d_pval_z); cudaFree(h->d_sval_z);
   h->d_h = nullptr; h->d_prow = nullptr; h->d_pnode = nullptr; h->d_pval = nullptr;
   h->d_snode = nullptr; h->d_srow = nullptr; h->d_sproj = nullptr; h->d_sval = nullptr;
-  h->d_nptr_all = nullptr;
+  h->d_nptr_all = nullptr; h->d_sperm = nullptr; h->d_pval_z = nullptr; h->d_sval_z = nullptr;
   h->nproj = 0;
   h->nsup = 0;
+  h->nnz = 0;
+  h->kpoint_nl = false;   // the phased projector values belong to the old CSR
 }
 
 }  // namespace dftfe
@@ -477,6 +479,7 @@ extern "C" dftfe_status dftfe_ham_set_nonlocal(dftfe_ham h, int nproj, const dou
   free_nonlocal(h);
   cudaStream_t s = h->stream;
   h->nproj = nproj;
+  h->nnz = nnz;
   h->nsup = (int64_t)snode.size();
   h->d_h = dev_upload(std::vector<double>(hcoup, hcoup + nproj), s);
   h->d_prow = dev_upload(std::vector<int64_t>(rowptr, rowptr + nproj + 1), s);
@@ -496,12 +499,12 @@ extern "C" dftfe_status dftfe_ham_set_nonlocal(dftfe_ham h, int nproj, const dou
     h->d_nptr_all = dev_upload(nall, s);
   }
   h->d_sproj = dev_upload(sproj, s);
-  int64_t* d_perm = dev_upload(order, s);
+  // node-major position t holds projector-major entry sperm[t] (kept for the k-point values)
+  h->d_sperm = dev_upload(order, s);
   DFTFE_CHECK_CUDA(cudaMalloc(&h->d_sval, sizeof(double) * std::max<int64_t>(nnz, 1)));
-  if (nnz) DFTFE_LAUNCH(k_gather_vals, nblk(nnz), 256, 0, s, h->d_sval, h->d_pval, d_perm, nnz);
+  if (nnz) DFTFE_LAUNCH(k_gather_vals, nblk(nnz), 256, 0, s, h->d_sval, h->d_pval, h->d_sperm, nnz);
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(s));
   cudaFree(d_chi);
-  cudaFree(d_perm);
   ABI_END
 }
 
@@ -512,7 +515,7 @@ extern "C" dftfe_status dftfe_ham_destroy(dftfe_ham h) {
   free_nonlocal(h);
   cudaFree(h->d_map); cudaFree(h->d_mass); cudaFree(h->d_minvsqrt);
   cudaFree(h->d_colour_cells); cudaFree(h->d_node_ptr); cudaFree(h->d_node_slot); cudaFree(h->d_K); cudaFree(h->d_P); cudaFree(h->d_pairs);
-  cudaFree(h->d_wq); cudaFree(h->d_Hc); cudaFree(h->d_Nq);
+  cudaFree(h->d_wq); cudaFree(h->d_Hc); cudaFree(h->d_Nq); cudaFree(h->d_ktab);
   for (auto& kv : h->ws) kv.second.release();
   for (auto& kv : h->timers)
     for (auto& ev : kv.second.events) {

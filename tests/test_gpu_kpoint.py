@@ -1,0 +1,252 @@
+"""GPU parity of the Bloch k-point path (complex128): every complex step through the C ABI
+against the complex FP64 oracle (oracle/kpoint.py) on the same seeded inputs, element by
+element, on meshes with an odd cell count (3-colour axis), p = 6 with two cells per axis
+(the stencil's two wrap-around neighbours are one node), ragged column tails, projectors,
+and k along one axis or general.  The k = 0 complex pass is checked against the real pass."""
+import math
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import kpoint
+from systems import oracle_system, gpu_system, small_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_APPLY = 1e-12
+TOL_EPS = 1e-9
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_07820_gb300 as dg
+    return dg
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = {
+    "p4_432_nl": (small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True), (0.3, -0.2, 0.45)),
+    "p6_223_nl": (small_case(1, n=(2, 2, 3), p=6, L=7.0, nl=True), (math.pi / 7.0, 0.0, 0.0)),
+    "p3_333_gll": (small_case(2, n=(3, 3, 3), p=3, L=6.0, nl=False, vquad=1), (0.1, 0.25, -0.6)),
+}
+
+
+def _disp(xyz, c):
+    if c["proj"] is None:
+        return None
+    cent, w, rc, hc = c["proj"]
+    return synth.projector_disp(xyz, cent, rc, c["L"])
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def pair(request, dg):
+    c, k = CASES[request.param]
+    om, oh = oracle_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    B = kpoint.BlochHamiltonian(oh, k)
+    if c["proj"] is not None:
+        cent, w, rc, hc = c["proj"]
+        rp, nd, chi = synth.projector_csr(om.node_xyz(), cent, w, rc, c["L"])
+        B.set_nonlocal(hc, rp, nd, chi, _disp(om.node_xyz(), c))
+    mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    nxyz, _ = dg.dftfe_mesh_coords(mesh, quad=False)
+    dg.dftfe_ham_set_kpoint(ham, k, _disp(nxyz, c))
+    yield om, B, mesh, ham
+    dg.dftfe_ham_destroy(ham)
+    dg.dftfe_mesh_destroy(mesh)
+
+
+def _zblock(seed, M, ncol):
+    return synth.random_block(seed, M, 2 * ncol).view(np.complex128)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("ncol", [1, 2, 5, 37])
+def test_apply_z(dg, pair, ncol):
+    om, B, mesh, ham = pair
+    X0 = _zblock(200 + ncol, om.ndofs, ncol)
+    X = _t(X0)
+    Y = torch.full_like(X, complex("nan"))
+    dg.dftfe_ham_apply_z(ham, X, Y)
+    assert _rel(Y.cpu().numpy(), B.apply(X0)) < TOL_APPLY
+
+
+def test_apply_z_column_slice_and_determinism(dg, pair):
+    om, B, mesh, ham = pair
+    X0 = _zblock(9, om.ndofs, 50)
+    X = _t(X0)
+    Y = torch.zeros_like(X)
+    dg.dftfe_ham_apply_z(ham, X[:, 10:45], Y[:, 10:45])
+    assert _rel(Y[:, 10:45].cpu().numpy(), B.apply(X0[:, 10:45])) < TOL_APPLY
+    assert torch.count_nonzero(Y[:, :10]) == 0
+    Y2 = torch.zeros_like(X)
+    dg.dftfe_ham_apply_z(ham, X[:, 10:45], Y2[:, 10:45])
+    assert torch.equal(Y, Y2)
+
+
+@pytest.mark.parametrize("scaled", [True, False])
+@pytest.mark.parametrize("ncol,degree", [(6, 1), (37, 9)])
+def test_chebyshev_filter_z(dg, pair, scaled, ncol, degree):
+    om, B, mesh, ham = pair
+    tmin, tmax, b = kpoint.spectrum_bounds(B, synth.counter_uniform(5, 2 * om.ndofs), 20)
+    bd = oracle.Bounds(tmin + 0.1 * (b - tmin), b, tmin if scaled else math.nan)
+    X0 = _zblock(11, om.ndofs, ncol)
+    X = _t(X0)
+    dg.dftfe_chebyshev_filter_z(ham, X, degree, dg.make_bounds(bd.a, bd.b, bd.a0))
+    ref = oracle.chebyshev_filter(B.apply, X0, degree, bd)
+    assert _rel(X.cpu().numpy(), ref) < 1e-10
+
+
+def test_lanczos_z(dg, pair):
+    om, B, mesh, ham = pair
+    v0 = synth.counter_uniform(21, 2 * om.ndofs)
+    ref = kpoint.spectrum_bounds(B, v0, 20)
+    got = dg.dftfe_lanczos_z(ham, 20, _t(v0))
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-10)
+    assert np.allclose(dg.dftfe_lanczos_z(ham, 20, None, 21), ref, rtol=1e-10, atol=1e-10)
+
+
+def test_cholgs_z(dg, pair):
+    om, B, mesh, ham = pair
+    N = 24
+    X0 = _zblock(12, om.ndofs, N) @ np.diag(np.linspace(1.0, 50.0, N))
+    X = _t(X0)
+    dg.dftfe_cholgs_z(ham, X)
+    ref, _, _ = kpoint.cholgs(X0)
+    x = X.cpu().numpy()
+    assert _rel(x, ref) < 1e-11
+    assert np.abs(x.conj().T @ x - np.eye(N)).max() < 1e-12
+
+
+def test_cholgs_z_not_spd_leaves_x_untouched(dg, pair):
+    om, B, mesh, ham = pair
+    X0 = _zblock(13, om.ndofs, 6)
+    X0[:, 4] = (0.3 - 0.7j) * X0[:, 1]          # complex-linearly dependent columns
+    X = _t(X0)
+    with pytest.raises(dg.DftfeError) as e:
+        dg.dftfe_cholgs_z(ham, X)
+    assert e.value.code == 4
+    assert np.array_equal(X.cpu().numpy(), X0)
+
+
+def test_rayleigh_ritz_z(dg, pair):
+    om, B, mesh, ham = pair
+    N = 20
+    Xo, _, _ = kpoint.cholgs(_zblock(14, om.ndofs, N))
+    X = _t(Xo)
+    ev = torch.empty(N, dtype=torch.float64, device="cuda")
+    HX = torch.empty_like(X)
+    dg.dftfe_rayleigh_ritz_z(ham, X, ev, HX)
+    Xr, Wr, theta, _ = kpoint.rayleigh_ritz(B.apply, Xo)
+    assert np.abs(ev.cpu().numpy() - theta).max() < 1e-11
+    x, w = X.cpu().numpy(), HX.cpu().numpy()
+    gaps = np.minimum(np.r_[np.inf, np.diff(theta)], np.r_[np.diff(theta), np.inf])
+    ok = gaps > 1e-4
+    assert ok.sum() >= N // 2
+    assert _rel(x[:, ok], Xr[:, ok]) < 1e-8           # same phase convention
+    assert _rel(w[:, ok], Wr[:, ok]) < 1e-8
+    assert np.abs(x.conj().T @ x - np.eye(N)).max() < 1e-12
+
+
+def test_residuals_z(dg, pair):
+    om, B, mesh, ham = pair
+    N = 10
+    Xo, _, _ = kpoint.cholgs(_zblock(15, om.ndofs, N))
+    Xr, Wr, theta, _ = kpoint.rayleigh_ritz(B.apply, Xo)
+    r = torch.empty(N, dtype=torch.float64, device="cuda")
+    dg.dftfe_residuals_z(ham, _t(Xr), _t(Wr), _t(theta), r)
+    assert _rel(r.cpu().numpy(), kpoint.residuals(Xr, Wr, theta)) < 1e-12
+
+
+@pytest.mark.parametrize("scaled", [True, False])
+def test_pass_sequence_z(dg, pair, scaled):
+    om, B, mesh, ham = pair
+    N, blk, deg = 14, 5, 8
+    X0 = _zblock(16, om.ndofs, N)
+    tmin, tmax, b = kpoint.spectrum_bounds(B, synth.counter_uniform(17, 2 * om.ndofs), 20)
+    bd = oracle.first_pass_bounds(tmin, b, N, om.ndofs)
+    if not scaled:
+        bd.a0 = math.nan
+    gb = dg.make_bounds(bd.a, bd.b, bd.a0)
+    X = _t(X0)
+    ev = torch.empty(N, dtype=torch.float64, device="cuda")
+    rs = torch.empty(N, dtype=torch.float64, device="cuda")
+    Xo = X0
+    for _ in range(3):
+        Xo, Wo, theta, r, bd = kpoint.chfsi_pass(B, Xo, blk, deg, bd)
+        dg.dftfe_chfsi_pass_z(ham, X, blk, deg, gb, ev, rs)
+        assert np.abs(ev.cpu().numpy() - theta).max() < TOL_EPS
+        assert np.allclose(rs.cpu().numpy(), r, rtol=1e-6, atol=1e-10)
+        assert abs(gb.a - bd.a) < TOL_EPS and (math.isnan(gb.a0) == math.isnan(bd.a0))
+
+
+def test_kpoint_bounds_from_library(dg, pair):
+    om, B, mesh, ham = pair
+    gb = dg.dftfe_spectrum_bounds_z(ham, 20, 17, 14)
+    tmin, tmax, b = kpoint.spectrum_bounds(B, synth.counter_uniform(17, 2 * om.ndofs), 20)
+    ref = oracle.first_pass_bounds(tmin, b, 14, om.ndofs)
+    assert np.allclose([gb.a, gb.b, gb.a0], [ref.a, ref.b, ref.a0], rtol=1e-10, atol=1e-10)
+
+
+def test_k_zero_complex_pass_equals_real_pass(dg):
+    """At k = 0 with a real start block the complex pass reproduces the real pass (the complex
+    Jacobi rotations reduce to the real ones up to signs, fixed by the same convention)."""
+    c = small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True)
+    mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    nxyz, _ = dg.dftfe_mesh_coords(mesh, quad=False)
+    dg.dftfe_ham_set_kpoint(ham, (0.0, 0.0, 0.0), _disp(nxyz, c))
+    M = nxyz.shape[0]
+    N = 12
+    X0 = synth.random_block(30, M, N)
+    Xr = _t(X0)
+    Xz = _t(X0.astype(np.complex128))
+    b1 = dg.dftfe_spectrum_bounds(ham, 20, 3, N)
+    b2 = dg.make_bounds(b1.a, b1.b, b1.a0)
+    ev1, rs1 = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(2))
+    ev2, rs2 = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(2))
+    for _ in range(2):
+        dg.dftfe_chfsi_pass(ham, Xr, 4, 10, b1, ev1, rs1)
+        dg.dftfe_chfsi_pass_z(ham, Xz, 4, 10, b2, ev2, rs2)
+    assert np.abs(ev1.cpu().numpy() - ev2.cpu().numpy()).max() < 1e-12
+    assert np.allclose(rs1.cpu().numpy(), rs2.cpu().numpy(), rtol=1e-8, atol=1e-12)
+    z = Xz.cpu().numpy()
+    assert np.abs(z.imag).max() < 1e-12
+    assert _rel(z.real, Xr.cpu().numpy()) < 1e-9
+    dg.dftfe_ham_destroy(ham)
+    dg.dftfe_mesh_destroy(mesh)
+
+
+def test_kpoint_state_errors(dg):
+    c = small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True)
+    mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    nxyz, _ = dg.dftfe_mesh_coords(mesh, quad=False)
+    X = torch.zeros((nxyz.shape[0], 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(dg.DftfeError) as e:
+        dg.dftfe_ham_apply_z(ham, X, torch.empty_like(X))
+    assert e.value.code == 7                               # no k-point yet
+    with pytest.raises(dg.DftfeError) as e:
+        dg.dftfe_ham_set_kpoint(ham, (0.1, 0.0, 0.0), None)
+    assert e.value.code == 1                               # projectors need displacements
+    dg.dftfe_ham_set_kpoint(ham, (0.1, 0.0, 0.0), _disp(nxyz, c))
+    dg.dftfe_ham_apply_z(ham, X, torch.empty_like(X))
+    cent, w, rc, hc = c["proj"]
+    rp, nd, chi = synth.projector_csr(nxyz, cent, w, rc, c["L"])
+    dg.dftfe_ham_set_nonlocal(ham, hc, rp, nd, chi)
+    with pytest.raises(dg.DftfeError) as e:
+        dg.dftfe_ham_apply_z(ham, X, torch.empty_like(X))
+    assert e.value.code == 7                               # stale phased projectors
+    with pytest.raises(TypeError):
+        dg.dftfe_ham_apply_z(ham, X.real.contiguous(), X.real.contiguous())
+    dg.dftfe_ham_destroy(ham)
+    dg.dftfe_mesh_destroy(mesh)
