@@ -206,6 +206,141 @@ def oracle_sample(wl, target_s=12.0):
 
 
 # ------------------------------------------------------------------ ours
+def kpoint_step(dg, dev, stream, steps=2, warmup=1):
+    """One complex128 ChFSI pass at a Bloch k-point, timed on its own (outside the pass value):
+    10 bohr cube, 8^3 cells, p = 5 (64,000 DoFs), 8 wells (depth 2 Ha, width 1 bohr) at seeded
+    uniform centres with 4 projectors each (width 1 bohr, cutoff 2.5 bohr, couplings
+    U[0.5, 2] Ha), k = (0.25, 0.10, -0.15) bohr^-1, 128 complex states, block 64, degree 20."""
+    import torch
+    L, n, p, N, blk, deg = 10.0, 8, 5, 128, 64, 20
+    kvec = (0.25, 0.10, -0.15)
+    s = synth.Stream(7)
+    cent = np.array([[L * s.uniform() for _ in range(3)] for _ in range(8)])
+    hc = np.array([0.5 + 1.5 * s.uniform() for _ in range(32)])
+    mesh = dg.dftfe_mesh_create(L, n, p)
+    ham = dg.dftfe_ham_create(mesh, stream.cuda_stream)
+    nxyz, qxyz = dg.dftfe_mesh_coords(mesh)
+    v = synth.gaussian_wells(qxyz.reshape(-1, 3), cent, 2.0, 1.0, L)
+    dg.dftfe_ham_set_potential(ham, torch.from_numpy(v).to(dev))
+    rowptr, node, chi = synth.projector_csr(nxyz, cent, 1.0, 2.5, L)
+    dg.dftfe_ham_set_nonlocal(ham, hc, rowptr, node, chi)
+    dg.dftfe_ham_set_kpoint(ham, kvec, synth.projector_disp(nxyz, cent, 2.5, L))
+    M = nxyz.shape[0]
+    Xr = torch.empty((M, 2 * N), dtype=torch.float64, device=dev)
+    dg.dftfe_random_uniform(Xr, 11)
+    X = Xr.view(torch.complex128)
+    b = dg.dftfe_spectrum_bounds_z(ham, 20, 12, N)
+    ev = torch.empty(N, dtype=torch.float64, device=dev)
+    rs = torch.empty(N, dtype=torch.float64, device=dev)
+    X0 = X.clone()
+    b0 = dg.make_bounds(b.a, b.b, b.a0)
+    for _ in range(warmup):
+        dg.dftfe_chfsi_pass_z(ham, X, blk, deg, b, ev, rs)
+    torch.cuda.synchronize()
+    dg.dftfe_profile_enable(ham, True)
+    l0 = dg.dftfe_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        dg.dftfe_chfsi_pass_z(ham, X, blk, deg, b, ev, rs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = (dg.dftfe_launch_count() - l0) // steps
+    spp = e0.elapsed_time(e1) / 1e3 / steps
+    fam = {}
+    for name in ("pass_filter", "pass_cholgs", "pass_rr", "kin_k", "nl_z", "cell_gemm_fp64", "gram", "rotate",
+                 "syevd_z"):
+        t, cnt = dg.dftfe_profile_query(ham, name)
+        if cnt:
+            fam[name] = {"ms": t / steps, "launches": cnt // steps}
+    dg.dftfe_profile_enable(ham, False)
+    nc, Nc = (p + 1) ** 3, n ** 3
+    apps = deg * N + N                                          # filter + W = H~X, complex columns
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roofs = {}
+    if "cell_gemm_fp64" in fam:
+        # the real cell products act on the real view: 2 real columns per complex column
+        a = 2.0 * Nc * nc * nc * 2 * apps / (fam["cell_gemm_fp64"]["ms"] / 1e3) / 1e12
+        roofs["cell_gemm_fp64"] = {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": a / FP64_PEAK_TFLOPS}
+    if "kin_k" in fam:
+        # FP64 work per node and complex column: 3 (p + 2) complex-by-real multiply-adds of the
+        # k.grad stencil on average (4 flops each) and the two recurrence terms (8 flops);
+        # HBM: read X_k and X_k-1, write Z (16 bytes each; the stencil neighbours are cache hits)
+        t = fam["kin_k"]["ms"] / 1e3
+        a = (12.0 * (p + 2) + 8.0) * M * apps / t / 1e12
+        gbs = 3.0 * M * 16 * apps / t / 1e9
+        roofs["kin_k"] = {"bound": "alu", "achieved": a, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": a / FP64_PEAK_TFLOPS, "hbm_achieved_gbs": gbs, "hbm_frac": gbs / hbm_peak,
+                          "note": "FP64 flops (12 (p+2) + 8) per node and complex column"}
+    # the same passes with the cell-kernel autotuner and the filter phase as a CUDA graph
+    dg.dftfe_ham_autotune(ham, True)
+    dg.dftfe_ham_use_graphs(ham, True)
+    X.copy_(X0)
+    b = b0
+    for _ in range(warmup + 1):          # tuning and the first (uncaptured) filter phase
+        dg.dftfe_chfsi_pass_z(ham, X, blk, deg, b, ev, rs)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        dg.dftfe_chfsi_pass_z(ham, X, blk, deg, b, ev, rs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spp_tg = e0.elapsed_time(e1) / 1e3 / steps
+    rows, best_ms, heur_ms = dg.dftfe_autotune_query(ham, 2 * blk)
+    out = {"workload": f"wells8-L10-8c-p5-nl-k ({M} DoFs, {N} complex states, block {blk}, degree {deg})",
+           "k": list(kvec), "s_per_pass": spp, "phases_ms_per_pass": {k: v["ms"] for k, v in fam.items()},
+           "rooflines": roofs, "gpu_launches_per_pass": launches, "max_resid": float(rs.max().item()),
+           "dtype": "c128 (FP64)",
+           "s_per_pass_autotuned_graphed": spp_tg,
+           "autotune": {"rows_per_cta": rows, "best_ms": best_ms, "heuristic_ms": heur_ms,
+                        "note": "one FP64 cell-product pass over the mesh on 2 x block real columns; "
+                                "rows_per_cta 0 = the built-in heuristic"},
+           "graph_replays": dg.dftfe_graph_query(ham)[0]}
+    dg.dftfe_ham_destroy(ham)
+    dg.dftfe_mesh_destroy(mesh)
+    return out
+
+
+def graph_step(dg, dev, stream, steps=5, warmup=3):
+    """Small-system passes (10 bohr cube, 6^3 cells, p = 4: 13,824 DoFs, 8 wells, 32 states,
+    block 32, degree 20) with plain launches and with the filter phase as a CUDA graph, FP64 and
+    TF32x3: launch-bound sizes, where the graph removes the gaps between short kernels."""
+    import torch
+    wl = synth.small_wells(0)
+    mesh = dg.dftfe_mesh_create(wl.L, wl.ncell, wl.degree)
+    ham = dg.dftfe_ham_create(mesh, stream.cuda_stream)
+    _, qxyz = dg.dftfe_mesh_coords(mesh, nodes=False)
+    v = synth.gaussian_wells(qxyz.reshape(-1, 3), wl.centres, wl.depth, wl.width, wl.L)
+    dg.dftfe_ham_set_potential(ham, torch.from_numpy(v).to(dev))
+    M, N = wl.ndofs, wl.nstates
+    X = torch.empty((M, N), dtype=torch.float64, device=dev)
+    ev = torch.empty(N, dtype=torch.float64, device=dev)
+    rs = torch.empty(N, dtype=torch.float64, device=dev)
+    out = {"workload": f"{wl.name} ({M} DoFs, {N} states, block {wl.block}, degree {wl.cheb_degree})"}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for pname, prec in (("fp64", dg.DFTFE_FP64), ("tf32x3", dg.DFTFE_MIXED_TF32X3)):
+        for graphs in (False, True):
+            dg.dftfe_ham_use_graphs(ham, graphs)
+            dg.dftfe_random_uniform(X, wl.seed)
+            b = dg.dftfe_spectrum_bounds(ham, 20, wl.seed + 1000, N)
+            for _ in range(warmup):
+                dg.dftfe_chfsi_pass(ham, X, wl.block, wl.cheb_degree, b, ev, rs, prec)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(steps):
+                dg.dftfe_chfsi_pass(ham, X, wl.block, wl.cheb_degree, b, ev, rs, prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[f"{pname}_{'graph' if graphs else 'plain'}_ms_per_pass"] = e0.elapsed_time(e1) / steps
+    dg.dftfe_ham_destroy(ham)
+    dg.dftfe_mesh_destroy(mesh)
+    return out
+
+
 def run_ours(args, rank, world, local, tdist):
     import torch
     import __graft_entry__
@@ -373,6 +508,13 @@ def run_ours(args, rank, world, local, tdist):
                 "density_fp64_tflops": 2.0 * Nc * (wl.degree + 1) ** 6 * (N + nfr) / (d1.elapsed_time(d2) / 1e3) / 1e12}
         del Xfr, rho
 
+    kstep = None
+    if not args.no_kpoint:
+        kstep = kpoint_step(dg, dev, stream)
+    gstep = None
+    if not args.no_graph_step:
+        gstep = graph_step(dg, dev, stream)
+
     # one extra FP64 pass and one pass in the timed precision from the same state: |d eps|
     compare = None
     if args.precision != "fp64" and not args.no_compare:
@@ -439,6 +581,8 @@ def run_ours(args, rank, world, local, tdist):
         "e2e": e2e,
         "mixed_vs_fp64": compare,
         "density_step": dens,
+        "kpoint_step": kstep,
+        "graph_step": gstep,
         "bounds": {"a": bounds.a, "b": bounds.b, "a0": bounds.a0},
         "max_resid": float(rs.max().item()),
     }
@@ -484,6 +628,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-density", action="store_true")
+    ap.add_argument("--no-kpoint", action="store_true")
+    ap.add_argument("--no-graph-step", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

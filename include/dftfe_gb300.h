@@ -155,6 +155,34 @@ dftfe_status dftfe_ham_export(dftfe_ham ham, double* mass, int32_t* cell_map,
 dftfe_status dftfe_ham_apply(dftfe_ham ham, const double* X, int64_t ldx,
                              double* Y, int64_t ldy, int ncol, dftfe_precision prec);
 
+/* Autotuner (no counterpart in the paper).  With enable = 1, the first FP64 cell-product
+ * pass over the mesh for each column count (real columns: 2 ncol for the _z calls) times
+ * every launch shape of the FP64 cell kernel -- 64, 128, ... rows of a cell per CTA, and the
+ * built-in heuristic -- on the caller's block into a scratch output and keeps the fastest
+ * for this ham (that first call synchronises the stream).  Every shape gives bit-identical
+ * results.  enable = 0 restores the heuristic; either call forgets earlier choices. */
+dftfe_status dftfe_ham_autotune(dftfe_ham ham, int enable);
+
+/* The tuned shape for ncol real columns: HOST rows_per_cta (0 = the heuristic won, -1 = not
+ * tuned yet), best_ms and heuristic_ms (one cell-product pass over the mesh; may be NULL). */
+dftfe_status dftfe_autotune_query(dftfe_ham ham, int ncol, int* rows_per_cta, double* best_ms,
+                                  double* heuristic_ms);
+
+/* CUDA graphs (no counterpart in the paper).  With enable = 1, the filter phase of
+ * dftfe_chfsi_pass and dftfe_chfsi_pass_z (every block's Chebyshev recurrence: about
+ * degree x (3 + colours) launches per block) runs as one CUDA graph launch: the first pass
+ * with given (precision, ncol, block, degree) runs directly, later ones capture the phase
+ * from the ham's stream and update the cached executable (bounds change only kernel
+ * arguments).  Results are bit-identical to enable = 0.  Per-kernel profiling timers
+ * (dftfe_profile_query) see the filter only as "pass_filter" while graphs are on.  Either
+ * call drops the cached graphs; synchronises the stream. */
+dftfe_status dftfe_ham_use_graphs(dftfe_ham ham, int enable);
+
+/* HOST counts since dftfe_ham_use_graphs: graph launches and instantiations (an update that
+ * the driver refuses, e.g. after a new potential adds the split-tile launches, instantiates
+ * afresh). */
+dftfe_status dftfe_graph_query(dftfe_ham ham, int64_t* replays, int64_t* instantiations);
+
 /* --------------------------------------------------------------- ChFSI steps */
 
 /* Counter-based SplitMix64 uniforms in [-1/2, 1/2) (Steele, Lea, Flood 2014):

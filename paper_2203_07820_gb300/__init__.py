@@ -81,6 +81,10 @@ _SIGS = {
     "dftfe_mlp_forward": [_vp, _int, _int, _int, _vp, _i64, _vp, _vp],
     "dftfe_mlp_loss_grad": [_vp, _int, _int, _int, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "dftfe_mlp_adam": [_vp, _vp, _vp, _vp, _i64, _int, C.c_float, C.c_float, C.c_float, C.c_float, _vp],
+    "dftfe_ham_use_graphs": [_vp, _int],
+    "dftfe_graph_query": [_vp, C.POINTER(_i64), C.POINTER(_i64)],
+    "dftfe_ham_autotune": [_vp, _int],
+    "dftfe_autotune_query": [_vp, _int, C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
     "dftfe_ham_set_kpoint": [_vp, _vp, _vp],
     "dftfe_ham_apply_z": [_vp, _vp, _i64, _vp, _i64, _int],
     "dftfe_lanczos_z": [_vp, _int, _vp, C.c_uint64, _vp],
@@ -207,6 +211,28 @@ def dftfe_ham_apply(ham, X, Y, prec=DFTFE_FP64):
     py, ldy = _dev(Y, "Y")
     ncol = 1 if X.dim() == 1 else X.shape[1]
     _check(_lib.dftfe_ham_apply(ham, px, ldx, py, ldy, ncol, prec))
+
+
+def dftfe_ham_use_graphs(ham, enable=True):
+    _check(_lib.dftfe_ham_use_graphs(ham, 1 if enable else 0))
+
+
+def dftfe_graph_query(ham):
+    """(graph launches, instantiations) since graphs were switched on."""
+    r, n = _i64(), _i64()
+    _check(_lib.dftfe_graph_query(ham, C.byref(r), C.byref(n)))
+    return r.value, n.value
+
+
+def dftfe_ham_autotune(ham, enable=True):
+    _check(_lib.dftfe_ham_autotune(ham, 1 if enable else 0))
+
+
+def dftfe_autotune_query(ham, ncol):
+    """(rows_per_cta, best_ms, heuristic_ms) for ncol real columns; rows_per_cta -1 = not tuned."""
+    r, b, hm = _int(), _dbl(), _dbl()
+    _check(_lib.dftfe_autotune_query(ham, int(ncol), C.byref(r), C.byref(b), C.byref(hm)))
+    return r.value, b.value, hm.value
 
 
 # ------------------------------------------------------------ ChFSI steps

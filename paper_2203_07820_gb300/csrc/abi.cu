@@ -4,6 +4,7 @@
 #include "internal.h"
 
 #include <cmath>
+#include <string>
 
 namespace dftfe {
 
@@ -178,13 +179,30 @@ extern "C" dftfe_status dftfe_chfsi_pass(dftfe_ham h, double* X, int64_t ld, int
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
                 "unknown precision");
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
-  auto* m = h->mesh;
   {
     ProfScope ps(h, "pass_filter");
-    for (int j0 = 0; j0 < ncol; j0 += block) {
-      const int nb = std::min(block, ncol - j0);
-      if (prec == DFTFE_FP64) chebyshev_filter(h, X + j0, ld, nb, degree, *inout);
-      else chebyshev_filter_mixed(h, X + j0, ld, nb, degree, *inout, prec == DFTFE_MIXED_TF32X3);
+    // the mixed cell kernel's timeout flag is zeroed before the filter and read after it, so
+    // the filter phase has no host read and can run as one CUDA graph
+    int* err = nullptr;
+    if (prec != DFTFE_FP64) {
+      err = (int*)ws_get(h, "mx_err", sizeof(int));
+      DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+    }
+    const dftfe_bounds bnd = *inout;
+    const std::string key = "pass/" + std::to_string((int)prec) + "/" + std::to_string(ncol) + "/" +
+                            std::to_string(block) + "/" + std::to_string(degree);
+    run_region(h, key, [&]() {
+      for (int j0 = 0; j0 < ncol; j0 += block) {
+        const int nb = std::min(block, ncol - j0);
+        if (prec == DFTFE_FP64) chebyshev_filter(h, X + j0, ld, nb, degree, bnd);
+        else chebyshev_filter_mixed(h, X + j0, ld, nb, degree, bnd, prec == DFTFE_MIXED_TF32X3, err);
+      }
+    });
+    if (err) {
+      int herr = 0;
+      DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+      if (herr) throw Error(DFTFE_ERR_TIMEOUT, "mixed cell kernel: a bounded wait timed out");
     }
   }
   chfsi_pass_tail(h, X, ld, ncol, inout, evals, resid, prec);

@@ -164,8 +164,10 @@ int fp64_row_splits(dftfe_ham h, int64_t ctas, int nc) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (nc + 63) / 64));
 }
 
-void local_part_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol,
-                     double alpha) {
+// rows_per_cta > 0 forces that many rows of a cell per CTA (a multiple of 64) in every colour;
+// 0 takes fp64_row_splits per colour.  Every choice gives the same bits (cell_fp64.cuh).
+static void local_part_rows(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol,
+                            double alpha, int rows_per_cta) {
   auto* m = h->mesh;
   set_smem_attrs();
   const int nc = m->nc;
@@ -186,12 +188,64 @@ void local_part_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64
       size_t sh = (size_t)nc * 32 * sizeof(double) + nc * sizeof(int32_t);
       const int tiles = (ncol + 31) / 32;
       const int splits = fp64_row_splits(h, n * tiles, nc);
-      const int rows = ((nc + splits - 1) / splits + 63) / 64 * 64;
+      const int rows = rows_per_cta > 0 ? rows_per_cta : ((nc + splits - 1) / splits + 63) / 64 * 64;
       dim3 grid((unsigned)n, (unsigned)tiles, (unsigned)((nc + rows - 1) / rows));
       DFTFE_LAUNCH(k_cell_fp64_wide, grid, 256, sh, h->stream, h->d_Hc, h->d_map, cells, nc, X, ldx, Z,
                    ldz, ncol, alpha, rows);
     }
   }
+}
+
+// Autotuner (no counterpart in the paper, whose cell GEMMs go to a vendor batched GEMM): the
+// first local part of a given column count times every rows-per-CTA shape of the wide
+// kernel (64, 128, ... rows of a cell per CTA, and the heuristic) on the caller's X into a
+// scratch output, twice each (the first run warms up), and keeps the fastest for the ham.
+static int tuned_rows(dftfe_ham h, const double* X, int64_t ldx, int ncol) {
+  auto it = h->tuned_fp64.find(ncol);
+  if (it != h->tuned_fp64.end()) return it->second.rows;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DFTFE_CHECK_CUDA(cudaStreamIsCapturing(h->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return 0;   // no timing inside a graph capture
+  auto* m = h->mesh;
+  double* Zs = (double*)ws_get(h, "tune_z", sizeof(double) * (size_t)m->M * ncol);
+  DFTFE_CHECK_CUDA(cudaMemsetAsync(Zs, 0, sizeof(double) * (size_t)m->M * ncol, h->stream));
+  struct Ev {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Ev() { for (auto x : e) if (x) cudaEventDestroy(x); }
+  } ev;
+  for (auto& x : ev.e) DFTFE_CHECK_CUDA(cudaEventCreate(&x));
+  const bool prof = h->profiling;
+  h->profiling = false;
+  TunedShape best;
+  best.best_ms = 1e300;
+  try {
+    for (int r = 0; r <= (m->nc + 63) / 64 * 64; r += 64) {
+      local_part_rows(h, X, ldx, Zs, ncol, ncol, 1.0, r);
+      DFTFE_CHECK_CUDA(cudaEventRecord(ev.e[0], h->stream));
+      local_part_rows(h, X, ldx, Zs, ncol, ncol, 1.0, r);
+      DFTFE_CHECK_CUDA(cudaEventRecord(ev.e[1], h->stream));
+      DFTFE_CHECK_CUDA(cudaEventSynchronize(ev.e[1]));
+      float ms = 0.f;
+      DFTFE_CHECK_CUDA(cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]));
+      if (r == 0) best.heuristic_ms = ms;
+      if (ms < best.best_ms) {
+        best.best_ms = ms;
+        best.rows = r;
+      }
+    }
+  } catch (...) {
+    h->profiling = prof;
+    throw;
+  }
+  h->profiling = prof;
+  h->tuned_fp64[ncol] = best;
+  return best.rows;
+}
+
+void local_part_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol,
+                     double alpha) {
+  const int rows = h->autotune && ncol > 4 ? tuned_rows(h, X, ldx, ncol) : 0;
+  local_part_rows(h, X, ldx, Z, ldz, ncol, alpha, rows);
 }
 
 // Z += alpha H~_nl X (FP64), nothing without projectors
@@ -289,6 +343,35 @@ extern "C" dftfe_status dftfe_ham_apply(dftfe_ham h, const double* X, int64_t ld
   if (prec == DFTFE_FP64) apply_combo(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
   else if (prec == DFTFE_FP64_FLOAT_PAIRS) apply_df(h, X, ldx, Y, ldy, ncol);
   else apply_mixed(h, X, ldx, Y, ldy, ncol, prec == DFTFE_MIXED_TF32X3);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_ham_autotune(dftfe_ham h, int enable) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h, "null ham");
+  DFTFE_REQUIRE(enable == 0 || enable == 1, "enable must be 0 or 1");
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  h->autotune = enable == 1;
+  h->tuned_fp64.clear();
+  // cached graphs hold the old launch shapes: the next pass of each runs directly again
+  for (auto& kv : h->graphs) kv.second.warm = false;
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_autotune_query(dftfe_ham h, int ncol, int* rows_per_cta, double* best_ms,
+                                             double* heuristic_ms) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && rows_per_cta, "null argument");
+  auto it = h->tuned_fp64.find(ncol);
+  if (it == h->tuned_fp64.end()) {
+    *rows_per_cta = -1;
+    if (best_ms) *best_ms = 0.0;
+    if (heuristic_ms) *heuristic_ms = 0.0;
+  } else {
+    *rows_per_cta = it->second.rows;
+    if (best_ms) *best_ms = it->second.best_ms;
+    if (heuristic_ms) *heuristic_ms = it->second.heuristic_ms;
+  }
   ABI_END
 }
 

@@ -564,7 +564,7 @@ static bool g_mixed_attr = false;
 // Eq. chebyfilter with FP32 vectors and split-precision cell products; the caller's FP64
 // block is converted in and out.
 void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int degree, const dftfe_bounds& b,
-                            bool tf32) {
+                            bool tf32, int* ext_err) {
   if (degree <= 0 || ncol <= 0) return;
   auto* m = h->mesh;
   if (!g_mixed_attr) {
@@ -579,8 +579,10 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
   buf[0] = (float*)ws_get(h, "mx_v0", sizeof(float) * m->M * (size_t)ld32);
   buf[1] = (float*)ws_get(h, "mx_v1", sizeof(float) * m->M * (size_t)ld32);
   buf[2] = (float*)ws_get(h, "mx_v2", sizeof(float) * m->M * (size_t)ld32);
-  int* err = (int*)ws_get(h, "mx_err", sizeof(int));
-  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  // with ext_err the caller owns the timeout flag (zeroed and read by the caller, so a whole
+  // pass can be enqueued, or captured in a graph, without a host read in between)
+  int* err = ext_err ? ext_err : (int*)ws_get(h, "mx_err", sizeof(int));
+  if (!ext_err) DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
   DFTFE_LAUNCH(k_to_f32, nblk(m->M * ncol), 256, 0, h->stream, X, ld, buf[0], ld32, m->M, ncol);
   const double e = (b.b - b.a) / 2.0, c = (b.b + b.a) / 2.0;
   const bool scaled = !std::isnan(b.a0);
@@ -611,6 +613,7 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
     cur = out;
   }
   DFTFE_LAUNCH(k_to_f64, nblk(m->M * ncol), 256, 0, h->stream, buf[cur], ld32, X, ld, m->M, ncol);
+  if (ext_err) return;
   int herr = 0;
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));

@@ -9,6 +9,7 @@
 #include <map>
 #include <stdexcept>
 #include <atomic>
+#include <functional>
 
 #include "../../include/dftfe_gb300.h"
 
@@ -90,6 +91,23 @@ struct DevBuf {
   void release();
 };
 
+// One autotuned launch shape of the FP64 cell kernel (rows of a cell per CTA; 0 = the
+// built-in heuristic) with its time and the heuristic's for one local part.
+struct TunedShape {
+  int rows = 0;
+  double best_ms = 0.0;
+  double heuristic_ms = 0.0;
+};
+
+// A CUDA graph of one enqueued region (graph.cu), re-captured on every call and applied to the
+// cached executable by cudaGraphExecUpdate (new bounds change only kernel arguments).
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  bool warm = false;      // the region has run once without capture (workspaces allocated)
+  int64_t replays = 0;
+  int64_t reinstantiations = 0;
+};
+
 struct KernelTimer {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
   size_t used = 0;
@@ -142,6 +160,13 @@ struct dftfe_ham_s {
   double* d_ktab = nullptr;        // 3 x p x (2p+1): k_d G~1_d stencil per axis (see kpoint.cu)
   double* d_pval_z = nullptr;      // nnz complex, projector-major: M^1/2 chi e^{-ik.d}
   double* d_sval_z = nullptr;      // the same values node-major
+  // CUDA graphs of the pass's filter phase (dftfe_ham_use_graphs), one slot per shape
+  bool use_graphs = false;
+  std::map<std::string, dftfe::GraphSlot> graphs;
+  cudaStream_t capture_stream = nullptr;   // private stream the regions are captured from
+  // autotuner (dftfe_ham_autotune): FP64 cell-kernel shape per real column count
+  bool autotune = false;
+  std::map<int, dftfe::TunedShape> tuned_fp64;
   // workspace
   std::map<std::string, dftfe::DevBuf> ws;
   // profiling
@@ -172,8 +197,10 @@ void copy_block(cudaStream_t s, const double* src, int64_t lds, double* dst, int
                 int64_t rows, int ncol);
 
 // hx_mixed.cu
+// ext_err: a device flag the caller zeroes and reads (a bounded wait timed out); NULL makes
+// the call zero and read its own (and synchronise)
 void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int degree,
-                            const dftfe_bounds& b, bool tf32);
+                            const dftfe_bounds& b, bool tf32, int* ext_err = nullptr);
 void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32);
 void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol);
 // hx.cu: Y = H~_nl X (Y overwritten; zero when there are no projectors), FP64
@@ -221,6 +248,12 @@ void syevd_z(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_sta
 
 // hx.cu: Z += alpha H~_loc X over all colours (FP64 cell products), ncol real columns
 void local_part_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64_t ldz, int ncol, double alpha);
+
+// graph.cu: run `enqueue` (work on h->stream only, no host synchronisation, no allocation
+// once it has run with the same key) directly, or through the CUDA graph slot `key` when the
+// ham uses graphs: the first call with a key runs directly, later ones capture and replay.
+void run_region(dftfe_ham h, const std::string& key, const std::function<void()>& enqueue);
+void free_graphs(dftfe_ham h);
 
 // kpoint.cu: Z = alpha H~^k X + s1 X + s2 Xp on complex blocks (ld in complex elements)
 void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, int64_t ldp, double* Z,

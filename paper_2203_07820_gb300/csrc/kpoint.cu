@@ -13,10 +13,11 @@
 // nodes, G_d is the 1D periodic derivative matrix G1_d (entries int l_a l_b' = w_a l_b'(x_a),
 // exact under GLL) along axis d times the 1D lumped masses of the two other axes, and the
 // Loewdin scaling cancels those, so G~_d = G~1_d along axis d with G~1_d = m_d^-1/2 G1_d
-// m_d^-1/2.  A stencil kernel applies it (2p+1 neighbours per axis), fused with the
-// recurrence terms.  Dense complex cell matrices (the paper's form) would make every cell
-// product four real FP64 products; here the cell products stay real and the k-dependent
-// part costs 3 (2p+1) complex multiply-adds per entry.
+// m_d^-1/2.  A stencil kernel applies it (p+1 neighbours per axis inside an element, 2p+1
+// on element faces), fused with the recurrence terms.  Dense complex cell matrices (the
+// paper's form) would make every cell product four real FP64 products; here the cell
+// products stay real and the k-dependent part costs 3 (p+2) complex-by-real multiply-adds
+// per entry on average (the kernel is bound by GB300's FP64 pipe, not by HBM).
 //
 // CholGS and Rayleigh-Ritz work on the real view.  With Xr the real view of X (M x 2N), the
 // real Gram G = Xr^T Xr holds every real inner product, and the complex S = X^H X is
@@ -31,6 +32,7 @@
 #include "internal.h"
 
 #include <cmath>
+#include <string>
 #include <vector>
 
 namespace dftfe {
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(256) k_kin_init(double2* __restrict__ Z, int64
                                                   const double2* __restrict__ Xp, int64_t ldp, int64_t M,
                                                   int ncol, double s1, double s2, double alpha,
                                                   const double* __restrict__ tab, int p, int64_t g0,
-                                                  int64_t g1) {
+                                                  int64_t g1, int kbits) {
   extern __shared__ double ts[];
   const int W = 2 * p + 1;
   for (int t = threadIdx.x; t < 3 * p * W; t += blockDim.x) ts[t] = tab[t];
@@ -66,18 +68,22 @@ __global__ void __launch_bounds__(256) k_kin_init(double2* __restrict__ Z, int64
   const int64_t pos[3] = {ix, iy, iz};
   const int64_t ext[3] = {g0, g1, g2};
   const int64_t stride[3] = {1, g0, g0 * g1};
+  const bool kmask[3] = {(kbits & 1) != 0, (kbits & 2) != 0, (kbits & 4) != 0};   // k_d != 0
   double sr = 0.0, si = 0.0;
+  // the structural non-zeros of row a: offsets -a..p-a within the node's cell, and for a = 0
+  // also -p..-1 in the previous cell (integer bounds: the FP64 pipe only does the products)
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double* T = ts + ((size_t)d * p + pos[d] % p) * W;
-    for (int o = -p; o <= p; ++o) {
-      const double tv = T[o + p];
-      if (tv == 0.0) continue;
+    if (!kmask[d]) continue;
+    const int a = (int)(pos[d] % p);
+    const double* T = ts + ((size_t)d * p + a) * W + p;
+    const int olo = a == 0 ? -p : -a;
+    for (int o = olo; o <= p - a; ++o) {
       int64_t j = pos[d] + o;
       j += j < 0 ? ext[d] : (j >= ext[d] ? -ext[d] : 0);
       const double2 v = X[(i + (j - pos[d]) * stride[d]) * ldx + c];
-      sr = fma(tv, v.x, sr);
-      si = fma(tv, v.y, si);
+      sr = fma(T[o], v.x, sr);
+      si = fma(T[o], v.y, si);
     }
   }
   const double2 xv = X[i * ldx + c];
@@ -252,7 +258,7 @@ void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, 
     const size_t sh = sizeof(double) * 3 * p * (2 * p + 1);
     DFTFE_LAUNCH(k_kin_init, nblk(m->M * ncol), 256, sh, h->stream, (double2*)Z, ldz, (const double2*)X, ldx,
                  (const double2*)Xp, ldp, m->M, ncol, s1 + 0.5 * alpha * k2, s2, alpha, h->d_ktab, p, m->g[0],
-                 m->g[1]);
+                 m->g[1], (h->kvec[0] != 0.0 ? 1 : 0) | (h->kvec[1] != 0.0 ? 2 : 0) | (h->kvec[2] != 0.0 ? 4 : 0));
   }
   if (h->nproj > 0) {
     ProfScope ps(h, "nl_z");
@@ -478,8 +484,13 @@ extern "C" dftfe_status dftfe_chfsi_pass_z(dftfe_ham h, double* X, int64_t ld, i
   auto* m = h->mesh;
   {
     ProfScope ps(h, "pass_filter");
-    for (int j0 = 0; j0 < ncol; j0 += block)
-      chebyshev_filter_z(h, X + 2 * (int64_t)j0, ld, std::min(block, ncol - j0), degree, *inout);
+    const dftfe_bounds bnd = *inout;
+    const std::string key = "pass_z/" + std::to_string(ncol) + "/" + std::to_string(block) + "/" +
+                            std::to_string(degree);
+    run_region(h, key, [&]() {
+      for (int j0 = 0; j0 < ncol; j0 += block)
+        chebyshev_filter_z(h, X + 2 * (int64_t)j0, ld, std::min(block, ncol - j0), degree, bnd);
+    });
   }
   {
     ProfScope ps(h, "pass_cholgs");

@@ -1,0 +1,160 @@
+"""CUDA graphs of the pass's filter phase and the FP64 cell-kernel autotuner: both change only
+how the work is launched, so every result must be bit-identical to the plain launches."""
+import math
+import numpy as np
+import pytest
+
+import synth
+from systems import gpu_system, small_case
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2203_07820_gb300 as dg
+    return dg
+
+
+def _sys(dg, c):
+    return gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+
+
+def _disp(dg, mesh, c):
+    nxyz, _ = dg.dftfe_mesh_coords(mesh, quad=False)
+    cent, w, rc, hc = c["proj"]
+    return synth.projector_disp(nxyz, cent, rc, c["L"])
+
+
+@pytest.mark.parametrize("prec_name", ["DFTFE_FP64", "DFTFE_MIXED_TF32X3"])
+@pytest.mark.parametrize("scaled", [True, False])
+def test_graphed_pass_is_bit_identical(dg, prec_name, scaled):
+    prec = getattr(dg, prec_name)
+    c = small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True)
+    (m1, h1), (m2, h2) = _sys(dg, c), _sys(dg, c)
+    dg.dftfe_ham_use_graphs(h2, True)
+    M = dg.dftfe_mesh_info(m1)[0]
+    N, blk, deg = 20, 8, 9
+    X0 = torch.from_numpy(synth.random_block(5, M, N)).cuda()
+    X1, X2 = X0.clone(), X0.clone()
+    b = dg.dftfe_spectrum_bounds(h1, 20, 3, N)
+    if not scaled:
+        b.a0 = math.nan
+    b1, b2 = dg.make_bounds(b.a, b.b, b.a0), dg.make_bounds(b.a, b.b, b.a0)
+    e1, r1, e2, r2 = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(4))
+    for it in range(4):
+        dg.dftfe_chfsi_pass(h1, X1, blk, deg, b1, e1, r1, prec)
+        dg.dftfe_chfsi_pass(h2, X2, blk, deg, b2, e2, r2, prec)
+        assert torch.equal(e1, e2) and torch.equal(r1, r2) and torch.equal(X1, X2), it
+        assert (b1.a, b1.a0) == (b2.a, b2.a0) or (math.isnan(b1.a0) and b1.a == b2.a)
+    replays, inst = dg.dftfe_graph_query(h2)
+    assert replays == 3 and inst >= 1                  # the first pass ran without a graph
+    for h, m in ((h1, m1), (h2, m2)):
+        dg.dftfe_ham_destroy(h)
+        dg.dftfe_mesh_destroy(m)
+
+
+def test_graphed_pass_survives_a_new_potential(dg):
+    """A new potential adds the split-tile launches to the next mixed filter (another graph
+    topology): the executable is instantiated afresh and the results stay identical."""
+    c = small_case(1, n=(2, 2, 3), p=6, L=7.0, nl=True)
+    (m1, h1), (m2, h2) = _sys(dg, c), _sys(dg, c)
+    dg.dftfe_ham_use_graphs(h2, True)
+    M = dg.dftfe_mesh_info(m1)[0]
+    _, qxyz = dg.dftfe_mesh_coords(m1, nodes=False)
+    N, blk, deg = 12, 12, 6
+    X1 = torch.from_numpy(synth.random_block(6, M, N)).cuda()
+    X2 = X1.clone()
+    b = dg.dftfe_spectrum_bounds(h1, 20, 3, N)
+    b1, b2 = dg.make_bounds(b.a, b.b, b.a0), dg.make_bounds(b.a, b.b, b.a0)
+    e1, r1, e2, r2 = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(4))
+    for it in range(4):
+        if it == 2:
+            v = synth.gaussian_wells(qxyz.reshape(-1, 3), c["centres"] + 0.05, c["depth"], c["width"], c["L"])
+            for h in (h1, h2):
+                dg.dftfe_ham_set_potential(h, torch.from_numpy(v).cuda())
+        dg.dftfe_chfsi_pass(h1, X1, blk, deg, b1, e1, r1, dg.DFTFE_MIXED_TF32X3)
+        dg.dftfe_chfsi_pass(h2, X2, blk, deg, b2, e2, r2, dg.DFTFE_MIXED_TF32X3)
+        assert torch.equal(e1, e2) and torch.equal(X1, X2), it
+    replays, inst = dg.dftfe_graph_query(h2)
+    assert replays == 3 and inst >= 2
+    for h, m in ((h1, m1), (h2, m2)):
+        dg.dftfe_ham_destroy(h)
+        dg.dftfe_mesh_destroy(m)
+
+
+def test_graphed_complex_pass_is_bit_identical(dg):
+    c = small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True)
+    (m1, h1), (m2, h2) = _sys(dg, c), _sys(dg, c)
+    k = (0.3, -0.2, 0.45)
+    for h, m in ((h1, m1), (h2, m2)):
+        dg.dftfe_ham_set_kpoint(h, k, _disp(dg, m, c))
+    dg.dftfe_ham_use_graphs(h2, True)
+    M = dg.dftfe_mesh_info(m1)[0]
+    N, blk, deg = 10, 4, 7
+    X1 = torch.from_numpy(synth.random_block(8, M, 2 * N).view(np.complex128)).cuda()
+    X2 = X1.clone()
+    b = dg.dftfe_spectrum_bounds_z(h1, 20, 3, N)
+    b1, b2 = dg.make_bounds(b.a, b.b, b.a0), dg.make_bounds(b.a, b.b, b.a0)
+    e1, r1, e2, r2 = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(4))
+    for it in range(3):
+        dg.dftfe_chfsi_pass_z(h1, X1, blk, deg, b1, e1, r1)
+        dg.dftfe_chfsi_pass_z(h2, X2, blk, deg, b2, e2, r2)
+        assert torch.equal(e1, e2) and torch.equal(X1, X2), it
+    assert dg.dftfe_graph_query(h2)[0] == 2
+    for h, m in ((h1, m1), (h2, m2)):
+        dg.dftfe_ham_destroy(h)
+        dg.dftfe_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("case", [small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True),
+                                  small_case(1, n=(2, 2, 3), p=6, L=7.0, nl=True)])
+def test_autotuned_apply_is_bit_identical(dg, case):
+    (m1, h1), (m2, h2) = _sys(dg, case), _sys(dg, case)
+    dg.dftfe_ham_autotune(h2, True)
+    M, _, nc, _ = dg.dftfe_mesh_info(m1)
+    assert dg.dftfe_autotune_query(h2, 40)[0] == -1
+    X = torch.from_numpy(synth.random_block(9, M, 40)).cuda()
+    Y1, Y2 = torch.empty_like(X), torch.empty_like(X)
+    dg.dftfe_ham_apply(h1, X, Y1)
+    dg.dftfe_ham_apply(h2, X, Y2)
+    assert torch.equal(Y1, Y2)
+    rows, best, heur = dg.dftfe_autotune_query(h2, 40)
+    assert rows == 0 or (rows % 64 == 0 and 64 <= rows <= (nc + 63) // 64 * 64)
+    assert 0 < best <= heur
+    dg.dftfe_ham_apply(h2, X, Y2)                      # tuned shape reused
+    assert torch.equal(Y1, Y2)
+    dg.dftfe_ham_autotune(h2, False)
+    assert dg.dftfe_autotune_query(h2, 40)[0] == -1
+    for h, m in ((h1, m1), (h2, m2)):
+        dg.dftfe_ham_destroy(h)
+        dg.dftfe_mesh_destroy(m)
+
+
+def test_autotuned_graphed_complex_pass_matches_plain(dg):
+    c = small_case(1, n=(2, 2, 3), p=6, L=7.0, nl=True)
+    (m1, h1), (m2, h2) = _sys(dg, c), _sys(dg, c)
+    for h, m in ((h1, m1), (h2, m2)):
+        dg.dftfe_ham_set_kpoint(h, (math.pi / 7.0, 0.0, 0.1), _disp(dg, m, c))
+    dg.dftfe_ham_autotune(h2, True)
+    dg.dftfe_ham_use_graphs(h2, True)
+    M = dg.dftfe_mesh_info(m1)[0]
+    N = 16
+    X1 = torch.from_numpy(synth.random_block(10, M, 2 * N).view(np.complex128)).cuda()
+    X2 = X1.clone()
+    b = dg.dftfe_spectrum_bounds_z(h1, 20, 4, N)
+    b1, b2 = dg.make_bounds(b.a, b.b, b.a0), dg.make_bounds(b.a, b.b, b.a0)
+    e1, r1, e2, r2 = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(4))
+    for _ in range(3):
+        dg.dftfe_chfsi_pass_z(h1, X1, 8, 8, b1, e1, r1)
+        dg.dftfe_chfsi_pass_z(h2, X2, 8, 8, b2, e2, r2)
+        assert torch.equal(e1, e2) and torch.equal(X1, X2)
+    assert dg.dftfe_autotune_query(h2, 16)[0] >= 0     # 8 complex columns = 16 real ones
+    for h, m in ((h1, m1), (h2, m2)):
+        dg.dftfe_ham_destroy(h)
+        dg.dftfe_mesh_destroy(m)
