@@ -290,6 +290,28 @@ def kpoint_step(dg, dev, stream, steps=2, warmup=1):
     torch.cuda.synchronize()
     spp_tg = e0.elapsed_time(e1) / 1e3 / steps
     rows, best_ms, heur_ms = dg.dftfe_autotune_query(ham, 2 * blk)
+    # the complex64 form (TF32x3 split cell products, FP32 complex vectors; CholGS / RR mixed on
+    # the real view, W from float pairs), and its Ritz values against a complex128 pass taken
+    # from the same state
+    X.copy_(X0)
+    b = dg.make_bounds(b0.a, b0.b, b0.a0)
+    for _ in range(warmup + 1):
+        dg.dftfe_chfsi_pass_z(ham, X, blk, deg, b, ev, rs, dg.DFTFE_MIXED_TF32X3)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        dg.dftfe_chfsi_pass_z(ham, X, blk, deg, b, ev, rs, dg.DFTFE_MIXED_TF32X3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spp_c64 = e0.elapsed_time(e1) / 1e3 / steps
+    Xa = X.clone()
+    ba, bb = dg.make_bounds(b.a, b.b, b.a0), dg.make_bounds(b.a, b.b, b.a0)
+    eva = torch.empty_like(ev)
+    dg.dftfe_chfsi_pass_z(ham, Xa, blk, deg, ba, eva, rs)
+    dg.dftfe_chfsi_pass_z(ham, X, blk, deg, bb, ev, rs, dg.DFTFE_MIXED_TF32X3)
+    torch.cuda.synchronize()
+    deps = float((ev[:N // 2] - eva[:N // 2]).abs().max().item())
+    del Xa
     out = {"workload": f"wells8-L10-8c-p5-nl-k ({M} DoFs, {N} complex states, block {blk}, degree {deg})",
            "k": list(kvec), "s_per_pass": spp, "phases_ms_per_pass": {k: v["ms"] for k, v in fam.items()},
            "rooflines": roofs, "gpu_launches_per_pass": launches, "max_resid": float(rs.max().item()),
@@ -298,7 +320,9 @@ def kpoint_step(dg, dev, stream, steps=2, warmup=1):
            "autotune": {"rows_per_cta": rows, "best_ms": best_ms, "heuristic_ms": heur_ms,
                         "note": "one FP64 cell-product pass over the mesh on 2 x block real columns; "
                                 "rows_per_cta 0 = the built-in heuristic"},
-           "graph_replays": dg.dftfe_graph_query(ham)[0]}
+           "graph_replays": dg.dftfe_graph_query(ham)[0],
+           "s_per_pass_c64_tf32x3": spp_c64,
+           "c64_vs_c128_max_abs_deps_lower_half_Ha": deps}
     dg.dftfe_ham_destroy(ham)
     dg.dftfe_mesh_destroy(mesh)
     return out

@@ -316,9 +316,12 @@ dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, int ncol, vo
  * Non-finite k or displacements: DFTFE_ERR_ARG.  Synchronises the stream. */
 dftfe_status dftfe_ham_set_kpoint(dftfe_ham ham, const double* k, const double* disp);
 
-/* Y = H~^k X for complex M x ncol blocks (X, Y DEVICE, not overlapping). */
+/* Y = H~^k X for complex M x ncol blocks (X, Y DEVICE, not overlapping).  prec as in
+ * dftfe_ham_apply: FP64; DFTFE_FP64_FLOAT_PAIRS (local part from float pairs, k terms and
+ * projectors FP64: the W of a mixed complex pass); or a split precision (FP32 complex inside:
+ * the split cell products act on the real view, the k terms and projectors in FP32). */
 dftfe_status dftfe_ham_apply_z(dftfe_ham ham, const double* X, int64_t ldx, double* Y,
-                               int64_t ldy, int ncol);
+                               int64_t ldy, int ncol, dftfe_precision prec);
 
 /* dftfe_lanczos on the real 2M x 2M form of H~^k (the same spectrum, each eigenvalue
  * twice), acting on the real view of one complex vector: v0 DEVICE, 2M doubles (M complex),
@@ -330,30 +333,41 @@ dftfe_status dftfe_lanczos_z(dftfe_ham ham, int k, const double* v0, uint64_t se
 dftfe_status dftfe_spectrum_bounds_z(dftfe_ham ham, int k, uint64_t seed, int nstates,
                                      dftfe_bounds* out);
 
-/* dftfe_chebyshev_filter (FP64) on a complex block with H~^k. */
+/* dftfe_chebyshev_filter on a complex block with H~^k.  A split precision runs the
+ * complex64 form: FP32 complex vectors, split cell products on the real view, the k terms
+ * and projectors in FP32. */
 dftfe_status dftfe_chebyshev_filter_z(dftfe_ham ham, double* X, int64_t ld, int ncol,
-                                      int degree, const dftfe_bounds* bounds);
+                                      int degree, const dftfe_bounds* bounds,
+                                      dftfe_precision prec);
 
 /* Cholesky-Gram-Schmidt on a complex block: S = X^H X, S = L L^H, X <- X L^-H
- * (1 <= ncol <= 1024).  DFTFE_ERR_NOT_SPD as dftfe_cholgs.  Synchronises the stream. */
-dftfe_status dftfe_cholgs_z(dftfe_ham ham, double* X, int64_t ld, int ncol);
+ * (1 <= ncol <= 1024).  A split precision selects the mixed overlap and rotation of
+ * dftfe_cholgs on the real view of X.  DFTFE_ERR_NOT_SPD as dftfe_cholgs.  Synchronises the
+ * stream. */
+dftfe_status dftfe_cholgs_z(dftfe_ham ham, double* X, int64_t ld, int ncol, dftfe_precision prec);
 
 /* Rayleigh-Ritz on an orthonormal complex block: W = H~^k X, H^ = X^H W (lower triangle,
  * Hermitian), H^ = Q Theta Q^H (Theta ascending, phases as above), X <- X Q.  evals: DEVICE
  * ncol doubles.  HX: DEVICE complex M x ncol (ldhx) receiving W Q, or NULL.  1 <= ncol <=
  * 1024.  Synchronises the stream. */
 dftfe_status dftfe_rayleigh_ritz_z(dftfe_ham ham, double* X, int64_t ld, int ncol,
-                                   double* evals, double* HX, int64_t ldhx);
+                                   double* evals, double* HX, int64_t ldhx,
+                                   dftfe_precision prec);
 
-/* Residual norms ||w_i - theta_i x_i||_2 of complex columns (X, HX complex with ld;
- * evals, resid DEVICE ncol doubles). */
+/* Residual norms of complex columns as dftfe_residuals (kind 0: ||w_i - theta_i x_i||_2;
+ * kind 1: the generalised form with psi = M^-1/2 x), |.| the complex modulus (X, HX complex
+ * with ld; evals, resid DEVICE ncol doubles). */
 dftfe_status dftfe_residuals_z(dftfe_ham ham, const double* X, const double* HX, int64_t ld,
-                               int ncol, const double* evals, double* resid);
+                               int ncol, const double* evals, double* resid, int kind);
 
-/* One ChFSI pass on a complex block at the ham's k-point, as dftfe_chfsi_pass with FP64
- * arithmetic (1 <= ncol <= 1024).  Synchronises the stream. */
+/* One ChFSI pass on a complex block at the ham's k-point, as dftfe_chfsi_pass
+ * (1 <= ncol <= 1024): DFTFE_FP64 is the complex128 form; a split precision the complex64
+ * form (filter in FP32 complex with split cell products; mixed overlap, projection and
+ * rotations on the real view; W from float pairs; Cholesky, eigensolve and residuals FP64).
+ * Synchronises the stream. */
 dftfe_status dftfe_chfsi_pass_z(dftfe_ham ham, double* X, int64_t ld, int ncol, int block,
-                                int degree, dftfe_bounds* inout, double* evals, double* resid);
+                                int degree, dftfe_bounds* inout, double* evals, double* resid,
+                                dftfe_precision prec);
 
 /* ------------------------------------------------------------ batched passes */
 /* Several independent systems (Gamma point, FP64) of uneven mesh size, degree, state count

@@ -145,10 +145,17 @@ def rayleigh_ritz(apply, X):
     return X @ Q, W @ Q, theta, Hh
 
 
-def residuals(X, W, theta):
-    """||w_i - theta_i x_i||_2 for unit x_i."""
+def residuals(X, W, theta, mass=None):
+    """||w_i - theta_i x_i||_2 for unit x_i, and with the lumped mass the generalised form
+    ||H psi - theta M psi|| / ||psi||, psi = M^-1/2 x (chfsi.residuals with the modulus)."""
     R = W - X * theta[None, :]
-    return np.sqrt(np.sum((R * R.conj()).real, axis=0))
+    r = np.sqrt(np.sum((R * R.conj()).real, axis=0))
+    if mass is None:
+        return r
+    m = np.asarray(mass)[:, None]
+    num = np.sqrt(np.sum(m * (R * R.conj()).real, axis=0))
+    den = np.sqrt(np.sum((X * X.conj()).real / m, axis=0))
+    return r, num / den
 
 
 def spectrum_bounds(bh, v0_real, k):

@@ -86,14 +86,14 @@ _SIGS = {
     "dftfe_ham_autotune": [_vp, _int],
     "dftfe_autotune_query": [_vp, _int, C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
     "dftfe_ham_set_kpoint": [_vp, _vp, _vp],
-    "dftfe_ham_apply_z": [_vp, _vp, _i64, _vp, _i64, _int],
+    "dftfe_ham_apply_z": [_vp, _vp, _i64, _vp, _i64, _int, _int],
     "dftfe_lanczos_z": [_vp, _int, _vp, C.c_uint64, _vp],
     "dftfe_spectrum_bounds_z": [_vp, _int, C.c_uint64, _int, C.POINTER(Bounds)],
-    "dftfe_chebyshev_filter_z": [_vp, _vp, _i64, _int, _int, C.POINTER(Bounds)],
-    "dftfe_cholgs_z": [_vp, _vp, _i64, _int],
-    "dftfe_rayleigh_ritz_z": [_vp, _vp, _i64, _int, _vp, _vp, _i64],
-    "dftfe_residuals_z": [_vp, _vp, _vp, _i64, _int, _vp, _vp],
-    "dftfe_chfsi_pass_z": [_vp, _vp, _i64, _int, _int, _int, C.POINTER(Bounds), _vp, _vp],
+    "dftfe_chebyshev_filter_z": [_vp, _vp, _i64, _int, _int, C.POINTER(Bounds), _int],
+    "dftfe_cholgs_z": [_vp, _vp, _i64, _int, _int],
+    "dftfe_rayleigh_ritz_z": [_vp, _vp, _i64, _int, _vp, _vp, _i64, _int],
+    "dftfe_residuals_z": [_vp, _vp, _vp, _i64, _int, _vp, _vp, _int],
+    "dftfe_chfsi_pass_z": [_vp, _vp, _i64, _int, _int, _int, C.POINTER(Bounds), _vp, _vp, _int],
     "dftfe_profile_enable": [_vp, _int],
     "dftfe_profile_query": [_vp, C.c_char_p, C.POINTER(_dbl), C.POINTER(_i64)],
 }
@@ -322,11 +322,11 @@ def dftfe_ham_set_kpoint(ham, k, disp=None):
         _check(_lib.dftfe_ham_set_kpoint(ham, pk, pd))
 
 
-def dftfe_ham_apply_z(ham, X, Y):
+def dftfe_ham_apply_z(ham, X, Y, prec=DFTFE_FP64):
     px, ldx = _zdev(X, "X")
     py, ldy = _zdev(Y, "Y")
     ncol = 1 if X.dim() == 1 else X.shape[1]
-    _check(_lib.dftfe_ham_apply_z(ham, px, ldx, py, ldy, ncol))
+    _check(_lib.dftfe_ham_apply_z(ham, px, ldx, py, ldy, ncol, prec))
 
 
 def dftfe_lanczos_z(ham, k, v0=None, seed=0):
@@ -342,34 +342,35 @@ def dftfe_spectrum_bounds_z(ham, k, seed, nstates):
     return b
 
 
-def dftfe_chebyshev_filter_z(ham, X, degree, bounds):
+def dftfe_chebyshev_filter_z(ham, X, degree, bounds, prec=DFTFE_FP64):
     px, ld = _zdev(X, "X")
-    _check(_lib.dftfe_chebyshev_filter_z(ham, px, ld, X.shape[1], int(degree), C.byref(bounds)))
+    _check(_lib.dftfe_chebyshev_filter_z(ham, px, ld, X.shape[1], int(degree), C.byref(bounds), prec))
 
 
-def dftfe_cholgs_z(ham, X):
+def dftfe_cholgs_z(ham, X, prec=DFTFE_FP64):
     px, ld = _zdev(X, "X")
-    _check(_lib.dftfe_cholgs_z(ham, px, ld, X.shape[1]))
+    _check(_lib.dftfe_cholgs_z(ham, px, ld, X.shape[1], prec))
 
 
-def dftfe_rayleigh_ritz_z(ham, X, evals, HX=None):
+def dftfe_rayleigh_ritz_z(ham, X, evals, HX=None, prec=DFTFE_FP64):
     px, ld = _zdev(X, "X")
     ph, ldh = _zdev(HX, "HX")
-    _check(_lib.dftfe_rayleigh_ritz_z(ham, px, ld, X.shape[1], _vp(evals.data_ptr()), ph, ldh))
+    _check(_lib.dftfe_rayleigh_ritz_z(ham, px, ld, X.shape[1], _vp(evals.data_ptr()), ph, ldh, prec))
 
 
-def dftfe_residuals_z(ham, X, HX, evals, resid):
+def dftfe_residuals_z(ham, X, HX, evals, resid, kind=0):
     px, ld = _zdev(X, "X")
     ph, ldh = _zdev(HX, "HX")
     if ldh != ld:
         raise ValueError("X and HX must share the leading dimension")
-    _check(_lib.dftfe_residuals_z(ham, px, ph, ld, X.shape[1], _vp(evals.data_ptr()), _vp(resid.data_ptr())))
+    _check(_lib.dftfe_residuals_z(ham, px, ph, ld, X.shape[1], _vp(evals.data_ptr()), _vp(resid.data_ptr()),
+                                  int(kind)))
 
 
-def dftfe_chfsi_pass_z(ham, X, block, degree, bounds, evals, resid):
+def dftfe_chfsi_pass_z(ham, X, block, degree, bounds, evals, resid, prec=DFTFE_FP64):
     px, ld = _zdev(X, "X")
     _check(_lib.dftfe_chfsi_pass_z(ham, px, ld, X.shape[1], int(block), int(degree), C.byref(bounds),
-                                   _vp(evals.data_ptr()), _vp(resid.data_ptr())))
+                                   _vp(evals.data_ptr()), _vp(resid.data_ptr()), prec))
     return bounds
 
 

@@ -146,6 +146,11 @@ void copy_block(cudaStream_t s, const double* src, int64_t lds, double* dst, int
   DFTFE_LAUNCH(k_copy_block, nblk(rows * ncol), 256, 0, s, src, lds, dst, ldd, rows, ncol);
 }
 
+void zero_block(cudaStream_t s, double* dst, int64_t ldd, int64_t rows, int ncol) {
+  if (rows * ncol == 0) return;
+  DFTFE_LAUNCH(k_axpby_init, nblk(rows * ncol), 256, 0, s, dst, ldd, nullptr, 0, nullptr, 0, rows, ncol, 0.0, 0.0);
+}
+
 static bool g_attr_set = false;
 static void set_smem_attrs() {
   if (g_attr_set) return;

@@ -523,10 +523,17 @@ static void node_slots(dftfe_ham h, const int32_t** ptr, const int32_t** slots) 
 // Z = alpha H~ X + s1 X + s2 Xp on FP32 blocks (ld multiple of 32), mixed cell products:
 // per 128-column tile, one launch of the cell kernel over all cells (per-cell outputs,
 // plain stores) and one assembly launch; then the nonlocal part.
+// kpoint: X, Xp, Z are the real views of complex blocks (ncol real columns): the real nonlocal
+// term is left out and the k-dependent terms (1/2|k|^2, -i k.grad, complex nonlocal) are
+// added after the assembly in FP32 (kpoint_add32).
 static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc, int nmt, const float* X, int64_t ldx,
                               const float* Xp, int64_t ldp, float* Z, int64_t ldz, int ncol, float alpha, float s1,
-                              float s2, int* err) {
+                              float s2, int* err, bool kpoint = false) {
   auto* m = h->mesh;
+  if (kpoint) {
+    const double k2 = h->kvec[0] * h->kvec[0] + h->kvec[1] * h->kvec[1] + h->kvec[2] * h->kvec[2];
+    s1 += (float)(0.5 * (double)alpha * k2);
+  }
   const int32_t *nptr, *nslot;
   node_slots(h, &nptr, &nslot);
   float* Yc = (float*)ws_get(h, "mx_yc", sizeof(float) * (size_t)m->Nc * m->nc * 128);
@@ -535,7 +542,7 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
   // nonlocal coefficients P = h (C~^T X) first: the assembly adds C~ P with the cell sums
   float* P = nullptr;
   const int ldP = (ncol + 3) / 4 * 4;
-  if (h->nproj > 0) {
+  if (h->nproj > 0 && !kpoint) {
     P = (float*)ws_get(h, "nl_coef32", sizeof(float) * h->nproj * (size_t)ldP);
     float* Pp = (float*)ws_get(h, "nl_coef32_part", sizeof(float) * h->nproj * (size_t)kNlSplits * ncol);
     dim3 g1((unsigned)(h->nproj * kNlSplits), (unsigned)((ncol + 127) / 128));
@@ -557,6 +564,7 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
     DFTFE_LAUNCH(k_assemble32, nblk((m->M + 7) / 8 * 256), 256, 0, h->stream, Z, ldz, X, ldx, Xp, ldp, Yc, nptr, nslot,
                  P ? h->d_nptr_all : nullptr, h->d_sproj, h->d_sval, P, ldP, m->M, col0, ncol, alpha, s1, s2);
   }
+  if (kpoint) kpoint_add32(h, X, ldx, Z, ldz, ncol / 2, alpha);
 }
 
 static bool g_mixed_attr = false;
@@ -564,7 +572,7 @@ static bool g_mixed_attr = false;
 // Eq. chebyfilter with FP32 vectors and split-precision cell products; the caller's FP64
 // block is converted in and out.
 void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int degree, const dftfe_bounds& b,
-                            bool tf32, int* ext_err) {
+                            bool tf32, int* ext_err, bool kpoint) {
   if (degree <= 0 || ncol <= 0) return;
   auto* m = h->mesh;
   if (!g_mixed_attr) {
@@ -608,7 +616,7 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
       s2 = -1.0;
     }
     apply_combo_mixed(h, tf32, A, nkc, nmt, buf[cur], ld32, prev >= 0 ? buf[prev] : nullptr, ld32, buf[out], ld32,
-                      ncol, (float)alpha, (float)s1, (float)s2, err);
+                      ncol, (float)alpha, (float)s1, (float)s2, err, kpoint);
     prev = cur;
     cur = out;
   }
@@ -621,7 +629,7 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
 }
 
 // Y = H~ X with the mixed cell products (FP64 in and out, FP32 inside); for parity tests.
-void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32) {
+void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32, bool kpoint) {
   auto* m = h->mesh;
   if (!g_mixed_attr) {
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
@@ -636,7 +644,7 @@ void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t l
   int* err = (int*)ws_get(h, "mx_err", sizeof(int));
   DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
   DFTFE_LAUNCH(k_to_f32, nblk(m->M * ncol), 256, 0, h->stream, X, ldx, x32, ld32, m->M, ncol);
-  apply_combo_mixed(h, tf32, A, nkc, nmt, x32, ld32, nullptr, 0, y32, ld32, ncol, 1.0f, 0.0f, 0.0f, err);
+  apply_combo_mixed(h, tf32, A, nkc, nmt, x32, ld32, nullptr, 0, y32, ld32, ncol, 1.0f, 0.0f, 0.0f, err, kpoint);
   DFTFE_LAUNCH(k_to_f64, nblk(m->M * ncol), 256, 0, h->stream, y32, ld32, Y, ldy, m->M, ncol);
   int herr = 0;
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -900,8 +908,14 @@ static size_t df_tiled_smem(int nc) {
   return hbytes + (size_t)nc * 32 * 8 + (size_t)((nc + 3) & ~3) * 4 + 16;
 }
 
+// Y = H~_nl X (with_nl) or 0, before the cell products add H~_loc X
+static void df_init(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl) {
+  if (with_nl) apply_nonlocal_fp64(h, X, ldx, Y, ldy, ncol);
+  else zero_block(h->stream, Y, ldy, h->mesh->M, ncol);
+}
+
 template <int TM>
-static bool apply_df_tiled(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {
+static bool apply_df_tiled(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl) {
   auto* m = h->mesh;
   const int nc = m->nc;
   if (nc > 32 * TM || nc <= 32 * (TM - 1)) return false;
@@ -921,7 +935,7 @@ static bool apply_df_tiled(dftfe_ham h, const double* X, int64_t ldx, double* Y,
   }
   int* err = (int*)ws_get(h, "df_err", sizeof(int));
   DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
-  apply_nonlocal_fp64(h, X, ldx, Y, ldy, ncol);
+  df_init(h, X, ldx, Y, ldy, ncol, with_nl);
   for (int c = 0; c < h->ncolours; ++c) {
     const int64_t n = h->colour_off[c + 1] - h->colour_off[c];
     if (n == 0) continue;
@@ -938,11 +952,11 @@ static bool apply_df_tiled(dftfe_ham h, const double* X, int64_t ldx, double* Y,
 }
 
 // Y = H~ X with the pair-of-floats cell products (nonlocal part FP64).
-void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {
+void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl) {
   // tiled kernel for the degrees it is instantiated for (rows per thread TM = ceil(nc/32))
-  if (apply_df_tiled<1>(h, X, ldx, Y, ldy, ncol) || apply_df_tiled<2>(h, X, ldx, Y, ldy, ncol) ||
-      apply_df_tiled<4>(h, X, ldx, Y, ldy, ncol) || apply_df_tiled<7>(h, X, ldx, Y, ldy, ncol) ||
-      apply_df_tiled<11>(h, X, ldx, Y, ldy, ncol))
+  if (apply_df_tiled<1>(h, X, ldx, Y, ldy, ncol, with_nl) || apply_df_tiled<2>(h, X, ldx, Y, ldy, ncol, with_nl) ||
+      apply_df_tiled<4>(h, X, ldx, Y, ldy, ncol, with_nl) || apply_df_tiled<7>(h, X, ldx, Y, ldy, ncol, with_nl) ||
+      apply_df_tiled<11>(h, X, ldx, Y, ldy, ncol, with_nl))
     return;
   auto* m = h->mesh;
   const int nc = m->nc;
@@ -958,7 +972,7 @@ void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy,
     h->df_version = h->potential_version;
   }
   // zero output and the FP64 nonlocal part, then the cell products colour by colour
-  apply_nonlocal_fp64(h, X, ldx, Y, ldy, ncol);
+  df_init(h, X, ldx, Y, ldy, ncol, with_nl);
   const size_t sh = (size_t)nc * 32 * sizeof(float2) + nc * sizeof(int32_t);
   for (int c = 0; c < h->ncolours; ++c) {
     const int64_t n = h->colour_off[c + 1] - h->colour_off[c];

@@ -160,6 +160,9 @@ struct dftfe_ham_s {
   double* d_ktab = nullptr;        // 3 x p x (2p+1): k_d G~1_d stencil per axis (see kpoint.cu)
   double* d_pval_z = nullptr;      // nnz complex, projector-major: M^1/2 chi e^{-ik.d}
   double* d_sval_z = nullptr;      // the same values node-major
+  float* d_ktab32 = nullptr;       // FP32 copies for the mixed k-point filter
+  float* d_pval_z32 = nullptr;
+  float* d_sval_z32 = nullptr;
   // CUDA graphs of the pass's filter phase (dftfe_ham_use_graphs), one slot per shape
   bool use_graphs = false;
   std::map<std::string, dftfe::GraphSlot> graphs;
@@ -195,14 +198,21 @@ void chebyshev_filter(dftfe_ham h, double* X, int64_t ld, int ncol, int degree,
                       const dftfe_bounds& b);
 void copy_block(cudaStream_t s, const double* src, int64_t lds, double* dst, int64_t ldd,
                 int64_t rows, int ncol);
+void zero_block(cudaStream_t s, double* dst, int64_t ldd, int64_t rows, int ncol);
 
 // hx_mixed.cu
 // ext_err: a device flag the caller zeroes and reads (a bounded wait timed out); NULL makes
 // the call zero and read its own (and synchronise)
+// kpoint: X is the real view of a complex block (ld, ncol in doubles) at the ham's k-point
 void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int degree,
-                            const dftfe_bounds& b, bool tf32, int* ext_err = nullptr);
-void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32);
-void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol);
+                            const dftfe_bounds& b, bool tf32, int* ext_err = nullptr, bool kpoint = false);
+void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32,
+                 bool kpoint = false);
+// with_nl = false: the local part only (real view of a complex block)
+void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl = true);
+// kpoint.cu: Z += alpha (-i k.grad X + H~_nl^k X) on FP32 complex blocks given by their real
+// views (ld in floats, ncolz complex columns); 1/2|k|^2 is the caller's
+void kpoint_add32(dftfe_ham h, const float* X, int64_t ldx, float* Z, int64_t ldz, int ncolz, float alpha);
 // hx.cu: Y = H~_nl X (Y overwritten; zero when there are no projectors), FP64
 void apply_nonlocal_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol);
 

@@ -49,9 +49,10 @@ static int read_status_z(dftfe_ham h, int* d_status) {
 // ------------------------------------------------------------------ kernels
 // Z = s1 X + s2 Xp - i alpha sum_d (G~1_d along axis d) X; tab = 3 x p x (2p+1), entry
 // (d, a, o + p) = k_d G~1_d(i, i + o) for a node i with i mod p = a (uniform mesh).
-__global__ void __launch_bounds__(256) k_kin_init(double2* __restrict__ Z, int64_t ldz,
+// Z and Xp may be the same array (each thread reads Xp before it writes Z at one entry)
+__global__ void __launch_bounds__(256) k_kin_init(double2* Z, int64_t ldz,
                                                   const double2* __restrict__ X, int64_t ldx,
-                                                  const double2* __restrict__ Xp, int64_t ldp, int64_t M,
+                                                  const double2* Xp, int64_t ldp, int64_t M,
                                                   int ncol, double s1, double s2, double alpha,
                                                   const double* __restrict__ tab, int p, int64_t g0,
                                                   int64_t g1, int kbits) {
@@ -150,6 +151,100 @@ __global__ void __launch_bounds__(256) k_nl_add_z(double2* __restrict__ Z, int64
   z->y += alpha * ai;
 }
 
+// FP32 forms for the mixed filter (complex64 vectors): Z += alpha (-i) sum_d G~1_d X along
+// axis d (the 1/2|k|^2 and recurrence terms are in the assembly that precedes it)
+__global__ void __launch_bounds__(256) k_kin_add32(float2* __restrict__ Z, int64_t ldz,
+                                                   const float2* __restrict__ X, int64_t ldx, int64_t M, int ncol,
+                                                   float alpha, const float* __restrict__ tab, int p, int64_t g0,
+                                                   int64_t g1, int kbits) {
+  extern __shared__ float tsf[];
+  const int W = 2 * p + 1;
+  for (int t = threadIdx.x; t < 3 * p * W; t += blockDim.x) tsf[t] = tab[t];
+  __syncthreads();
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= M * ncol) return;
+  const int64_t i = t / ncol;
+  const int c = (int)(t - i * ncol);
+  const int64_t pos[3] = {i % g0, (i / g0) % g1, i / (g0 * g1)};
+  const int64_t ext[3] = {g0, g1, M / (g0 * g1)};
+  const int64_t stride[3] = {1, g0, g0 * g1};
+  float sr = 0.f, si = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (!(kbits & (1 << d))) continue;
+    const int a = (int)(pos[d] % p);
+    const float* T = tsf + ((size_t)d * p + a) * W + p;
+    for (int o = a == 0 ? -p : -a; o <= p - a; ++o) {
+      int64_t j = pos[d] + o;
+      j += j < 0 ? ext[d] : (j >= ext[d] ? -ext[d] : 0);
+      const float2 v = X[(i + (j - pos[d]) * stride[d]) * ldx + c];
+      sr = fmaf(T[o], v.x, sr);
+      si = fmaf(T[o], v.y, si);
+    }
+  }
+  float2* z = Z + i * ldz + c;
+  z->x = fmaf(alpha, si, z->x);
+  z->y = fmaf(-alpha, sr, z->y);
+}
+
+__global__ void __launch_bounds__(256) k_nl_coef32_z(const float2* __restrict__ X, int64_t ldx, int ncol,
+                                                     const int64_t* __restrict__ prow,
+                                                     const int32_t* __restrict__ pnode,
+                                                     const float2* __restrict__ pval,
+                                                     const double* __restrict__ hcoup, float2* __restrict__ P) {
+  __shared__ float2 red[8][32];
+  const int a = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.y * 32 + lane;
+  float sr = 0.f, si = 0.f;
+  if (col < ncol)
+    for (int64_t e = prow[a] + warp; e < prow[a + 1]; e += 8) {
+      const float2 cv = pval[e];
+      const float2 xv = X[(int64_t)pnode[e] * ldx + col];
+      sr = fmaf(cv.x, xv.x, fmaf(cv.y, xv.y, sr));
+      si = fmaf(cv.x, xv.y, fmaf(-cv.y, xv.x, si));
+    }
+  red[warp][lane] = make_float2(sr, si);
+  __syncthreads();
+  if (warp == 0 && col < ncol) {
+    float tr = 0.f, ti = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      tr += red[w][lane].x;
+      ti += red[w][lane].y;
+    }
+    const float hv = (float)hcoup[a];
+    P[(int64_t)a * ncol + col] = make_float2(hv * tr, hv * ti);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_nl_add32_z(float2* __restrict__ Z, int64_t ldz, int ncol,
+                                                    const int32_t* __restrict__ snode,
+                                                    const int64_t* __restrict__ srow,
+                                                    const int32_t* __restrict__ sproj,
+                                                    const float2* __restrict__ sval,
+                                                    const float2* __restrict__ P, int64_t nsup, float alpha) {
+  const int lane = threadIdx.x & 31;
+  const int64_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int col = blockIdx.y * 32 + lane;
+  if (s >= nsup || col >= ncol) return;
+  float ar = 0.f, ai = 0.f;
+  for (int64_t t = srow[s]; t < srow[s + 1]; ++t) {
+    const float2 cv = sval[t];
+    const float2 pv = P[(int64_t)sproj[t] * ncol + col];
+    ar = fmaf(cv.x, pv.x, fmaf(-cv.y, pv.y, ar));
+    ai = fmaf(cv.x, pv.y, fmaf(cv.y, pv.x, ai));
+  }
+  float2* z = Z + (int64_t)snode[s] * ldz + col;
+  z->x = fmaf(alpha, ar, z->x);
+  z->y = fmaf(alpha, ai, z->y);
+}
+
+__global__ void k_to_f2(float2* __restrict__ dst, const double2* __restrict__ src, int64_t n) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = make_float2((float)src[t].x, (float)src[t].y);
+}
+
 // pz[e] = pval[e] e^{-i k.disp_e}
 __global__ void k_phase_vals(double2* __restrict__ pz, const double* __restrict__ pval,
                              const double* __restrict__ disp, double k0, double k1, double k2, int64_t nnz) {
@@ -235,8 +330,14 @@ static void build_ktab(dftfe_ham h) {
       }
   }
   if (!h->d_ktab) DFTFE_CHECK_CUDA(cudaMalloc(&h->d_ktab, sizeof(double) * tab.size()));
-  DFTFE_CHECK_CUDA(cudaMemcpyAsync(h->d_ktab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice,
-                                   h->stream));
+  if (!h->d_ktab32) DFTFE_CHECK_CUDA(cudaMalloc(&h->d_ktab32, sizeof(float) * tab.size()));
+  std::vector<float> tab32(tab.begin(), tab.end());
+  DFTFE_CHECK_CUDA(cudaMemcpy(h->d_ktab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+  DFTFE_CHECK_CUDA(cudaMemcpy(h->d_ktab32, tab32.data(), sizeof(float) * tab32.size(), cudaMemcpyHostToDevice));
+}
+
+static int kbits_of(dftfe_ham h) {
+  return (h->kvec[0] != 0.0 ? 1 : 0) | (h->kvec[1] != 0.0 ? 2 : 0) | (h->kvec[2] != 0.0 ? 4 : 0);
 }
 
 static void require_kpoint(dftfe_ham h) {
@@ -258,7 +359,7 @@ void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, 
     const size_t sh = sizeof(double) * 3 * p * (2 * p + 1);
     DFTFE_LAUNCH(k_kin_init, nblk(m->M * ncol), 256, sh, h->stream, (double2*)Z, ldz, (const double2*)X, ldx,
                  (const double2*)Xp, ldp, m->M, ncol, s1 + 0.5 * alpha * k2, s2, alpha, h->d_ktab, p, m->g[0],
-                 m->g[1], (h->kvec[0] != 0.0 ? 1 : 0) | (h->kvec[1] != 0.0 ? 2 : 0) | (h->kvec[2] != 0.0 ? 4 : 0));
+                 m->g[1], kbits_of(h));
   }
   if (h->nproj > 0) {
     ProfScope ps(h, "nl_z");
@@ -271,6 +372,56 @@ void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, 
                  (const double2*)h->d_sval_z, P, h->nsup, alpha);
   }
   local_part_fp64(h, X, 2 * ldx, Z, 2 * ldz, 2 * ncol, alpha);
+}
+
+void kpoint_add32(dftfe_ham h, const float* X, int64_t ldx, float* Z, int64_t ldz, int ncolz, float alpha) {
+  require_kpoint(h);
+  auto* m = h->mesh;
+  if (ncolz <= 0) return;
+  const int p = m->p;
+  {
+    ProfScope ps(h, "kin_k32");
+    const size_t sh = sizeof(float) * 3 * p * (2 * p + 1);
+    DFTFE_LAUNCH(k_kin_add32, nblk(m->M * ncolz), 256, sh, h->stream, (float2*)Z, ldz / 2, (const float2*)X, ldx / 2,
+                 m->M, ncolz, alpha, h->d_ktab32, p, m->g[0], m->g[1], kbits_of(h));
+  }
+  if (h->nproj > 0) {
+    ProfScope ps(h, "nl_z32");
+    float2* P = (float2*)ws_get(h, "nl_coef32_z", sizeof(float2) * h->nproj * (size_t)ncolz);
+    dim3 g1((unsigned)h->nproj, (unsigned)((ncolz + 31) / 32));
+    DFTFE_LAUNCH(k_nl_coef32_z, g1, 256, 0, h->stream, (const float2*)X, ldx / 2, ncolz, h->d_prow, h->d_pnode,
+                 (const float2*)h->d_pval_z32, h->d_h, P);
+    dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncolz + 31) / 32));
+    DFTFE_LAUNCH(k_nl_add32_z, g2, 256, 0, h->stream, (float2*)Z, ldz / 2, ncolz, h->d_snode, h->d_srow, h->d_sproj,
+                 (const float2*)h->d_sval_z32, P, h->nsup, alpha);
+  }
+}
+
+// W = H~^k X with the local part from float pairs (about 44 bits, FP32 pipes) on the real view
+// and the k-dependent and nonlocal terms in FP64: the W of a mixed complex Rayleigh-Ritz
+static void apply_z_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {
+  require_kpoint(h);
+  auto* m = h->mesh;
+  apply_df(h, X, 2 * ldx, Y, 2 * ldy, 2 * ncol, false);
+  const double k2 = h->kvec[0] * h->kvec[0] + h->kvec[1] * h->kvec[1] + h->kvec[2] * h->kvec[2];
+  const int p = m->p;
+  {
+    // in place: Y = 1/2|k|^2 X + 1 * Y - i k.grad X (each thread reads and writes its own entry)
+    ProfScope ps(h, "kin_k");
+    const size_t sh = sizeof(double) * 3 * p * (2 * p + 1);
+    DFTFE_LAUNCH(k_kin_init, nblk(m->M * ncol), 256, sh, h->stream, (double2*)Y, ldy, (const double2*)X, ldx,
+                 (const double2*)Y, ldy, m->M, ncol, 0.5 * k2, 1.0, 1.0, h->d_ktab, p, m->g[0], m->g[1], kbits_of(h));
+  }
+  if (h->nproj > 0) {
+    ProfScope ps(h, "nl_z");
+    double2* P = (double2*)ws_get(h, "nl_coef_z", sizeof(double2) * h->nproj * (size_t)ncol);
+    dim3 g1((unsigned)h->nproj, (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_nl_coef_z, g1, 256, 0, h->stream, (const double2*)X, ldx, ncol, h->d_prow, h->d_pnode,
+                 (const double2*)h->d_pval_z, h->d_h, P);
+    dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
+    DFTFE_LAUNCH(k_nl_add_z, g2, 256, 0, h->stream, (double2*)Y, ldy, ncol, h->d_snode, h->d_srow, h->d_sproj,
+                 (const double2*)h->d_sval_z, P, h->nsup, 1.0);
+  }
 }
 
 // Eq. chebyfilter on a complex block (the recurrence of chebyshev_filter, real coefficients)
@@ -313,32 +464,46 @@ static void chebyshev_filter_z(dftfe_ham h, double* X, int64_t ld, int ncol, int
 }
 
 // S = X^H X = L L^H, X <- X L^-H, through the real view (file comment)
-static void cholgs_z(dftfe_ham h, double* X, int64_t ld, int ncol) {
+// mixed: the real-view Gram with FP64 diagonal and FP32-accuracy off-diagonal entries and the
+// mixed rotation (the Gamma-point mixed scheme applied to the real view)
+static void real_view_gram(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int N2,
+                           double* C, bool mixed) {
+  auto* m = h->mesh;
+  if (mixed) {
+    gram_lower_mixed(h, A, lda, B, ldb, m->M, N2, C);
+  } else {
+    const int nsplit = gram_nsplit(h, m->M, N2);
+    double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N2 * N2);
+    gram_lower(h, A, lda, B, ldb, m->M, N2, C, part, nsplit);
+  }
+}
+
+static void cholgs_z(dftfe_ham h, double* X, int64_t ld, int ncol, bool mixed) {
   auto* m = h->mesh;
   const int N2 = 2 * ncol;
   double* S = (double*)ws_get(h, "S", sizeof(double) * (size_t)N2 * N2);
   double* Z = (double*)ws_get(h, "Zinv", sizeof(double) * (size_t)N2 * N2);
   int* st = (int*)ws_get(h, "status", sizeof(int) * 4);
-  const int nsplit = gram_nsplit(h, m->M, N2);
-  double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N2 * N2);
-  gram_lower(h, X, 2 * ld, X, 2 * ld, m->M, N2, S, part, nsplit);
+  real_view_gram(h, X, 2 * ld, X, 2 * ld, N2, S, mixed);
   DFTFE_LAUNCH(k_herm_expand, nblk((int64_t)ncol * ncol), 256, 0, h->stream, S, ncol);
   potrf(h->stream, S, N2, st);
   if (read_status_z(h, st) == DFTFE_ERR_NOT_SPD)
     throw Error(DFTFE_ERR_NOT_SPD, "overlap matrix is not positive definite");
   trtri_lower_to_upper_t(h->stream, S, Z, N2);
-  rotate_inplace(h, X, 2 * ld, m->M, N2, Z, true);
+  if (mixed) rotate_inplace_mixed(h, X, 2 * ld, m->M, N2, Z, true);
+  else rotate_inplace(h, X, 2 * ld, m->M, N2, Z, true);
 }
 
 // W = H~^k X, H^ = X^H W = Q Theta Q^H, X <- X Q, W <- W Q
-static void rayleigh_ritz_z(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals, double* W, int64_t ldw) {
+static void rayleigh_ritz_z(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals, double* W, int64_t ldw,
+                            bool mixed) {
   auto* m = h->mesh;
   const int N2 = 2 * ncol;
-  apply_combo_z(h, X, ld, nullptr, 0, W, ldw, ncol, 1.0, 0.0, 0.0);
+  // W FP64-accurate in both precisions (float pairs for the local part of a mixed pass)
+  if (mixed) apply_z_df(h, X, ld, W, ldw, ncol);
+  else apply_combo_z(h, X, ld, nullptr, 0, W, ldw, ncol, 1.0, 0.0, 0.0);
   double* G = (double*)ws_get(h, "Hhat", sizeof(double) * (size_t)N2 * N2);
-  const int nsplit = gram_nsplit(h, m->M, N2);
-  double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N2 * N2);
-  gram_lower(h, X, 2 * ld, W, 2 * ldw, m->M, N2, G, part, nsplit);
+  real_view_gram(h, X, 2 * ld, W, 2 * ldw, N2, G, mixed);
   double* Hz = (double*)ws_get(h, "Hz", sizeof(double2) * (size_t)ncol * ncol);
   double* Qz = (double*)ws_get(h, "Qz", sizeof(double2) * (size_t)ncol * ncol);
   double* Qr = (double*)ws_get(h, "Q", sizeof(double) * (size_t)N2 * N2);
@@ -349,8 +514,25 @@ static void rayleigh_ritz_z(dftfe_ham h, double* X, int64_t ld, int ncol, double
   if (s == DFTFE_ERR_NOCONV) throw Error(DFTFE_ERR_NOCONV, "subspace eigensolver did not converge");
   if (s != 0) throw Error((dftfe_status)s, "subspace eigensolver: a bounded grid wait timed out");
   DFTFE_LAUNCH(k_realify, nblk((int64_t)ncol * ncol), 256, 0, h->stream, (const double2*)Qz, ncol, Qr);
-  rotate_inplace(h, X, 2 * ld, m->M, N2, Qr, false);
-  rotate_inplace(h, W, 2 * ldw, m->M, N2, Qr, false);
+  if (mixed) {
+    rotate_inplace_mixed(h, X, 2 * ld, m->M, N2, Qr, false);
+    rotate_inplace_mixed(h, W, 2 * ldw, m->M, N2, Qr, false);
+  } else {
+    rotate_inplace(h, X, 2 * ld, m->M, N2, Qr, false);
+    rotate_inplace(h, W, 2 * ldw, m->M, N2, Qr, false);
+  }
+}
+
+static bool valid_prec(dftfe_precision prec) {
+  return prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3;
+}
+
+// the filter of one complex column block in the pass's precision (mixed: FP32 complex vectors,
+// split cell products on the real view, FP32 k-terms; err as for chebyshev_filter_mixed)
+static void filter_z_any(dftfe_ham h, double* X, int64_t ld, int ncol, int degree, const dftfe_bounds& b,
+                         dftfe_precision prec, int* err) {
+  if (prec == DFTFE_FP64) chebyshev_filter_z(h, X, ld, ncol, degree, b);
+  else chebyshev_filter_mixed(h, X, 2 * ld, 2 * ncol, degree, b, prec == DFTFE_MIXED_TF32X3, err, true);
 }
 
 }  // namespace dftfe
@@ -381,6 +563,13 @@ extern "C" dftfe_status dftfe_ham_set_kpoint(dftfe_ham h, const double* kvec, co
                  kvec[1], kvec[2], nnz);
     DFTFE_LAUNCH(k_gather_z, nblk(nnz), 256, 0, h->stream, (double2*)h->d_sval_z, (const double2*)h->d_pval_z,
                  h->d_sperm, nnz);
+    cudaFree(h->d_pval_z32);
+    cudaFree(h->d_sval_z32);
+    h->d_pval_z32 = h->d_sval_z32 = nullptr;
+    DFTFE_CHECK_CUDA(cudaMalloc(&h->d_pval_z32, sizeof(float2) * nnz));
+    DFTFE_CHECK_CUDA(cudaMalloc(&h->d_sval_z32, sizeof(float2) * nnz));
+    DFTFE_LAUNCH(k_to_f2, nblk(nnz), 256, 0, h->stream, (float2*)h->d_pval_z32, (const double2*)h->d_pval_z, nnz);
+    DFTFE_LAUNCH(k_to_f2, nblk(nnz), 256, 0, h->stream, (float2*)h->d_sval_z32, (const double2*)h->d_sval_z, nnz);
     DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
     cudaFree(d_disp);
     h->kpoint_nl = true;
@@ -391,12 +580,15 @@ extern "C" dftfe_status dftfe_ham_set_kpoint(dftfe_ham h, const double* kvec, co
 }
 
 extern "C" dftfe_status dftfe_ham_apply_z(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy,
-                                          int ncol) {
+                                          int ncol, dftfe_precision prec) {
   ABI_BEGIN
   DFTFE_REQUIRE(h && X && Y, "null argument");
   DFTFE_REQUIRE(ncol >= 0 && ldx >= ncol && ldy >= ncol, "bad ncol / leading dimension");
+  DFTFE_REQUIRE(valid_prec(prec) || prec == DFTFE_FP64_FLOAT_PAIRS, "unknown precision");
   require_kpoint(h);
-  apply_combo_z(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
+  if (prec == DFTFE_FP64) apply_combo_z(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
+  else if (prec == DFTFE_FP64_FLOAT_PAIRS) apply_z_df(h, X, ldx, Y, ldy, ncol);
+  else apply_mixed(h, X, 2 * ldx, Y, 2 * ldy, 2 * ncol, prec == DFTFE_MIXED_TF32X3, true);
   ABI_END
 }
 
@@ -425,32 +617,35 @@ extern "C" dftfe_status dftfe_spectrum_bounds_z(dftfe_ham h, int k, uint64_t see
 }
 
 extern "C" dftfe_status dftfe_chebyshev_filter_z(dftfe_ham h, double* X, int64_t ld, int ncol, int degree,
-                                                 const dftfe_bounds* bounds) {
+                                                 const dftfe_bounds* bounds, dftfe_precision prec) {
   ABI_BEGIN
   DFTFE_REQUIRE(h && X && bounds, "null argument");
   DFTFE_REQUIRE(ncol >= 0 && ld >= ncol && degree >= 0, "bad ncol / ld / degree");
   DFTFE_REQUIRE(bounds->b > bounds->a, "need b > a");
   DFTFE_REQUIRE(std::isnan(bounds->a0) || bounds->a0 < bounds->a, "need a0 < a for the scaled filter");
+  DFTFE_REQUIRE(valid_prec(prec), "unknown precision");
   require_kpoint(h);
-  chebyshev_filter_z(h, X, ld, ncol, degree, *bounds);
+  filter_z_any(h, X, ld, ncol, degree, *bounds, prec, nullptr);
   ABI_END
 }
 
-extern "C" dftfe_status dftfe_cholgs_z(dftfe_ham h, double* X, int64_t ld, int ncol) {
+extern "C" dftfe_status dftfe_cholgs_z(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_precision prec) {
   ABI_BEGIN
   DFTFE_REQUIRE(h && X, "null argument");
   DFTFE_REQUIRE(ncol >= 1 && ncol <= 1024 && ld >= ncol, "bad ncol / ld (at most 1024 complex columns)");
   DFTFE_REQUIRE(ncol <= h->mesh->M, "more columns than DoFs");
-  cholgs_z(h, X, ld, ncol);
+  DFTFE_REQUIRE(valid_prec(prec), "unknown precision");
+  cholgs_z(h, X, ld, ncol, prec != DFTFE_FP64);
   ABI_END
 }
 
 extern "C" dftfe_status dftfe_rayleigh_ritz_z(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals,
-                                              double* HX, int64_t ldhx) {
+                                              double* HX, int64_t ldhx, dftfe_precision prec) {
   ABI_BEGIN
   DFTFE_REQUIRE(h && X && evals, "null argument");
   DFTFE_REQUIRE(ncol >= 1 && ncol <= 1024 && ld >= ncol, "bad ncol / ld (at most 1024 complex columns)");
   DFTFE_REQUIRE(!HX || ldhx >= ncol, "bad ldhx");
+  DFTFE_REQUIRE(valid_prec(prec), "unknown precision");
   require_kpoint(h);
   double* W = HX;
   int64_t ldw = ldhx;
@@ -458,21 +653,22 @@ extern "C" dftfe_status dftfe_rayleigh_ritz_z(dftfe_ham h, double* X, int64_t ld
     W = (double*)ws_get(h, "W", sizeof(double) * 2 * (size_t)h->mesh->M * ncol);
     ldw = ncol;
   }
-  rayleigh_ritz_z(h, X, ld, ncol, evals, W, ldw);
+  rayleigh_ritz_z(h, X, ld, ncol, evals, W, ldw, prec != DFTFE_FP64);
   ABI_END
 }
 
 extern "C" dftfe_status dftfe_residuals_z(dftfe_ham h, const double* X, const double* HX, int64_t ld, int ncol,
-                                          const double* evals, double* resid) {
+                                          const double* evals, double* resid, int kind) {
   ABI_BEGIN
   DFTFE_REQUIRE(h && X && HX && evals && resid, "null argument");
   DFTFE_REQUIRE(ncol >= 1 && ld >= ncol, "bad ncol / ld");
-  residual_norms(h, X, 2 * ld, HX, 2 * ld, h->mesh->M, ncol, evals, resid, 0, 2);
+  DFTFE_REQUIRE(kind == 0 || kind == 1, "kind must be 0 or 1");
+  residual_norms(h, X, 2 * ld, HX, 2 * ld, h->mesh->M, ncol, evals, resid, kind, 2);
   ABI_END
 }
 
 extern "C" dftfe_status dftfe_chfsi_pass_z(dftfe_ham h, double* X, int64_t ld, int ncol, int block, int degree,
-                                           dftfe_bounds* inout, double* evals, double* resid) {
+                                           dftfe_bounds* inout, double* evals, double* resid, dftfe_precision prec) {
   ABI_BEGIN
   DFTFE_REQUIRE(h && X && inout && evals && resid, "null argument");
   DFTFE_REQUIRE(ncol >= 1 && ncol <= 1024 && ld >= ncol && block >= 1 && degree >= 0,
@@ -480,26 +676,39 @@ extern "C" dftfe_status dftfe_chfsi_pass_z(dftfe_ham h, double* X, int64_t ld, i
   DFTFE_REQUIRE(ncol <= h->mesh->M, "more columns than DoFs");
   DFTFE_REQUIRE(inout->b > inout->a, "need b > a");
   DFTFE_REQUIRE(std::isnan(inout->a0) || inout->a0 < inout->a, "need a0 < a for the scaled filter");
+  DFTFE_REQUIRE(valid_prec(prec), "unknown precision");
   require_kpoint(h);
   auto* m = h->mesh;
+  const bool mixed = prec != DFTFE_FP64;
   {
     ProfScope ps(h, "pass_filter");
+    int* err = nullptr;
+    if (mixed) {
+      err = (int*)ws_get(h, "mx_err", sizeof(int));
+      DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+    }
     const dftfe_bounds bnd = *inout;
-    const std::string key = "pass_z/" + std::to_string(ncol) + "/" + std::to_string(block) + "/" +
-                            std::to_string(degree);
+    const std::string key = "pass_z/" + std::to_string((int)prec) + "/" + std::to_string(ncol) + "/" +
+                            std::to_string(block) + "/" + std::to_string(degree);
     run_region(h, key, [&]() {
       for (int j0 = 0; j0 < ncol; j0 += block)
-        chebyshev_filter_z(h, X + 2 * (int64_t)j0, ld, std::min(block, ncol - j0), degree, bnd);
+        filter_z_any(h, X + 2 * (int64_t)j0, ld, std::min(block, ncol - j0), degree, bnd, prec, err);
     });
+    if (err) {
+      int herr = 0;
+      DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+      if (herr) throw Error(DFTFE_ERR_TIMEOUT, "mixed cell kernel: a bounded wait timed out");
+    }
   }
   {
     ProfScope ps(h, "pass_cholgs");
-    cholgs_z(h, X, ld, ncol);
+    cholgs_z(h, X, ld, ncol, mixed);
   }
   double* W = (double*)ws_get(h, "W", sizeof(double) * 2 * (size_t)m->M * ncol);
   {
     ProfScope ps(h, "pass_rr");
-    rayleigh_ritz_z(h, X, ld, ncol, evals, W, ncol);
+    rayleigh_ritz_z(h, X, ld, ncol, evals, W, ncol, mixed);
   }
   residual_norms(h, X, 2 * ld, W, 2 * (int64_t)ncol, m->M, ncol, evals, resid, 0, 2);
   double ends[2];

@@ -198,6 +198,8 @@ static void free_nonlocal(dftfe_ham h) {
   cudaFree(h->d_h); cudaFree(h->d_prow); cudaFree(h->d_pnode); cudaFree(h->d_pval);
   cudaFree(h->d_snode); cudaFree(h->d_srow); cudaFree(h->d_sproj); cudaFree(h->d_sval);
   cudaFree(h->d_nptr_all); cudaFree(h->d_sperm); cudaFree(h->d_pval_z); cudaFree(h->d_sval_z);
+  cudaFree(h->d_pval_z32); cudaFree(h->d_sval_z32);
+  h->d_pval_z32 = nullptr; h->d_sval_z32 = nullptr;
   h->d_h = nullptr; h->d_prow = nullptr; h->d_pnode = nullptr; h->d_pval = nullptr;
   h->d_snode = nullptr; h->d_srow = nullptr; h->d_sproj = nullptr; h->d_sval = nullptr;
   h->d_nptr_all = nullptr; h->d_sperm = nullptr; h->d_pval_z = nullptr; h->d_sval_z = nullptr;
@@ -516,7 +518,7 @@ extern "C" dftfe_status dftfe_ham_destroy(dftfe_ham h) {
   free_nonlocal(h);
   cudaFree(h->d_map); cudaFree(h->d_mass); cudaFree(h->d_minvsqrt);
   cudaFree(h->d_colour_cells); cudaFree(h->d_node_ptr); cudaFree(h->d_node_slot); cudaFree(h->d_K); cudaFree(h->d_P); cudaFree(h->d_pairs);
-  cudaFree(h->d_wq); cudaFree(h->d_Hc); cudaFree(h->d_Nq); cudaFree(h->d_ktab);
+  cudaFree(h->d_wq); cudaFree(h->d_Hc); cudaFree(h->d_Nq); cudaFree(h->d_ktab); cudaFree(h->d_ktab32);
   for (auto& kv : h->ws) kv.second.release();
   for (auto& kv : h->timers)
     for (auto& ev : kv.second.events) {

@@ -88,7 +88,9 @@ def test_graphed_pass_survives_a_new_potential(dg):
         dg.dftfe_mesh_destroy(m)
 
 
-def test_graphed_complex_pass_is_bit_identical(dg):
+@pytest.mark.parametrize("prec_name", ["DFTFE_FP64", "DFTFE_MIXED_TF32X3"])
+def test_graphed_complex_pass_is_bit_identical(dg, prec_name):
+    prec = getattr(dg, prec_name)
     c = small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True)
     (m1, h1), (m2, h2) = _sys(dg, c), _sys(dg, c)
     k = (0.3, -0.2, 0.45)
@@ -103,8 +105,8 @@ def test_graphed_complex_pass_is_bit_identical(dg):
     b1, b2 = dg.make_bounds(b.a, b.b, b.a0), dg.make_bounds(b.a, b.b, b.a0)
     e1, r1, e2, r2 = (torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(4))
     for it in range(3):
-        dg.dftfe_chfsi_pass_z(h1, X1, blk, deg, b1, e1, r1)
-        dg.dftfe_chfsi_pass_z(h2, X2, blk, deg, b2, e2, r2)
+        dg.dftfe_chfsi_pass_z(h1, X1, blk, deg, b1, e1, r1, prec)
+        dg.dftfe_chfsi_pass_z(h2, X2, blk, deg, b2, e2, r2, prec)
         assert torch.equal(e1, e2) and torch.equal(X1, X2), it
     assert dg.dftfe_graph_query(h2)[0] == 2
     for h, m in ((h1, m1), (h2, m2)):

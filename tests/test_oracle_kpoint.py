@@ -226,3 +226,20 @@ def test_complex_passes_converge_to_dense_eigenvalues():
     ok = r < 1e-7
     assert ok[:8].all()
     assert np.abs(theta[ok] - lam[:12][ok]).max() < 1e-9
+
+
+def test_complex_generalised_residual_reduces_to_the_real_one():
+    """At a real block the complex residuals (both forms) are the real oracle's; on exact
+    eigenvectors of H~^k both vanish."""
+    cent, hc = atoms(9, 2, 6.0)
+    m, H, nl = system(6.0, 2, 3, cent, hc)
+    X = synth.random_block(3, m.ndofs, 5)
+    W = H.apply(X)
+    th = np.linspace(-1.0, 1.0, 5)
+    r0, g0 = oracle.residuals(X, W, th, m.mass)
+    r1, g1 = kpoint.residuals(X.astype(np.complex128), W.astype(np.complex128), th, m.mass)
+    assert np.allclose(r0, r1, rtol=1e-14) and np.allclose(g0, g1, rtol=1e-14)
+    B = bloch(H, (0.2, 0.1, -0.3), nl)
+    lam, V = np.linalg.eigh(B.dense())
+    r, g = kpoint.residuals(V[:, :4], B.apply(V[:, :4]), lam[:4], m.mass)
+    assert r.max() < 1e-11 and g.max() < 1e-11
