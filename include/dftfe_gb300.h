@@ -370,13 +370,16 @@ dftfe_status dftfe_chfsi_pass_z(dftfe_ham ham, double* X, int64_t ld, int ncol, 
                                 dftfe_precision prec);
 
 /* ------------------------------------------------------------ batched passes */
-/* Several independent systems (Gamma point, FP64) of uneven mesh size, degree, state count
- * and block size advanced by one ChFSI pass each with shared launches: per Chebyshev step one
- * launch forms the recurrence terms of every system and one launch per colour runs the cell
- * products of every system's cells of that colour; the nonlocal term, CholGS and
- * Rayleigh-Ritz run per system.  Results are bit-identical to dftfe_chfsi_pass on each system
- * alone (same operations in the same order).  No counterpart in the paper, which runs one
- * system per job. */
+/* Several independent systems (FP64) of uneven mesh size, degree, state count and block
+ * size -- each at the Gamma point or at its ham's Bloch k-point (item.kpoint), so several
+ * k-points of one system are several hams of the same mesh and potential -- advanced by one
+ * ChFSI pass each with shared launches: per Chebyshev step one launch forms the recurrence
+ * terms of every Gamma-point system and one launch per colour runs the cell products of
+ * every system's cells of that colour (a complex block through its real view); the k-point
+ * terms, the nonlocal term, CholGS and Rayleigh-Ritz run per system.  Results are
+ * bit-identical to dftfe_chfsi_pass / dftfe_chfsi_pass_z on each system alone (same
+ * operations in the same order).  No counterpart in the paper, which runs one system per
+ * job. */
 typedef struct dftfe_batch_s* dftfe_batch;
 
 typedef struct {
@@ -388,6 +391,9 @@ typedef struct {
   dftfe_bounds bounds;  /* in: filter bounds; out: updated as dftfe_chfsi_pass does */
   double* evals;        /* device, ncol: Ritz values (ascending) */
   double* resid;        /* device, ncol: residual norms */
+  int kpoint;           /* 0: real block at the Gamma point; 1: complex block (complex128,
+                           ld and ncol in complex elements, ncol <= 1024) at the k-point set on
+                           the item's ham by dftfe_ham_set_kpoint, as in dftfe_chfsi_pass_z */
 } dftfe_batch_item;
 
 /* Build a batch over nsys (1..4096) distinct Hamiltonians created on one stream; the batch

@@ -376,7 +376,7 @@ def dftfe_chfsi_pass_z(ham, X, block, degree, bounds, evals, resid, prec=DFTFE_F
 
 class BatchItem(C.Structure):
     _fields_ = [("X", _vp), ("ld", _i64), ("ncol", _int), ("block", _int), ("degree", _int),
-                ("bounds", Bounds), ("evals", _vp), ("resid", _vp)]
+                ("bounds", Bounds), ("evals", _vp), ("resid", _vp), ("kpoint", _int)]
 
 
 def dftfe_batch_create(hams):
@@ -391,13 +391,15 @@ def dftfe_batch_destroy(batch):
 
 
 def dftfe_batch_chfsi_pass(batch, Xs, blocks, degrees, bounds, evals, resids, prec=DFTFE_FP64):
-    """One pass for every system of the batch; `bounds` (list of Bounds) are updated in place."""
+    """One pass for every system of the batch; `bounds` (list of Bounds) are updated in place.
+    A complex128 block is filtered at its ham's k-point (dftfe_ham_set_kpoint)."""
     n = len(Xs)
     items = (BatchItem * n)()
     for i in range(n):
-        px, ld = _dev(Xs[i], "X")
+        cplx = Xs[i].is_complex()
+        px, ld = _zdev(Xs[i], "X") if cplx else _dev(Xs[i], "X")
         items[i] = BatchItem(px, ld, Xs[i].shape[1], int(blocks[i]), int(degrees[i]), bounds[i],
-                             _vp(evals[i].data_ptr()), _vp(resids[i].data_ptr()))
+                             _vp(evals[i].data_ptr()), _vp(resids[i].data_ptr()), 1 if cplx else 0)
     _check(_lib.dftfe_batch_chfsi_pass(batch, C.cast(items, _vp), prec))
     for i in range(n):
         bounds[i].a, bounds[i].b, bounds[i].a0 = items[i].bounds.a, items[i].bounds.b, items[i].bounds.a0

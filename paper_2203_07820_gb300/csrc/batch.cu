@@ -1,11 +1,14 @@
-// Batched ChFSI passes (FP64, Gamma point): independent systems of uneven mesh size, degree,
-// state count and block size filtered with shared launches.  Per Chebyshev step one launch
-// forms s1 X_k + s2 X_{k-1} for every system, and one launch per colour runs the cell
-// products of every system's cells of that colour (a work list of (system, cell) pairs built
-// once); the nonlocal term is added per system.  The orthonormalisation and Rayleigh-Ritz
-// steps then run per system.  Each system's arithmetic, and its order, is that of a single
-// pass (the cell body is shared with the per-colour kernel), so the results are bit-identical
-// to passes run one system at a time; the gain is fewer, fuller launches for small systems.
+// Batched ChFSI passes (FP64): independent systems of uneven mesh size, degree, state count
+// and block size -- at the Gamma point or, item by item, at the ham's Bloch k-point with a
+// complex block -- filtered with shared launches.  Per Chebyshev step one launch forms
+// s1 X_k + s2 X_{k-1} for every real system (a complex system forms it with its k.grad
+// stencil, as a single k-point pass does), and one launch per colour runs the cell products
+// of every system's cells of that colour (a work list of (system, cell) pairs built once; a
+// complex block enters as its real view); the nonlocal term is added per system.  The
+// orthonormalisation and Rayleigh-Ritz steps then run per system.  Each system's
+// arithmetic, and its order, is that of a single pass (the cell body is shared with the
+// per-colour kernel), so the results are bit-identical to passes run one system at a time;
+// the gain is fewer, fuller launches for small systems.
 #include "internal.h"
 #include "cell_fp64.cuh"
 
@@ -37,6 +40,7 @@ struct SysStep {
   double* Z;
   int64_t ldx, ldp, ldz, M;
   int nc, ncol, active;
+  int cplx;                // real view of a complex block: the init is the k-point kernel's
   double alpha, s1, s2;
 };
 }  // namespace bt
@@ -45,7 +49,7 @@ struct SysStep {
 // same order as the single-system k_axpby_init
 __global__ void k_batch_axpby(const bt::SysStep* __restrict__ st) {
   const bt::SysStep& d = st[blockIdx.y];
-  if (!d.active) return;
+  if (!d.active || d.cplx) return;
   const int64_t n = d.M * d.ncol;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t / d.ncol;
@@ -120,7 +124,9 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
     std::vector<int> alone;                       // blocks of at most 4 columns: narrow kernel
     for (int s = 0; s < ns; ++s) {
       dftfe_ham h = bt->hams[s];
-      nb[s] = std::min(items[s].block, items[s].ncol - j * items[s].block);
+      // a complex block is handled through its real view: 2 doubles per complex column
+      const int cw = items[s].kpoint ? 2 : 1;
+      nb[s] = cw * std::min(items[s].block, items[s].ncol - j * items[s].block);
       if (nb[s] <= 0 || items[s].degree <= 0) { nb[s] = 0; continue; }
       if (nb[s] <= 4) {
         alone.push_back(s);
@@ -129,8 +135,8 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
       }
       double* w1 = (double*)ws_get(h, "cheb_w1", sizeof(double) * h->mesh->M * (size_t)nb[s]);
       double* w2 = (double*)ws_get(h, "cheb_w2", sizeof(double) * h->mesh->M * (size_t)nb[s]);
-      buf[s] = {items[s].X + (int64_t)j * items[s].block, w1, w2};
-      lds[s] = {items[s].ld, nb[s], nb[s]};
+      buf[s] = {items[s].X + (int64_t)cw * j * items[s].block, w1, w2};
+      lds[s] = {cw * items[s].ld, nb[s], nb[s]};
       tiles[s] = (nb[s] + 31) / 32;
       maxtiles = std::max(maxtiles, tiles[s]);
     }
@@ -157,6 +163,7 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
         d.nc = h->mesh->nc;
         d.ncol = nb[s];
         d.active = 1;
+        d.cplx = items[s].kpoint ? 1 : 0;
         d.alpha = alpha;
         d.s1 = s1;
         d.s2 = s2;
@@ -173,7 +180,12 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
       DFTFE_LAUNCH(k_batch_axpby, dim3(std::max(gx, 1u), (unsigned)ns), 256, 0, bt->stream, dk);
       for (int s = 0; s < ns; ++s) {
         const bt::SysStep& d = host[(size_t)(k - 1) * ns + s];
-        if (d.active) nonlocal_add_fp64(bt->hams[s], d.X, d.ldx, d.Z, d.ldz, d.ncol, d.alpha);
+        if (!d.active) continue;
+        if (d.cplx)      // the recurrence terms, 1/2|k|^2, -i k.grad and the phased projectors
+          kpoint_init_terms(bt->hams[s], d.X, d.ldx / 2, d.Xp, d.ldp / 2, d.Z, d.ldz / 2, d.ncol / 2, d.alpha,
+                            d.s1, d.s2);
+        else
+          nonlocal_add_fp64(bt->hams[s], d.X, d.ldx, d.Z, d.ldz, d.ncol, d.alpha);
       }
       for (int c = 0; c < bt->ncolours; ++c) {
         const int64_t n = bt->work_off[c + 1] - bt->work_off[c];
@@ -190,8 +202,12 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
         copy_block(bt->stream, buf[s][cur[s]], lds[s][cur[s]], buf[s][0], lds[s][0], bt->hams[s]->mesh->M, nb[s]);
     for (int s : alone) {
       const int n = std::min(items[s].block, items[s].ncol - j * items[s].block);
-      chebyshev_filter(bt->hams[s], items[s].X + (int64_t)j * items[s].block, items[s].ld, n, items[s].degree,
-                       items[s].bounds);
+      if (items[s].kpoint)
+        chebyshev_filter_z_fp64(bt->hams[s], items[s].X + 2 * (int64_t)j * items[s].block, items[s].ld, n,
+                                items[s].degree, items[s].bounds);
+      else
+        chebyshev_filter(bt->hams[s], items[s].X + (int64_t)j * items[s].block, items[s].ld, n, items[s].degree,
+                         items[s].bounds);
     }
     // the host descriptors must outlive the copy above: wait before they go out of scope
     DFTFE_CHECK_CUDA(cudaStreamSynchronize(bt->stream));
@@ -277,8 +293,11 @@ extern "C" dftfe_status dftfe_batch_chfsi_pass(dftfe_batch b, dftfe_batch_item* 
     const dftfe_batch_item& it = items[s];
     dftfe_ham h = b->hams[s];
     DFTFE_REQUIRE(it.X && it.evals && it.resid, "null array in a batch item");
-    DFTFE_REQUIRE(it.ncol >= 1 && it.ncol <= 2048 && it.ld >= it.ncol && it.block >= 1 && it.degree >= 0,
+    DFTFE_REQUIRE(it.kpoint == 0 || it.kpoint == 1, "kpoint must be 0 or 1");
+    DFTFE_REQUIRE(it.ncol >= 1 && it.ncol <= (it.kpoint ? 1024 : 2048) && it.ld >= it.ncol && it.block >= 1 &&
+                      it.degree >= 0,
                   "bad sizes in a batch item");
+    if (it.kpoint) require_kpoint(h);
     DFTFE_REQUIRE(it.ncol <= h->mesh->M, "more columns than DoFs");
     DFTFE_REQUIRE(it.bounds.b > it.bounds.a, "need b > a");
     DFTFE_REQUIRE(std::isnan(it.bounds.a0) || it.bounds.a0 < it.bounds.a, "need a0 < a for the scaled filter");
@@ -289,7 +308,11 @@ extern "C" dftfe_status dftfe_batch_chfsi_pass(dftfe_batch b, dftfe_batch_item* 
     batch_filter(b, items);
   }
   for (int s = 0; s < ns; ++s)
-    chfsi_pass_tail(b->hams[s], items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
-                    items[s].resid, prec);
+    if (items[s].kpoint)
+      chfsi_pass_tail_z(b->hams[s], items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
+                        items[s].resid, prec);
+    else
+      chfsi_pass_tail(b->hams[s], items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
+                      items[s].resid, prec);
   ABI_END
 }

@@ -268,6 +268,15 @@ void free_graphs(dftfe_ham h);
 // kpoint.cu: Z = alpha H~^k X + s1 X + s2 Xp on complex blocks (ld in complex elements)
 void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, int64_t ldp, double* Z,
                    int64_t ldz, int ncol, double alpha, double s1, double s2);
+// the part of apply_combo_z before the cell products: Z = s1 X + s2 Xp + alpha (1/2|k|^2 X
+// - i k.grad X + H~_nl^k X)
+void kpoint_init_terms(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, int64_t ldp, double* Z,
+                       int64_t ldz, int ncol, double alpha, double s1, double s2);
+void chebyshev_filter_z_fp64(dftfe_ham h, double* X, int64_t ld, int ncol, int degree, const dftfe_bounds& b);
+void chfsi_pass_tail_z(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_bounds* inout, double* evals,
+                       double* resid, dftfe_precision prec);
+// DFTFE_ERR_STATE unless the potential and the k-point (with current projector phases) are set
+void require_kpoint(dftfe_ham h);
 
 }  // namespace dftfe
 

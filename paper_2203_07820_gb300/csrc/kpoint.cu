@@ -340,18 +340,16 @@ static int kbits_of(dftfe_ham h) {
   return (h->kvec[0] != 0.0 ? 1 : 0) | (h->kvec[1] != 0.0 ? 2 : 0) | (h->kvec[2] != 0.0 ? 4 : 0);
 }
 
-static void require_kpoint(dftfe_ham h) {
+void require_kpoint(dftfe_ham h) {
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   if (!h->has_kpoint) throw Error(DFTFE_ERR_STATE, "set the k-point first (dftfe_ham_set_kpoint)");
   if (h->nproj > 0 && !h->kpoint_nl)
     throw Error(DFTFE_ERR_STATE, "the projectors changed: call dftfe_ham_set_kpoint again");
 }
 
-void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, int64_t ldp, double* Z,
-                   int64_t ldz, int ncol, double alpha, double s1, double s2) {
-  require_kpoint(h);
+void kpoint_init_terms(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, int64_t ldp, double* Z,
+                       int64_t ldz, int ncol, double alpha, double s1, double s2) {
   auto* m = h->mesh;
-  if (ncol <= 0) return;
   const double k2 = h->kvec[0] * h->kvec[0] + h->kvec[1] * h->kvec[1] + h->kvec[2] * h->kvec[2];
   const int p = m->p;
   {
@@ -371,6 +369,13 @@ void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, 
     DFTFE_LAUNCH(k_nl_add_z, g2, 256, 0, h->stream, (double2*)Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj,
                  (const double2*)h->d_sval_z, P, h->nsup, alpha);
   }
+}
+
+void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, int64_t ldp, double* Z,
+                   int64_t ldz, int ncol, double alpha, double s1, double s2) {
+  require_kpoint(h);
+  if (ncol <= 0) return;
+  kpoint_init_terms(h, X, ldx, Xp, ldp, Z, ldz, ncol, alpha, s1, s2);
   local_part_fp64(h, X, 2 * ldx, Z, 2 * ldz, 2 * ncol, alpha);
 }
 
@@ -425,7 +430,7 @@ static void apply_z_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int
 }
 
 // Eq. chebyfilter on a complex block (the recurrence of chebyshev_filter, real coefficients)
-static void chebyshev_filter_z(dftfe_ham h, double* X, int64_t ld, int ncol, int degree, const dftfe_bounds& b) {
+void chebyshev_filter_z_fp64(dftfe_ham h, double* X, int64_t ld, int ncol, int degree, const dftfe_bounds& b) {
   if (degree <= 0 || ncol <= 0) return;
   auto* m = h->mesh;
   const double e = (b.b - b.a) / 2.0, c = (b.b + b.a) / 2.0;
@@ -531,8 +536,31 @@ static bool valid_prec(dftfe_precision prec) {
 // split cell products on the real view, FP32 k-terms; err as for chebyshev_filter_mixed)
 static void filter_z_any(dftfe_ham h, double* X, int64_t ld, int ncol, int degree, const dftfe_bounds& b,
                          dftfe_precision prec, int* err) {
-  if (prec == DFTFE_FP64) chebyshev_filter_z(h, X, ld, ncol, degree, b);
+  if (prec == DFTFE_FP64) chebyshev_filter_z_fp64(h, X, ld, ncol, degree, b);
   else chebyshev_filter_mixed(h, X, 2 * ld, 2 * ncol, degree, b, prec == DFTFE_MIXED_TF32X3, err, true);
+}
+
+// the complex pass after its filter: CholGS, Rayleigh-Ritz, residuals, bounds update
+void chfsi_pass_tail_z(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_bounds* inout, double* evals,
+                       double* resid, dftfe_precision prec) {
+  auto* m = h->mesh;
+  const bool mixed = prec != DFTFE_FP64;
+  {
+    ProfScope ps(h, "pass_cholgs");
+    cholgs_z(h, X, ld, ncol, mixed);
+  }
+  double* W = (double*)ws_get(h, "W", sizeof(double) * 2 * (size_t)m->M * ncol);
+  {
+    ProfScope ps(h, "pass_rr");
+    rayleigh_ritz_z(h, X, ld, ncol, evals, W, ncol, mixed);
+  }
+  residual_norms(h, X, 2 * ld, W, 2 * (int64_t)ncol, m->M, ncol, evals, resid, 0, 2);
+  double ends[2];
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[0], evals, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[1], evals + ncol - 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  inout->a = ends[1];
+  if (!std::isnan(inout->a0)) inout->a0 = ends[0];
 }
 
 }  // namespace dftfe
@@ -701,21 +729,6 @@ extern "C" dftfe_status dftfe_chfsi_pass_z(dftfe_ham h, double* X, int64_t ld, i
       if (herr) throw Error(DFTFE_ERR_TIMEOUT, "mixed cell kernel: a bounded wait timed out");
     }
   }
-  {
-    ProfScope ps(h, "pass_cholgs");
-    cholgs_z(h, X, ld, ncol, mixed);
-  }
-  double* W = (double*)ws_get(h, "W", sizeof(double) * 2 * (size_t)m->M * ncol);
-  {
-    ProfScope ps(h, "pass_rr");
-    rayleigh_ritz_z(h, X, ld, ncol, evals, W, ncol, mixed);
-  }
-  residual_norms(h, X, 2 * ld, W, 2 * (int64_t)ncol, m->M, ncol, evals, resid, 0, 2);
-  double ends[2];
-  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[0], evals, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[1], evals + ncol - 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
-  inout->a = ends[1];
-  if (!std::isnan(inout->a0)) inout->a0 = ends[0];
+  chfsi_pass_tail_z(h, X, ld, ncol, inout, evals, resid, prec);
   ABI_END
 }

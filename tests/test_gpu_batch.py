@@ -133,3 +133,98 @@ def test_batch_of_sixteen_small_systems_timing(dg, capsys):
         for mesh, ham, *_ in made:
             dg.dftfe_ham_destroy(ham)
             dg.dftfe_mesh_destroy(mesh)
+
+
+# (seed, cells, p, L, states, block, degree, k)
+KSYSTEMS = [
+    (0, (3, 3, 3), 4, 6.0, 12, 5, 9, (0.2, -0.1, 0.3)),
+    (0, (3, 3, 3), 4, 6.0, 12, 5, 9, (math.pi / 6.0, 0.0, 0.0)),   # a second k-point of the same system
+    (2, (2, 2, 3), 6, 7.0, 10, 2, 7, (0.0, 0.4, 0.0)),              # 2-column blocks: narrow kernel alone
+    (3, (4, 3, 2), 5, 8.0, 16, 16, 8, (0.1, 0.1, 0.1)),
+]
+
+
+def _make_k(dg, spec):
+    seed, n, p, L, N, block, deg, k = spec
+    c = small_case(seed, n=n, p=p, L=L, nl=True)
+    mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    nxyz, _ = dg.dftfe_mesh_coords(mesh, quad=False)
+    cent, w, rc, hc = c["proj"]
+    dg.dftfe_ham_set_kpoint(ham, k, synth.projector_disp(nxyz, cent, rc, c["L"]))
+    M = nxyz.shape[0]
+    Xr = torch.empty((M, 2 * N), dtype=torch.float64, device="cuda")
+    dg.dftfe_random_uniform(Xr, 300 + seed)
+    bd = dg.dftfe_spectrum_bounds_z(ham, 20, 9 + seed, N)
+    return mesh, ham, Xr.view(torch.complex128), bd, block, deg
+
+
+def test_batched_kpoint_and_gamma_passes_are_bit_identical(dg):
+    """Complex items at k-points (two k-points of one system among them) and real Gamma-point
+    items in one batch: each result equals the pass of that item alone."""
+    made = [_make_k(dg, s) for s in KSYSTEMS] + [_make(dg, SYSTEMS[1]), _make(dg, SYSTEMS[2])]
+    batch = dg.dftfe_batch_create([m[1] for m in made])
+    try:
+        Xb = [m[2].clone() for m in made]
+        Xs = [m[2].clone() for m in made]
+        bb = [dg.make_bounds(m[3].a, m[3].b, m[3].a0) for m in made]
+        bs = [dg.make_bounds(m[3].a, m[3].b, m[3].a0) for m in made]
+        evb = [torch.empty(x.shape[1], dtype=torch.float64, device="cuda") for x in Xb]
+        rsb = [torch.empty_like(e) for e in evb]
+        evs = [torch.empty_like(e) for e in evb]
+        rss = [torch.empty_like(e) for e in evb]
+        for _ in range(2):
+            dg.dftfe_batch_chfsi_pass(batch, Xb, [m[4] for m in made], [m[5] for m in made], bb, evb, rsb)
+            for i, (mesh, ham, X0, _, block, deg) in enumerate(made):
+                if X0.is_complex():
+                    dg.dftfe_chfsi_pass_z(ham, Xs[i], block, deg, bs[i], evs[i], rss[i])
+                else:
+                    dg.dftfe_chfsi_pass(ham, Xs[i], block, deg, bs[i], evs[i], rss[i])
+            torch.cuda.synchronize()
+            for i in range(len(made)):
+                assert torch.equal(Xb[i], Xs[i]), i
+                assert torch.equal(evb[i], evs[i]) and torch.equal(rsb[i], rss[i]), i
+        # the two k-points of the same system differ (the k terms are there)
+        assert not torch.equal(evb[0], evb[1])
+    finally:
+        dg.dftfe_batch_destroy(batch)
+        for mesh, ham, *_ in made:
+            dg.dftfe_ham_destroy(ham)
+            dg.dftfe_mesh_destroy(mesh)
+
+
+def test_batch_of_systems_times_kpoints_timing(dg, capsys):
+    """Four small systems x four k-points each in one batched pass against one by one."""
+    specs = []
+    for i in range(4):
+        n = (3 + i % 2, 3, 3 + i // 2)
+        for q in range(4):
+            k = (0.5 * q / (6.0 + n[0]), 0.1 * q, -0.05 * q)
+            specs.append((i, n, 4 + i % 3, 6.0 + n[0], 16, 16, 16, k))
+    made = [_make_k(dg, s) for s in specs]
+    batch = dg.dftfe_batch_create([m[1] for m in made])
+    try:
+        def run(batched):
+            Xs = [m[2].clone() for m in made]
+            bds = [dg.make_bounds(m[3].a, m[3].b, m[3].a0) for m in made]
+            evs = [torch.empty(x.shape[1], dtype=torch.float64, device="cuda") for x in Xs]
+            rss = [torch.empty_like(e) for e in evs]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if batched:
+                dg.dftfe_batch_chfsi_pass(batch, Xs, [m[4] for m in made], [m[5] for m in made], bds, evs, rss)
+            else:
+                for i, m in enumerate(made):
+                    dg.dftfe_chfsi_pass_z(m[1], Xs[i], m[4], m[5], bds[i], evs[i], rss[i])
+            torch.cuda.synchronize()
+            return time.perf_counter() - t0, Xs
+        run(True), run(False)
+        tb, xb = run(True)
+        ts, xs = run(False)
+        assert all(torch.equal(a, b) for a, b in zip(xb, xs))
+        with capsys.disabled():
+            print(f"\n4 systems x 4 k-points (complex128): batched pass {tb * 1e3:.1f} ms, one by one {ts * 1e3:.1f} ms")
+    finally:
+        dg.dftfe_batch_destroy(batch)
+        for mesh, ham, *_ in made:
+            dg.dftfe_ham_destroy(ham)
+            dg.dftfe_mesh_destroy(mesh)
