@@ -407,6 +407,15 @@ dftfe_status dftfe_batch_chfsi_pass(dftfe_batch batch, dftfe_batch_item* items, 
 /* Synchronise the batch's stream and free it (NULL is a no-op). */
 dftfe_status dftfe_batch_destroy(dftfe_batch batch);
 
+/* CUDA graph of the batched filter phase (every round and step of every system, one graph
+ * launch), as dftfe_ham_use_graphs for one ham: the first batched pass with given item shapes
+ * runs directly, later ones capture and update the cached executable.  Bit-identical results.
+ * Synchronises the stream and drops cached graphs. */
+dftfe_status dftfe_batch_use_graphs(dftfe_batch batch, int enable);
+
+/* HOST counts of graph launches and instantiations of the batch since dftfe_batch_use_graphs. */
+dftfe_status dftfe_batch_graph_query(dftfe_batch batch, int64_t* replays, int64_t* instantiations);
+
 /* ------------------------------------------ learned degree / bounds proposer */
 /* The network that proposes the Chebyshev degree and the unwanted-interval bounds of the
  * next pass from the last passes' Ritz values, residuals and bounds (a learned replacement

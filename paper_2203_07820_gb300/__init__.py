@@ -78,6 +78,8 @@ _SIGS = {
     "dftfe_batch_create": [C.POINTER(_vp), _int, C.POINTER(_vp)],
     "dftfe_batch_chfsi_pass": [_vp, _vp, _int],
     "dftfe_batch_destroy": [_vp],
+    "dftfe_batch_use_graphs": [_vp, _int],
+    "dftfe_batch_graph_query": [_vp, C.POINTER(_i64), C.POINTER(_i64)],
     "dftfe_mlp_forward": [_vp, _int, _int, _int, _vp, _i64, _vp, _vp],
     "dftfe_mlp_loss_grad": [_vp, _int, _int, _int, _vp, _vp, _vp, _i64, _vp, _vp, _vp],
     "dftfe_mlp_adam": [_vp, _vp, _vp, _vp, _i64, _int, C.c_float, C.c_float, C.c_float, C.c_float, _vp],
@@ -388,6 +390,16 @@ def dftfe_batch_create(hams):
 
 def dftfe_batch_destroy(batch):
     _check(_lib.dftfe_batch_destroy(batch))
+
+
+def dftfe_batch_use_graphs(batch, enable=True):
+    _check(_lib.dftfe_batch_use_graphs(batch, 1 if enable else 0))
+
+
+def dftfe_batch_graph_query(batch):
+    r, n = _i64(), _i64()
+    _check(_lib.dftfe_batch_graph_query(batch, C.byref(r), C.byref(n)))
+    return r.value, n.value
 
 
 def dftfe_batch_chfsi_pass(batch, Xs, blocks, degrees, bounds, evals, resids, prec=DFTFE_FP64):

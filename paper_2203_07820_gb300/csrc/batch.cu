@@ -15,19 +15,11 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <map>
+#include <string>
 #include <vector>
 
-struct dftfe_batch_s {
-  std::vector<dftfe_ham> hams;
-  cudaStream_t stream = nullptr;
-  int ncolours = 0;                         // most colours of any system
-  std::vector<int64_t> work_off;            // per colour: range in the work list
-  int32_t* d_wsys = nullptr;                // work list: system of each item
-  int32_t* d_wcell = nullptr;               // work list: cell of each item
-  int nc_max = 0;
-  void* d_steps = nullptr;                  // per-step system descriptors
-  size_t steps_bytes = 0;
-};
+
 
 namespace dftfe {
 
@@ -44,6 +36,27 @@ struct SysStep {
   double alpha, s1, s2;
 };
 }  // namespace bt
+
+}  // namespace dftfe
+
+struct dftfe_batch_s {
+  std::vector<dftfe_ham> hams;
+  cudaStream_t stream = nullptr;
+  int ncolours = 0;                         // most colours of any system
+  std::vector<int64_t> work_off;            // per colour: range in the work list
+  int32_t* d_wsys = nullptr;                // work list: system of each item
+  int32_t* d_wcell = nullptr;               // work list: cell of each item
+  int nc_max = 0;
+  void* d_steps = nullptr;                  // per-step system descriptors
+  size_t steps_bytes = 0;
+  std::vector<dftfe::bt::SysStep> host_steps;   // their host copy (kept until the next pass)
+  // CUDA graph of the filter phase (dftfe_batch_use_graphs)
+  bool use_graphs = false;
+  std::map<std::string, dftfe::GraphSlot> graphs;
+  cudaStream_t capture_stream = nullptr;
+};
+
+namespace dftfe {
 
 // Z = s1 X + s2 Xp for every active system (blockIdx.y = system); the same operations in the
 // same order as the single-system k_axpby_init
@@ -97,6 +110,19 @@ static void cheb_coef(const dftfe_bounds& b, int k, double& sigma, double& alpha
   }
 }
 
+// One round = block j of every system.  The descriptors of every round and step are formed
+// on the host and uploaded before any launch, so the launches of the whole filter phase need
+// no host work in between and can be captured as one CUDA graph.
+struct RoundPlan {
+  std::vector<int> nb;                       // real columns of block j (0: none / alone)
+  std::vector<int> alone;                    // blocks of at most 4 real columns: single filter
+  std::vector<int> cur;                      // buffer holding the result after the last step
+  std::vector<std::array<double*, 3>> buf;
+  std::vector<std::array<int64_t, 3>> lds;
+  int maxtiles = 0;
+  int64_t maxwork = 0;
+};
+
 static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
   const int ns = (int)bt->hams.size();
   int rounds = 0, maxdeg = 0;
@@ -104,7 +130,8 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
     rounds = std::max(rounds, (items[s].ncol + items[s].block - 1) / items[s].block);
     maxdeg = std::max(maxdeg, items[s].degree);
   }
-  const size_t need = sizeof(bt::SysStep) * (size_t)std::max(maxdeg, 1) * ns;
+  const size_t per_round = (size_t)std::max(maxdeg, 1) * ns;
+  const size_t need = sizeof(bt::SysStep) * per_round * std::max(rounds, 1);
   if (need > bt->steps_bytes) {
     if (bt->d_steps) DFTFE_CHECK_CUDA(cudaFree(bt->d_steps));
     bt->d_steps = nullptr;
@@ -114,104 +141,142 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
   bt::SysStep* dsteps = (bt::SysStep*)bt->d_steps;
   const size_t sh = (size_t)bt->nc_max * 32 * sizeof(double) + bt->nc_max * sizeof(int32_t);
   DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_batch_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  // the two recurrence workspaces of each system, at the size of its widest block (all
+  // rounds' descriptors point into them, so they must not be reallocated between rounds)
+  std::vector<double*> w1(ns, nullptr), w2(ns, nullptr);
+  for (int s = 0; s < ns; ++s) {
+    const int cw = items[s].kpoint ? 2 : 1;
+    const int widest = cw * std::min(items[s].block, items[s].ncol);
+    if (widest <= 4 || items[s].degree <= 0) continue;
+    dftfe_ham h = bt->hams[s];
+    w1[s] = (double*)ws_get(h, "cheb_w1", sizeof(double) * h->mesh->M * (size_t)widest);
+    w2[s] = (double*)ws_get(h, "cheb_w2", sizeof(double) * h->mesh->M * (size_t)widest);
+  }
+  bt->host_steps.assign(per_round * std::max(rounds, 1), bt::SysStep{});
+  std::vector<RoundPlan> plan(rounds);
   for (int j = 0; j < rounds; ++j) {
-    // per system: block j of its columns, three rotating buffers, the step descriptors
-    std::vector<bt::SysStep> host((size_t)std::max(maxdeg, 1) * ns);
-    std::vector<int> cur(ns, 0), prev(ns, -1), nb(ns, 0), tiles(ns, 0);
-    std::vector<std::array<double*, 3>> buf(ns);
-    std::vector<std::array<int64_t, 3>> lds(ns);
-    int maxtiles = 0;
-    std::vector<int> alone;                       // blocks of at most 4 columns: narrow kernel
+    RoundPlan& r = plan[j];
+    r.nb.assign(ns, 0);
+    r.cur.assign(ns, 0);
+    r.buf.resize(ns);
+    r.lds.resize(ns);
+    std::vector<int> prev(ns, -1);
     for (int s = 0; s < ns; ++s) {
-      dftfe_ham h = bt->hams[s];
       // a complex block is handled through its real view: 2 doubles per complex column
       const int cw = items[s].kpoint ? 2 : 1;
-      nb[s] = cw * std::min(items[s].block, items[s].ncol - j * items[s].block);
-      if (nb[s] <= 0 || items[s].degree <= 0) { nb[s] = 0; continue; }
-      if (nb[s] <= 4) {
-        alone.push_back(s);
-        nb[s] = 0;
+      int nb = cw * std::min(items[s].block, items[s].ncol - j * items[s].block);
+      if (nb <= 0 || items[s].degree <= 0) continue;
+      if (nb <= 4) {
+        r.alone.push_back(s);
         continue;
       }
-      double* w1 = (double*)ws_get(h, "cheb_w1", sizeof(double) * h->mesh->M * (size_t)nb[s]);
-      double* w2 = (double*)ws_get(h, "cheb_w2", sizeof(double) * h->mesh->M * (size_t)nb[s]);
-      buf[s] = {items[s].X + (int64_t)cw * j * items[s].block, w1, w2};
-      lds[s] = {cw * items[s].ld, nb[s], nb[s]};
-      tiles[s] = (nb[s] + 31) / 32;
-      maxtiles = std::max(maxtiles, tiles[s]);
+      r.nb[s] = nb;
+      r.buf[s] = {items[s].X + (int64_t)cw * j * items[s].block, w1[s], w2[s]};
+      r.lds[s] = {cw * items[s].ld, nb, nb};
+      r.maxtiles = std::max(r.maxtiles, (nb + 31) / 32);
+      r.maxwork = std::max<int64_t>(r.maxwork, bt->hams[s]->mesh->M * nb);
     }
     std::vector<double> sigma(ns, 0.0);
     for (int k = 1; k <= maxdeg; ++k)
       for (int s = 0; s < ns; ++s) {
-        bt::SysStep& d = host[(size_t)(k - 1) * ns + s];
-        d = bt::SysStep{};
-        if (nb[s] == 0 || k > items[s].degree) continue;
+        bt::SysStep& d = bt->host_steps[(size_t)j * per_round + (size_t)(k - 1) * ns + s];
+        if (r.nb[s] == 0 || k > items[s].degree) continue;
         dftfe_ham h = bt->hams[s];
         int out = 0;
-        while (out == cur[s] || out == prev[s]) ++out;
+        while (out == r.cur[s] || out == prev[s]) ++out;
         double alpha, s1, s2;
         cheb_coef(items[s].bounds, k, sigma[s], alpha, s1, s2);
         d.Hc = h->d_Hc;
         d.map = h->d_map;
-        d.X = buf[s][cur[s]];
-        d.ldx = lds[s][cur[s]];
-        d.Xp = prev[s] >= 0 ? buf[s][prev[s]] : nullptr;
-        d.ldp = prev[s] >= 0 ? lds[s][prev[s]] : 0;
-        d.Z = buf[s][out];
-        d.ldz = lds[s][out];
+        d.X = r.buf[s][r.cur[s]];
+        d.ldx = r.lds[s][r.cur[s]];
+        d.Xp = prev[s] >= 0 ? r.buf[s][prev[s]] : nullptr;
+        d.ldp = prev[s] >= 0 ? r.lds[s][prev[s]] : 0;
+        d.Z = r.buf[s][out];
+        d.ldz = r.lds[s][out];
         d.M = h->mesh->M;
         d.nc = h->mesh->nc;
-        d.ncol = nb[s];
+        d.ncol = r.nb[s];
         d.active = 1;
         d.cplx = items[s].kpoint ? 1 : 0;
         d.alpha = alpha;
         d.s1 = s1;
         d.s2 = s2;
-        prev[s] = cur[s];
-        cur[s] = out;
+        prev[s] = r.cur[s];
+        r.cur[s] = out;
       }
-    DFTFE_CHECK_CUDA(cudaMemcpyAsync(dsteps, host.data(), sizeof(bt::SysStep) * host.size(), cudaMemcpyHostToDevice,
-                                     bt->stream));
-    int64_t maxwork = 0;
-    for (int s = 0; s < ns; ++s) maxwork = std::max<int64_t>(maxwork, bt->hams[s]->mesh->M * nb[s]);
-    for (int k = 1; k <= maxdeg; ++k) {
-      const bt::SysStep* dk = dsteps + (size_t)(k - 1) * ns;
-      const unsigned gx = (unsigned)std::min<int64_t>((maxwork + 255) / 256, 4096);
-      DFTFE_LAUNCH(k_batch_axpby, dim3(std::max(gx, 1u), (unsigned)ns), 256, 0, bt->stream, dk);
-      for (int s = 0; s < ns; ++s) {
-        const bt::SysStep& d = host[(size_t)(k - 1) * ns + s];
-        if (!d.active) continue;
-        if (d.cplx)      // the recurrence terms, 1/2|k|^2, -i k.grad and the phased projectors
-          kpoint_init_terms(bt->hams[s], d.X, d.ldx / 2, d.Xp, d.ldp / 2, d.Z, d.ldz / 2, d.ncol / 2, d.alpha,
-                            d.s1, d.s2);
-        else
-          nonlocal_add_fp64(bt->hams[s], d.X, d.ldx, d.Z, d.ldz, d.ncol, d.alpha);
-      }
-      for (int c = 0; c < bt->ncolours; ++c) {
-        const int64_t n = bt->work_off[c + 1] - bt->work_off[c];
-        if (n == 0 || maxtiles == 0) continue;
-        ProfScope ps(bt->hams[0], "batch_cell");
-        const int splits = fp64_row_splits(bt->hams[0], n * maxtiles, bt->nc_max);
-        const int rows = ((bt->nc_max + splits - 1) / splits + 63) / 64 * 64;
-        DFTFE_LAUNCH(k_batch_cell, dim3((unsigned)n, (unsigned)maxtiles, (unsigned)((bt->nc_max + rows - 1) / rows)), 256,
-                     sh, bt->stream, dk, bt->d_wsys + bt->work_off[c], bt->d_wcell + bt->work_off[c], rows);
-      }
-    }
-    for (int s = 0; s < ns; ++s)
-      if (nb[s] > 0 && cur[s] != 0)
-        copy_block(bt->stream, buf[s][cur[s]], lds[s][cur[s]], buf[s][0], lds[s][0], bt->hams[s]->mesh->M, nb[s]);
-    for (int s : alone) {
-      const int n = std::min(items[s].block, items[s].ncol - j * items[s].block);
-      if (items[s].kpoint)
-        chebyshev_filter_z_fp64(bt->hams[s], items[s].X + 2 * (int64_t)j * items[s].block, items[s].ld, n,
-                                items[s].degree, items[s].bounds);
-      else
-        chebyshev_filter(bt->hams[s], items[s].X + (int64_t)j * items[s].block, items[s].ld, n, items[s].degree,
-                         items[s].bounds);
-    }
-    // the host descriptors must outlive the copy above: wait before they go out of scope
-    DFTFE_CHECK_CUDA(cudaStreamSynchronize(bt->stream));
   }
+  // from pageable memory: the call returns once the data is staged, so the host descriptors
+  // may be rewritten by the next pass
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(dsteps, bt->host_steps.data(), sizeof(bt::SysStep) * bt->host_steps.size(),
+                                   cudaMemcpyHostToDevice, bt->stream));
+
+  auto enqueue = [&]() {
+    for (int j = 0; j < rounds; ++j) {
+      const RoundPlan& r = plan[j];
+      for (int k = 1; k <= maxdeg; ++k) {
+        const size_t off = (size_t)j * per_round + (size_t)(k - 1) * ns;
+        const bt::SysStep* dk = dsteps + off;
+        if (r.maxwork > 0) {
+          const unsigned gx = (unsigned)std::min<int64_t>((r.maxwork + 255) / 256, 4096);
+          DFTFE_LAUNCH(k_batch_axpby, dim3(std::max(gx, 1u), (unsigned)ns), 256, 0, bt->stream, dk);
+        }
+        for (int s = 0; s < ns; ++s) {
+          const bt::SysStep& d = bt->host_steps[off + s];
+          if (!d.active) continue;
+          if (d.cplx)      // the recurrence terms, 1/2|k|^2, -i k.grad and the phased projectors
+            kpoint_init_terms(bt->hams[s], d.X, d.ldx / 2, d.Xp, d.ldp / 2, d.Z, d.ldz / 2, d.ncol / 2, d.alpha,
+                              d.s1, d.s2);
+          else
+            nonlocal_add_fp64(bt->hams[s], d.X, d.ldx, d.Z, d.ldz, d.ncol, d.alpha);
+        }
+        for (int c = 0; c < bt->ncolours; ++c) {
+          const int64_t n = bt->work_off[c + 1] - bt->work_off[c];
+          if (n == 0 || r.maxtiles == 0) continue;
+          ProfScope ps(bt->hams[0], "batch_cell");
+          const int splits = fp64_row_splits(bt->hams[0], n * r.maxtiles, bt->nc_max);
+          const int rows = ((bt->nc_max + splits - 1) / splits + 63) / 64 * 64;
+          DFTFE_LAUNCH(k_batch_cell, dim3((unsigned)n, (unsigned)r.maxtiles, (unsigned)((bt->nc_max + rows - 1) / rows)),
+                       256, sh, bt->stream, dk, bt->d_wsys + bt->work_off[c], bt->d_wcell + bt->work_off[c], rows);
+        }
+      }
+      for (int s = 0; s < ns; ++s)
+        if (r.nb[s] > 0 && r.cur[s] != 0)
+          copy_block(bt->stream, r.buf[s][r.cur[s]], r.lds[s][r.cur[s]], r.buf[s][0], r.lds[s][0],
+                     bt->hams[s]->mesh->M, r.nb[s]);
+      for (int s : r.alone) {
+        const int n = std::min(items[s].block, items[s].ncol - j * items[s].block);
+        if (items[s].kpoint)
+          chebyshev_filter_z_fp64(bt->hams[s], items[s].X + 2 * (int64_t)j * items[s].block, items[s].ld, n,
+                                  items[s].degree, items[s].bounds);
+        else
+          chebyshev_filter(bt->hams[s], items[s].X + (int64_t)j * items[s].block, items[s].ld, n, items[s].degree,
+                           items[s].bounds);
+      }
+    }
+  };
+  if (!bt->use_graphs) {
+    enqueue();
+    return;
+  }
+  std::string key = "batch";
+  for (int s = 0; s < ns; ++s)
+    key += "/" + std::to_string(items[s].ncol) + "," + std::to_string(items[s].block) + "," +
+           std::to_string(items[s].degree) + "," + std::to_string(items[s].kpoint);
+  GraphSlot& slot = bt->graphs[key];
+  if (!slot.warm) {
+    enqueue();
+    slot.warm = true;
+    return;
+  }
+  if (!bt->capture_stream) DFTFE_CHECK_CUDA(cudaStreamCreateWithFlags(&bt->capture_stream, cudaStreamNonBlocking));
+  std::vector<cudaStream_t*> streams = {&bt->stream};
+  std::vector<bool*> prof;
+  for (auto h : bt->hams) {
+    streams.push_back(&h->stream);
+    prof.push_back(&h->profiling);
+  }
+  capture_and_launch(slot, bt->stream, bt->capture_stream, streams, prof, enqueue);
 }
 
 }  // namespace dftfe
@@ -280,6 +345,9 @@ extern "C" dftfe_status dftfe_batch_destroy(dftfe_batch b) {
   cudaFree(b->d_wsys);
   cudaFree(b->d_wcell);
   cudaFree(b->d_steps);
+  for (auto& kv : b->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
   delete b;
   ABI_END
 }
@@ -314,5 +382,30 @@ extern "C" dftfe_status dftfe_batch_chfsi_pass(dftfe_batch b, dftfe_batch_item* 
     else
       chfsi_pass_tail(b->hams[s], items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
                       items[s].resid, prec);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_batch_use_graphs(dftfe_batch b, int enable) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(b, "null batch");
+  DFTFE_REQUIRE(enable == 0 || enable == 1, "enable must be 0 or 1");
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(b->stream));
+  for (auto& kv : b->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  b->graphs.clear();
+  b->use_graphs = enable == 1;
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_batch_graph_query(dftfe_batch b, int64_t* replays, int64_t* instantiations) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(b && replays && instantiations, "null argument");
+  int64_t r = 0, n = 0;
+  for (auto& kv : b->graphs) {
+    r += kv.second.replays;
+    n += kv.second.reinstantiations;
+  }
+  *replays = r;
+  *instantiations = n;
   ABI_END
 }

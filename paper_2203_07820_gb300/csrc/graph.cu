@@ -13,38 +13,33 @@
 
 namespace dftfe {
 
-void run_region(dftfe_ham h, const std::string& key, const std::function<void()>& enqueue) {
-  if (!h->use_graphs) {
-    enqueue();
-    return;
-  }
-  GraphSlot& slot = h->graphs[key];
-  if (!slot.warm) {
-    enqueue();
-    slot.warm = true;
-    return;
-  }
-  // per-kernel timers would record events inside the graph; the caller times the region
-  if (!h->capture_stream) DFTFE_CHECK_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
-  const bool prof = h->profiling;
-  const cudaStream_t own = h->stream;
+// The capture itself, shared by single hams and batches: every stream variable in `streams`
+// (all holding the stream `own`) points at `cap` while `enqueue` runs, and every profiling
+// flag in `prof` is cleared (per-kernel timers would record events inside the graph; the
+// caller times the region as a whole).
+void capture_and_launch(GraphSlot& slot, cudaStream_t own, cudaStream_t cap, const std::vector<cudaStream_t*>& streams,
+                        const std::vector<bool*>& prof, const std::function<void()>& enqueue) {
+  std::vector<bool> saved;
+  for (bool* f : prof) saved.push_back(*f);
+  auto restore = [&]() {
+    for (auto* sp : streams) *sp = own;
+    for (size_t i = 0; i < prof.size(); ++i) *prof[i] = saved[i];
+  };
   cudaGraph_t g = nullptr;
-  DFTFE_CHECK_CUDA(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-  h->profiling = false;
-  h->stream = h->capture_stream;
+  DFTFE_CHECK_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  for (auto* sp : streams) *sp = cap;
+  for (bool* f : prof) *f = false;
   try {
     enqueue();
   } catch (...) {
-    h->stream = own;
-    h->profiling = prof;
-    cudaStreamEndCapture(h->capture_stream, &g);
+    restore();
+    cudaStreamEndCapture(cap, &g);
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
     throw;
   }
-  h->stream = own;
-  h->profiling = prof;
-  DFTFE_CHECK_CUDA(cudaStreamEndCapture(h->capture_stream, &g));
+  restore();
+  DFTFE_CHECK_CUDA(cudaStreamEndCapture(cap, &g));
   if (slot.exec) {
     cudaGraphExecUpdateResultInfo info;
     if (cudaGraphExecUpdate(slot.exec, g, &info) != cudaSuccess) {
@@ -63,8 +58,23 @@ void run_region(dftfe_ham h, const std::string& key, const std::function<void()>
     ++slot.reinstantiations;
   }
   cudaGraphDestroy(g);
-  DFTFE_CHECK_CUDA(cudaGraphLaunch(slot.exec, h->stream));
+  DFTFE_CHECK_CUDA(cudaGraphLaunch(slot.exec, own));
   ++slot.replays;
+}
+
+void run_region(dftfe_ham h, const std::string& key, const std::function<void()>& enqueue) {
+  if (!h->use_graphs) {
+    enqueue();
+    return;
+  }
+  GraphSlot& slot = h->graphs[key];
+  if (!slot.warm) {
+    enqueue();
+    slot.warm = true;
+    return;
+  }
+  if (!h->capture_stream) DFTFE_CHECK_CUDA(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+  capture_and_launch(slot, h->stream, h->capture_stream, {&h->stream}, {&h->profiling}, enqueue);
 }
 
 void free_graphs(dftfe_ham h) {

@@ -264,6 +264,10 @@ void local_part_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int64
 // ham uses graphs: the first call with a key runs directly, later ones capture and replay.
 void run_region(dftfe_ham h, const std::string& key, const std::function<void()>& enqueue);
 void free_graphs(dftfe_ham h);
+// capture `enqueue` from stream `cap` (the variables in `streams`, all equal to `own`, point at
+// it meanwhile; the flags in `prof` are cleared), update or instantiate slot.exec, launch on own
+void capture_and_launch(GraphSlot& slot, cudaStream_t own, cudaStream_t cap, const std::vector<cudaStream_t*>& streams,
+                        const std::vector<bool*>& prof, const std::function<void()>& enqueue);
 
 // kpoint.cu: Z = alpha H~^k X + s1 X + s2 Xp on complex blocks (ld in complex elements)
 void apply_combo_z(dftfe_ham h, const double* X, int64_t ldx, const double* Xp, int64_t ldp, double* Z,

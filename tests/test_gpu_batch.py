@@ -125,9 +125,22 @@ def test_batch_of_sixteen_small_systems_timing(dg, capsys):
         tb, xb = run(True)
         ts, xs = run(False)
         assert all(torch.equal(a, b) for a, b in zip(xb, xs))
+        dg.dftfe_batch_use_graphs(batch, True)
+        run(True)                                               # first graphed pass runs directly
+        tg, xg = run(True)
+        assert all(torch.equal(a, b) for a, b in zip(xg, xs))
+        for m in made:
+            dg.dftfe_profile_enable(m[1], True)
+        run(True)
+        filt = dg.dftfe_profile_query(made[0][1], "batch_filter")[0]
+        chol = sum(dg.dftfe_profile_query(m[1], "pass_cholgs")[0] for m in made)
+        rr = sum(dg.dftfe_profile_query(m[1], "pass_rr")[0] for m in made)
+        for m in made:
+            dg.dftfe_profile_enable(m[1], False)
         with capsys.disabled():
             print(f"\n16 systems ({sum(m[2].shape[0] for m in made)} DoFs in all): batched pass {tb * 1e3:.1f} ms, "
-                  f"one by one {ts * 1e3:.1f} ms")
+                  f"graphed {tg * 1e3:.1f} ms, one by one {ts * 1e3:.1f} ms; batched phases: filter {filt:.1f} ms, "
+                  f"CholGS {chol:.1f} ms, Rayleigh-Ritz {rr:.1f} ms")
     finally:
         dg.dftfe_batch_destroy(batch)
         for mesh, ham, *_ in made:
@@ -226,5 +239,39 @@ def test_batch_of_systems_times_kpoints_timing(dg, capsys):
     finally:
         dg.dftfe_batch_destroy(batch)
         for mesh, ham, *_ in made:
+            dg.dftfe_ham_destroy(ham)
+            dg.dftfe_mesh_destroy(mesh)
+
+
+def test_graphed_batched_pass_is_bit_identical(dg):
+    """The batched filter phase as one CUDA graph (Gamma-point and k-point items, a narrow
+    block among them) gives the bits of the plain batched pass."""
+    specs = [SYSTEMS[0], SYSTEMS[2]]
+    made1 = [_make(dg, s) for s in specs] + [_make_k(dg, KSYSTEMS[0]), _make_k(dg, KSYSTEMS[2])]
+    made2 = [_make(dg, s) for s in specs] + [_make_k(dg, KSYSTEMS[0]), _make_k(dg, KSYSTEMS[2])]
+    b1 = dg.dftfe_batch_create([m[1] for m in made1])
+    b2 = dg.dftfe_batch_create([m[1] for m in made2])
+    dg.dftfe_batch_use_graphs(b2, True)
+    try:
+        X1 = [m[2].clone() for m in made1]
+        X2 = [m[2].clone() for m in made1]
+        bd1 = [dg.make_bounds(m[3].a, m[3].b, m[3].a0) for m in made1]
+        bd2 = [dg.make_bounds(m[3].a, m[3].b, m[3].a0) for m in made1]
+        e1 = [torch.empty(x.shape[1], dtype=torch.float64, device="cuda") for x in X1]
+        r1 = [torch.empty_like(e) for e in e1]
+        e2 = [torch.empty_like(e) for e in e1]
+        r2 = [torch.empty_like(e) for e in e1]
+        blocks, degs = [m[4] for m in made1], [m[5] for m in made1]
+        for it in range(3):
+            dg.dftfe_batch_chfsi_pass(b1, X1, blocks, degs, bd1, e1, r1)
+            dg.dftfe_batch_chfsi_pass(b2, X2, blocks, degs, bd2, e2, r2)
+            torch.cuda.synchronize()
+            for i in range(len(X1)):
+                assert torch.equal(X1[i], X2[i]) and torch.equal(e1[i], e2[i]), (it, i)
+        assert dg.dftfe_batch_graph_query(b2)[0] == 2
+    finally:
+        dg.dftfe_batch_destroy(b1)
+        dg.dftfe_batch_destroy(b2)
+        for mesh, ham, *_ in made1 + made2:
             dg.dftfe_ham_destroy(ham)
             dg.dftfe_mesh_destroy(mesh)
