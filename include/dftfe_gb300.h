@@ -316,6 +316,13 @@ dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, int ncol, vo
  * Non-finite k or displacements: DFTFE_ERR_ARG.  Synchronises the stream. */
 dftfe_status dftfe_ham_set_kpoint(dftfe_ham ham, const double* k, const double* disp);
 
+/* The k.grad stencil the _z calls apply (host only, no device work): on this structured
+ * periodic mesh G~_d acts along axis d alone, G~_d = G~1_d with G~1_d = m_d^-1/2 G1_d m_d^-1/2,
+ * G1_d the assembled 1D periodic matrix of int l_a l_b' (= w_a l_b'(x_a), exact under GLL) and
+ * m_d the 1D lumped mass.  table: HOST 3 x p x (2p+1) doubles, entry (d, a, o + p) =
+ * k_d G~1_d(i, i + o) for any node i with i mod p = a (zero outside the element couplings). */
+dftfe_status dftfe_mesh_kpoint_stencil(dftfe_mesh mesh, const double* k, double* table);
+
 /* Y = H~^k X for complex M x ncol blocks (X, Y DEVICE, not overlapping).  prec as in
  * dftfe_ham_apply: FP64; DFTFE_FP64_FLOAT_PAIRS (local part from float pairs, k terms and
  * projectors FP64: the W of a mixed complex pass); or a split precision (FP32 complex inside:

@@ -88,6 +88,7 @@ _SIGS = {
     "dftfe_ham_autotune": [_vp, _int],
     "dftfe_autotune_query": [_vp, _int, C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
     "dftfe_ham_set_kpoint": [_vp, _vp, _vp],
+    "dftfe_mesh_kpoint_stencil": [_vp, _vp, _vp],
     "dftfe_ham_apply_z": [_vp, _vp, _i64, _vp, _i64, _int, _int],
     "dftfe_lanczos_z": [_vp, _int, _vp, C.c_uint64, _vp],
     "dftfe_spectrum_bounds_z": [_vp, _int, C.c_uint64, _int, C.POINTER(Bounds)],
@@ -322,6 +323,14 @@ def dftfe_ham_set_kpoint(ham, k, disp=None):
     else:
         dd, pd = _host(np.asarray(disp, np.float64).reshape(-1, 3), np.float64)
         _check(_lib.dftfe_ham_set_kpoint(ham, pk, pd))
+
+
+def dftfe_mesh_kpoint_stencil(mesh, k, degree):
+    """Host table of the k.grad stencil, shape (3, p, 2p + 1)."""
+    kk, pk = _host(np.asarray(k, np.float64).reshape(3), np.float64)
+    out = np.zeros((3, degree, 2 * degree + 1))
+    _check(_lib.dftfe_mesh_kpoint_stencil(mesh, pk, out.ctypes.data_as(_vp)))
+    return out
 
 
 def dftfe_ham_apply_z(ham, X, Y, prec=DFTFE_FP64):

@@ -312,10 +312,9 @@ __global__ void k_realify(const double2* __restrict__ Q, int N, double* __restri
 
 // -------------------------------------------------------------- host side
 // k_d G~1_d stencil tables (see the file comment)
-static void build_ktab(dftfe_ham h) {
-  auto* m = h->mesh;
+// host: tab[(d p + a)(2p+1) + o + p] = k_d G~1_d(i, i + o) for nodes i with i mod p = a
+static void stencil_table(const dftfe_mesh_s* m, const double* kvec, double* tab) {
   const int p = m->p, n1 = m->n1, W = 2 * p + 1;
-  std::vector<double> tab(3 * (size_t)p * W, 0.0);
   const auto& w = m->gll.w;
   const auto& D = m->D;
   for (int d = 0; d < 3; ++d) {
@@ -326,9 +325,16 @@ static void build_ktab(dftfe_ham h) {
         if (a + o >= 0 && a + o <= p) g += w[a] * D[(size_t)a * n1 + a + o];     // the cell where the node is local a
         if (a == 0 && o <= 0) g += w[p] * D[(size_t)p * n1 + p + o];           // a = 0: also local p of the previous cell
         const int64_t j = ((a + o) % gd + gd) % gd;
-        tab[((size_t)d * p + a) * W + (o + p)] = h->kvec[d] * g / std::sqrt(m->m1[d][a] * m->m1[d][j]);
+        tab[((size_t)d * p + a) * W + (o + p)] = kvec[d] * g / std::sqrt(m->m1[d][a] * m->m1[d][j]);
       }
   }
+}
+
+static void build_ktab(dftfe_ham h) {
+  auto* m = h->mesh;
+  const int p = m->p, W = 2 * p + 1;
+  std::vector<double> tab(3 * (size_t)p * W, 0.0);
+  stencil_table(m, h->kvec, tab.data());
   if (!h->d_ktab) DFTFE_CHECK_CUDA(cudaMalloc(&h->d_ktab, sizeof(double) * tab.size()));
   if (!h->d_ktab32) DFTFE_CHECK_CUDA(cudaMalloc(&h->d_ktab32, sizeof(float) * tab.size()));
   std::vector<float> tab32(tab.begin(), tab.end());
@@ -566,6 +572,14 @@ void chfsi_pass_tail_z(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_bound
 }  // namespace dftfe
 
 using namespace dftfe;
+
+extern "C" dftfe_status dftfe_mesh_kpoint_stencil(dftfe_mesh m, const double* kvec, double* table) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(m && kvec && table, "null argument");
+  for (int d = 0; d < 3; ++d) DFTFE_REQUIRE(std::isfinite(kvec[d]), "k must be finite");
+  stencil_table(m, kvec, table);
+  ABI_END
+}
 
 extern "C" dftfe_status dftfe_ham_set_kpoint(dftfe_ham h, const double* kvec, const double* disp) {
   ABI_BEGIN

@@ -77,3 +77,42 @@ def test_null_arguments_rejected(dg):
     assert lib.dftfe_ham_apply(None, None, 0, None, 0, 0, 0) == 1
     assert lib.dftfe_chfsi_pass(None, None, 0, 0, 0, 0, None, None, None, 0) == 1
     assert lib.dftfe_random_uniform(None, -1, 0, 0, None) == 1
+
+
+def _g1_tilde(L, n, p):
+    """m^-1/2 G1 m^-1/2 for the 1D periodic mesh, G1 assembled from int l_a l_b' = w_a l_b'(x_a)."""
+    from oracle.basis import gll_rule, lagrange_deriv_table
+    x, w = gll_rule(p)
+    D = lagrange_deriv_table(x, x)
+    h = L / n
+    g = n * p
+    G1 = np.zeros((g, g))
+    m1 = np.zeros(g)
+    for c in range(n):
+        idx = [(c * p + a) % g for a in range(p + 1)]
+        G1[np.ix_(idx, idx)] += w[:, None] * D
+        m1[idx] += w * h / 2
+    s = 1.0 / np.sqrt(m1)
+    return s[:, None] * G1 * s[None, :]
+
+
+@pytest.mark.parametrize("L,n,p,k", [((6.0, 7.0, 8.0), (3, 4, 5), 4, (0.3, -0.7, 1.1)),
+                                     ((5.0, 5.0, 9.0), (3, 3, 3), 6, (0.25, 0.0, -0.4)),
+                                     ((4.0, 6.0, 5.0), (2, 2, 3), 3, (0.5, 0.2, 0.1))])
+def test_kpoint_stencil_table_matches_1d_assembly(dg, L, n, p, k):
+    """The library's k.grad stencil (host table, no GPU) against the 1D periodic operator
+    assembled here: every entry k_d G~1_d(i, i + o), summed where two offsets reach the same
+    node (two cells per axis)."""
+    mesh = dg.dftfe_mesh_create(L, n, p)
+    tab = dg.dftfe_mesh_kpoint_stencil(mesh, k, p)
+    dg.dftfe_mesh_destroy(mesh)
+    for d in range(3):
+        G = k[d] * _g1_tilde(L[d], n[d], p)
+        g = n[d] * p
+        for c in range(n[d]):
+            for a in range(p):
+                i = c * p + a
+                row = np.zeros(g)
+                for o in range(-p, p + 1):
+                    row[(i + o) % g] += tab[d, a, o + p]
+                assert np.abs(row - G[i]).max() <= 1e-13 * max(1.0, np.abs(G).max()), (d, c, a)

@@ -349,3 +349,35 @@ def test_kpoint_state_errors(dg):
         dg.dftfe_ham_apply_z(ham, X.real.contiguous(), X.real.contiguous())
     dg.dftfe_ham_destroy(ham)
     dg.dftfe_mesh_destroy(mesh)
+
+
+def test_bench_kpoint_workload_apply_matches_oracle(dg):
+    """bench.py's k-point workload (10 bohr cube, 8^3 cells, p = 5: 64,000 DoFs, 8 wells with
+    projectors, k = (0.25, 0.10, -0.15)) at its block width (64 complex columns): the FP64
+    apply element by element, the TF32x3 apply within its bound."""
+    L, n, p = 10.0, 8, 5
+    k = (0.25, 0.10, -0.15)
+    s = synth.Stream(7)
+    cent = np.array([[L * s.uniform() for _ in range(3)] for _ in range(8)])
+    hc = np.array([0.5 + 1.5 * s.uniform() for _ in range(32)])
+    om, oh = oracle_system(L, n, p, cent, 2.0, 1.0, 0, (cent, 1.0, 2.5, hc))
+    B = kpoint.BlochHamiltonian(oh, k)
+    rp, nd, chi = synth.projector_csr(om.node_xyz(), cent, 1.0, 2.5, L)
+    B.set_nonlocal(hc, rp, nd, chi, synth.projector_disp(om.node_xyz(), cent, 2.5, L))
+    mesh, ham = gpu_system(L, n, p, cent, 2.0, 1.0, 0, (cent, 1.0, 2.5, hc))
+    try:
+        nxyz, _ = dg.dftfe_mesh_coords(mesh, quad=False)
+        dg.dftfe_ham_set_kpoint(ham, k, synth.projector_disp(nxyz, cent, 2.5, L))
+        X0 = _zblock(77, om.ndofs, 64)
+        X = _t(X0)
+        Y = torch.empty_like(X)
+        ref = B.apply(X0)
+        dg.dftfe_ham_apply_z(ham, X, Y)
+        assert _rel(Y.cpu().numpy(), ref) < TOL_APPLY
+        dg.dftfe_ham_apply_z(ham, X, Y, 2)
+        err = np.abs(Y.cpu().numpy() - ref)
+        c = 8.0 + om.nodes_per_cell * 2.0 ** -24 / U[2]
+        assert np.all(err <= c * U[2] * _abs_bound(om, B, X0) + 1e-30)
+    finally:
+        dg.dftfe_ham_destroy(ham)
+        dg.dftfe_mesh_destroy(mesh)
