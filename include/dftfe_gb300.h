@@ -293,7 +293,7 @@ dftfe_status dftfe_density(dftfe_ham ham, const double* Xo, int64_t ldo, int nco
 dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, int ncol, void* stream);
 
 /* -------------------------------------------------------------- Bloch k-points */
-/* The periodic part u of a Bloch state psi = e^{ik.x} u (Sec. 2, Eq. bloch) solves the reduced
+/* The periodic part u of a Bloch state psi = e^{ik.x} u (Sec. 2.1, Eq. bloch) solves the reduced
  * equation after Eq. bloch.  Discretised with the same basis and quadratures as at the Gamma
  * point, its Loewdin form is
  *   H~^k = H~_loc + 1/2 |k|^2 - i sum_d k_d G~_d + C~^k diag(h) C~^k^H,

@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-With the Bloch form psi = e^{ik.x} u (Sec. 2, Eq. bloch), the periodic part u solves
-the reduced Kohn-Sham equation on the cell (Sec. 2, the equation after Eq. bloch):
+With the Bloch form psi = e^{ik.x} u (Sec. 2.1, Eq. bloch), the periodic part u solves
+the reduced Kohn-Sham equation on the cell (Sec. 2.1, the equation after Eq. bloch):
   (-1/2 lap - i k.grad + 1/2 |k|^2 + V_loc) u + e^{-ik.x} V_nl (e^{ik.y} u) = eps u.
 Discretised with the same real spectral-element basis N_j and the same quadratures as at
 the Gamma point (hamiltonian.py), cell by cell:

@@ -1,4 +1,4 @@
-// Bloch k-points (Sec. 2: psi = e^{ik.x} u, Eq. bloch, and the reduced Kohn-Sham equation
+// Bloch k-points (Sec. 2.1: psi = e^{ik.x} u, Eq. bloch, and the reduced Kohn-Sham equation
 // after it): H~^k on complex blocks and the complex ChFSI steps, FP64 (complex128).
 //
 //   H~^k = H~_loc + 1/2 |k|^2 - i sum_d k_d G~_d + C~^k diag(h) C~^k^H,

@@ -1,4 +1,4 @@
-"""Oracle pins for the Bloch k-point Hamiltonian H~^k and the complex ChFSI steps (Sec. 2,
+"""Oracle pins for the Bloch k-point Hamiltonian H~^k and the complex ChFSI steps (Sec. 2.1,
 the reduced Kohn-Sham equation after Eq. bloch; Eq. chebyfilter, Alg. 2 with complex
 blocks).  Independent routes: 1D operators assembled here and combined as a Kronecker sum,
 the free-electron closed form 1/2 |k + G|^2, Bloch folding of a doubled supercell at the
