@@ -39,7 +39,6 @@ constexpr int kStagesA = 4, kStagesB = 2;
 constexpr int kTile = 16384;                       // one 128-row x 128-byte operand tile
 constexpr int kStageBytes = 2 * kTile;             // hi + lo
 constexpr int kMaxMTiles = 4;                      // 4 x 128 accumulator columns = 512 TMEM columns
-constexpr long kSpinLimit = tc::kSpinLimit;
 constexpr int kPatchLd = 36;                       // epilogue patch row stride (floats)
 constexpr int kPatchBytes = 4 * 32 * kPatchLd * 4;
 

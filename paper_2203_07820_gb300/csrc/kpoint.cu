@@ -598,8 +598,12 @@ extern "C" dftfe_status dftfe_ham_set_kpoint(dftfe_ham h, const double* kvec, co
     h->d_pval_z = h->d_sval_z = nullptr;
     DFTFE_CHECK_CUDA(cudaMalloc(&h->d_pval_z, sizeof(double2) * nnz));
     DFTFE_CHECK_CUDA(cudaMalloc(&h->d_sval_z, sizeof(double2) * nnz));
-    double* d_disp = nullptr;
-    DFTFE_CHECK_CUDA(cudaMalloc(&d_disp, sizeof(double) * 3 * nnz));
+    struct DevFree {
+      double* p = nullptr;
+      ~DevFree() { cudaFree(p); }
+    } disp_buf;
+    DFTFE_CHECK_CUDA(cudaMalloc(&disp_buf.p, sizeof(double) * 3 * nnz));
+    double* d_disp = disp_buf.p;
     DFTFE_CHECK_CUDA(cudaMemcpyAsync(d_disp, disp, sizeof(double) * 3 * nnz, cudaMemcpyHostToDevice, h->stream));
     DFTFE_LAUNCH(k_phase_vals, nblk(nnz), 256, 0, h->stream, (double2*)h->d_pval_z, h->d_pval, d_disp, kvec[0],
                  kvec[1], kvec[2], nnz);
@@ -613,7 +617,6 @@ extern "C" dftfe_status dftfe_ham_set_kpoint(dftfe_ham h, const double* kvec, co
     DFTFE_LAUNCH(k_to_f2, nblk(nnz), 256, 0, h->stream, (float2*)h->d_pval_z32, (const double2*)h->d_pval_z, nnz);
     DFTFE_LAUNCH(k_to_f2, nblk(nnz), 256, 0, h->stream, (float2*)h->d_sval_z32, (const double2*)h->d_sval_z, nnz);
     DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
-    cudaFree(d_disp);
     h->kpoint_nl = true;
   }
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
@@ -720,7 +723,6 @@ extern "C" dftfe_status dftfe_chfsi_pass_z(dftfe_ham h, double* X, int64_t ld, i
   DFTFE_REQUIRE(std::isnan(inout->a0) || inout->a0 < inout->a, "need a0 < a for the scaled filter");
   DFTFE_REQUIRE(valid_prec(prec), "unknown precision");
   require_kpoint(h);
-  auto* m = h->mesh;
   const bool mixed = prec != DFTFE_FP64;
   {
     ProfScope ps(h, "pass_filter");
