@@ -72,3 +72,31 @@ def test_workload_recipes():
     site = (np.arange(4) + 0.5) * 7.5
     assert np.all(np.abs(w1.centres[:4, 0] - site) <= 0.5)
     assert np.all((w1.couplings >= 0.5) & (w1.couplings <= 2.0))
+
+
+def test_projector_disp_matches_the_csr_entries():
+    """Each displacement reproduces its CSR entry's projector value (same order, minimum
+    image, per-axis box lengths)."""
+    import math
+    L = np.array([6.0, 7.0, 8.0])
+    s = synth.Stream(4)
+    pts = np.array([[L[d] * s.uniform() for d in range(3)] for _ in range(400)])
+    cent = np.array([[0.2, 6.8, 4.0], [5.9, 0.1, 7.9]])
+    w, rc = 1.0, 2.5
+    rowptr, node, chi = synth.projector_csr(pts, cent, w, rc, L)
+    disp = synth.projector_disp(pts, cent, rc, L)
+    assert disp.shape == (node.size, 3)
+    n_s = (math.pi * w * w) ** 0.75
+    n_p = math.sqrt(0.5 * (math.pi * w * w) ** 1.5)
+    for a in range(len(cent)):
+        for j in range(4):
+            e0, e1 = rowptr[4 * a + j], rowptr[4 * a + j + 1]
+            d = disp[e0:e1]
+            # the displacement is the minimum image of node - centre
+            raw = pts[node[e0:e1]] - cent[a]
+            assert np.allclose(d, raw - L * np.round(raw / L))
+            r2 = np.einsum("ij,ij->i", d, d)
+            assert np.all(r2 < rc * rc)
+            g = np.exp(-r2 / (2 * w * w))
+            ref = g / n_s if j == 0 else (d[:, j - 1] / w) * g / n_p
+            assert np.allclose(chi[e0:e1], ref, rtol=1e-14, atol=1e-300)
