@@ -92,3 +92,32 @@ def test_density_without_mass_scaling_is_caught():
         Po, Pf = H.Nq @ X[rows], H.Nq @ Xfr[rows]                 # missing M^-1/2
         bad[c] = 2.0 * (np.sum(Po * Po, axis=1) + (Pf * Pf) @ (f - 1.0))
     assert abs(np.sum(bad * (H.Wq * m.detJ)[None, :]) - ne) > 1e-2
+
+
+# ---------------------------------------------------------------- Bloch k-points
+def _kpoint_kron(L, n, p, k, m):
+    from test_oracle_kpoint import one_d_bloch
+    A = [one_d_bloch(L[d], n[d], p, k[d]) for d in range(3)]
+    I = [np.eye(m.g[d]) for d in range(3)]
+    return (np.kron(I[2], np.kron(I[1], A[0])) + np.kron(I[2], np.kron(A[1], I[0]))
+            + np.kron(A[2], np.kron(I[1], I[0])))
+
+
+def test_k_terms_mistakes_are_caught_by_the_kronecker_pin():
+    """Dropping 1/2|k|^2, flipping the sign of the -i k.grad term (i.e. using +i) without
+    flipping k elsewhere, or permuting k's components all move H~^k off the Kronecker sum of
+    1D Bloch operators; the correct oracle is on it."""
+    from oracle import kpoint
+    L, n, p, k = (4.0, 5.0, 6.0), (2, 3, 2), 2, (0.3, -0.7, 0.2)
+    m = oracle.PeriodicMesh(L, n, p)
+    ref = _kpoint_kron(L, n, p, k, m)
+    B = kpoint.BlochHamiltonian(oracle.Hamiltonian(m), k)
+    assert np.abs(B.dense() - ref).max() < 1e-12 * np.abs(ref).max()
+    Bk = B.Bk.copy()
+    # Bk = -i k.G + 1/2|k|^2 M^c: its real part is the (diagonal) mass term
+    assert np.abs(Bk.real - np.diag(Bk.real.diagonal())).max() == 0.0
+    for name, bad in (("no 1/2|k|^2", Bk - np.diag(Bk.real.diagonal())),
+                      ("+i k.grad", np.conj(Bk)),
+                      ("permuted k", kpoint.BlochHamiltonian(oracle.Hamiltonian(m), (k[1], k[0], k[2])).Bk)):
+        B.Bk = bad
+        assert np.abs(B.dense() - ref).max() > 1e-3 * np.abs(ref).max(), name
