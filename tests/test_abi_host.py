@@ -116,3 +116,36 @@ def test_kpoint_stencil_table_matches_1d_assembly(dg, L, n, p, k):
                 for o in range(-p, p + 1):
                     row[(i + o) % g] += tab[d, a, o + p]
                 assert np.abs(row - G[i]).max() <= 1e-13 * max(1.0, np.abs(G).max()), (d, c, a)
+
+
+def test_null_arguments_rejected_by_the_kpoint_graph_and_tuning_calls(dg):
+    """The k-point, graph, autotuner and batch-graph entry points check their handles and
+    arguments on the host (no GPU needed for the refusals)."""
+    import ctypes as C
+    lib = dg.lib()
+    k = (C.c_double * 3)(0.1, 0.2, 0.3)
+    assert lib.dftfe_ham_set_kpoint(None, k, None) == 1
+    assert lib.dftfe_ham_apply_z(None, None, 0, None, 0, 0, 0) == 1
+    assert lib.dftfe_lanczos_z(None, 20, None, 0, None) == 1
+    assert lib.dftfe_spectrum_bounds_z(None, 20, 0, 4, None) == 1
+    assert lib.dftfe_chebyshev_filter_z(None, None, 0, 0, 0, None, 0) == 1
+    assert lib.dftfe_cholgs_z(None, None, 0, 0, 0) == 1
+    assert lib.dftfe_rayleigh_ritz_z(None, None, 0, 0, None, None, 0, 0) == 1
+    assert lib.dftfe_residuals_z(None, None, None, 0, 0, None, None, 0) == 1
+    assert lib.dftfe_chfsi_pass_z(None, None, 0, 0, 0, 0, None, None, None, 0) == 1
+    assert lib.dftfe_ham_use_graphs(None, 1) == 1
+    assert lib.dftfe_graph_query(None, None, None) == 1
+    assert lib.dftfe_ham_autotune(None, 1) == 1
+    assert lib.dftfe_autotune_query(None, 8, None, None, None) == 1
+    assert lib.dftfe_batch_use_graphs(None, 1) == 1
+    assert lib.dftfe_batch_graph_query(None, None, None) == 1
+    mesh = dg.dftfe_mesh_create(6.0, 2, 3)
+    try:
+        assert lib.dftfe_mesh_kpoint_stencil(mesh, None, None) == 1
+        bad = np.array([0.1, np.nan, 0.0])
+        out = np.zeros(3 * 3 * 7)
+        assert lib.dftfe_mesh_kpoint_stencil(mesh, bad.ctypes.data_as(C.c_void_p),
+                                             out.ctypes.data_as(C.c_void_p)) == 1
+        assert np.all(out == 0.0)                       # outputs untouched on DFTFE_ERR_ARG
+    finally:
+        dg.dftfe_mesh_destroy(mesh)
