@@ -8,6 +8,27 @@ are numpy.  A non-zero status raises DftfeError with the library's message.
 
 The library must have been built (``__graft_entry__.build()`` or
 ``python -m paper_2203_07820_gb300._build``); importing without it raises.
+
+One pass at the Gamma point (FP64 or a split precision)::
+
+    mesh = dftfe_mesh_create(L, ncell, degree)
+    ham = dftfe_ham_create(mesh)
+    dftfe_ham_set_potential(ham, v_quad)                # CUDA float64, ncells x quad_per_cell
+    dftfe_ham_set_nonlocal(ham, h, rowptr, node, chi)   # optional projectors (host CSR)
+    X = torch.empty((M, N), dtype=torch.float64, device="cuda"); dftfe_random_uniform(X, seed)
+    b = dftfe_spectrum_bounds(ham, 20, seed, N)
+    dftfe_chfsi_pass(ham, X, block, degree, b, evals, resid, DFTFE_MIXED_TF32X3)
+
+At a Bloch k-point the block is complex128 and the calls end in ``_z``::
+
+    dftfe_ham_set_kpoint(ham, k, disp)                  # disp: projector displacements
+    Z = torch.empty((M, N), dtype=torch.complex128, device="cuda")
+    dftfe_chfsi_pass_z(ham, Z, block, degree, dftfe_spectrum_bounds_z(ham, 20, seed, N), evals, resid)
+
+Many systems (each its own ham, Gamma or k-point items) in one batched pass::
+
+    batch = dftfe_batch_create(hams)
+    dftfe_batch_chfsi_pass(batch, blocks_X, blocks, degrees, bounds, evals, resids)
 """
 import ctypes as C
 import math
