@@ -243,3 +243,35 @@ def test_complex_generalised_residual_reduces_to_the_real_one():
     lam, V = np.linalg.eigh(B.dense())
     r, g = kpoint.residuals(V[:, :4], B.apply(V[:, :4]), lam[:4], m.mass)
     assert r.max() < 1e-11 and g.max() < 1e-11
+
+
+def test_realification_identities_used_by_the_complex_cholgs_and_rr():
+    """The library runs complex CholGS / Rayleigh-Ritz on real views (M x 2N, real and imaginary
+    parts interleaved).  Checked here in numpy: the complex Gram is read off the real Gram
+    G = Xr^T Xr; the interleaved real form rho(S) of S = X^H X has the real Cholesky factor
+    rho(L) (L the complex one); the real solve with rho(L) gives the real view of X L^-H; and
+    right multiplication by rho(Q) gives the real view of X Q."""
+    X = synth.random_block(3, 200, 2 * 7).view(np.complex128)
+    N = X.shape[1]
+    Xr = X.view(np.float64)
+    G = Xr.T @ Xr
+
+    def rho(A):
+        R = np.zeros((2 * A.shape[0], 2 * A.shape[1]))
+        R[0::2, 0::2] = A.real
+        R[1::2, 1::2] = A.real
+        R[0::2, 1::2] = A.imag
+        R[1::2, 0::2] = -A.imag
+        return R
+    S = X.conj().T @ X
+    Sg = (G[0::2, 0::2] + G[1::2, 1::2]) + 1j * (G[0::2, 1::2] - G[1::2, 0::2])
+    assert np.allclose(Sg, S, atol=1e-12)
+    L = np.linalg.cholesky(S)
+    Lr = np.linalg.cholesky(rho(S))
+    assert np.allclose(Lr, rho(L), atol=1e-12)
+    Xo, _, _ = kpoint.cholgs(X)
+    Xo_real = Xr @ np.linalg.inv(Lr).T
+    assert np.allclose(Xo_real, np.ascontiguousarray(Xo).view(np.float64), atol=1e-12)
+    Q = np.linalg.qr(synth.random_block(4, N, 2 * N).view(np.complex128))[0]
+    assert np.allclose(Xr @ rho(Q), np.ascontiguousarray(X @ Q).view(np.float64), atol=1e-12)
+    assert np.allclose(rho(Q.conj().T), rho(Q).T) and np.allclose(rho(L @ Q), rho(L) @ rho(Q))
