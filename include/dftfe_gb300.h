@@ -8,7 +8,8 @@
  * Lagrange elements on Gauss-Lobatto-Legendre (GLL) nodes (Eq. fem), lumped
  * diagonal M by GLL quadrature, is solved in the Loewdin form
  * H~ = M^-1/2 H M^-1/2 (Eq. hep).  H = H^loc + H^nl at the Gamma point
- * (Eq. discreteHam without the GGA and k terms; Eq. nonlocalHamDiscrete).
+ * (Eq. discreteHam without the GGA term; Eq. nonlocalHamDiscrete), and at a Bloch
+ * k-point on complex blocks through the _z calls (Sec. 2.1, the reduced equation).
  * The pass (Sec. 3.1-3.2): Chebyshev filter (Eq. chebyfilter), then
  * Cholesky-Gram-Schmidt and Rayleigh-Ritz (the orthonormalise-first reading of
  * Alg. 2), then residuals.
