@@ -88,7 +88,9 @@ def test_hermitian_with_projectors():
 
 
 @pytest.mark.parametrize("p,n,L,k", [(2, (2, 3, 2), (4.0, 5.0, 6.0), (0.3, -0.7, 0.2)),
-                                     (4, (3, 2, 2), (6.0, 6.5, 7.0), (0.5, 0.1, -0.35))])
+                                     (4, (3, 2, 2), (6.0, 6.5, 7.0), (0.5, 0.1, -0.35)),
+                                     (1, (3, 2, 4), (3.0, 4.0, 5.0), (0.9, -0.2, 0.4)),
+                                     (8, (2, 2, 2), (5.0, 5.5, 6.0), (-0.3, 0.6, 0.15))])
 def test_free_electron_is_kronecker_sum_of_1d_bloch_operators(p, n, L, k):
     """V = 0: H~^k = A_z (x) I (x) I + I (x) A_y (x) I + I (x) I (x) A_x (x fastest), each A_d the
     1D operator above; a transposed component, a wrong sign of i or a missing 1/2|k|^2 fails."""
