@@ -98,7 +98,9 @@ def _g1_tilde(L, n, p):
 
 @pytest.mark.parametrize("L,n,p,k", [((6.0, 7.0, 8.0), (3, 4, 5), 4, (0.3, -0.7, 1.1)),
                                      ((5.0, 5.0, 9.0), (3, 3, 3), 6, (0.25, 0.0, -0.4)),
-                                     ((4.0, 6.0, 5.0), (2, 2, 3), 3, (0.5, 0.2, 0.1))])
+                                     ((4.0, 6.0, 5.0), (2, 2, 3), 3, (0.5, 0.2, 0.1)),
+                                     ((3.0, 4.0, 5.0), (2, 3, 4), 1, (0.7, -0.1, 0.3)),
+                                     ((6.0, 6.0, 7.0), (2, 3, 2), 8, (0.2, 0.4, -0.6))])
 def test_kpoint_stencil_table_matches_1d_assembly(dg, L, n, p, k):
     """The library's k.grad stencil (host table, no GPU) against the 1D periodic operator
     assembled here: every entry k_d G~1_d(i, i + o), summed where two offsets reach the same
