@@ -470,6 +470,16 @@ dftfe_status dftfe_profile_enable(dftfe_ham ham, int enable);
 dftfe_status dftfe_profile_query(dftfe_ham ham, const char* kernel, double* total_ms,
                                  int64_t* launches);
 
+/* Test hook for the bounded device waits (no counterpart in the paper).  The dense subspace
+ * eigensolver (Rayleigh-Ritz, a cooperative launch whose CTAs meet at a grid barrier after
+ * every Jacobi round) gives up a wait after a spin limit of about a second, records
+ * DFTFE_ERR_TIMEOUT, lets every CTA return and leaves the context usable; the calling entry
+ * point then returns DFTFE_ERR_TIMEOUT with X unchanged.  spin_limit > 0 replaces that limit
+ * (iterations of a ~64 ns sleep; 0 restores the default) and withhold_arrival = 1 makes the
+ * barrier expect one arrival more than the grid holds, so the first wait runs out for certain
+ * (0 restores normal operation).  Both stay in force for later calls on this handle. */
+dftfe_status dftfe_ham_set_wait_test(dftfe_ham ham, int64_t spin_limit, int withhold_arrival);
+
 /* Number of kernels this library has launched in this process (all handles). */
 int64_t dftfe_launch_count(void);
 

@@ -118,6 +118,7 @@ _SIGS = {
     "dftfe_rayleigh_ritz_z": [_vp, _vp, _i64, _int, _vp, _vp, _i64, _int],
     "dftfe_residuals_z": [_vp, _vp, _vp, _i64, _int, _vp, _vp, _int],
     "dftfe_chfsi_pass_z": [_vp, _vp, _i64, _int, _int, _int, C.POINTER(Bounds), _vp, _vp, _int],
+    "dftfe_ham_set_wait_test": [_vp, _i64, _int],
     "dftfe_profile_enable": [_vp, _int],
     "dftfe_profile_query": [_vp, C.c_char_p, C.POINTER(_dbl), C.POINTER(_i64)],
 }
@@ -503,6 +504,12 @@ def dftfe_cholgs_noalloc(X, stream=None):
 
 
 # -------------------------------------------------------- instrumentation
+def dftfe_ham_set_wait_test(ham, spin_limit=0, withhold_arrival=False):
+    """Test hook: spin limit of the eigensolver's bounded grid-barrier waits (0 = default)
+    and one arrival withheld so that the next wait runs out (False = normal operation)."""
+    _check(_lib.dftfe_ham_set_wait_test(ham, int(spin_limit), 1 if withhold_arrival else 0))
+
+
 def dftfe_profile_enable(ham, enable=True):
     _check(_lib.dftfe_profile_enable(ham, 1 if enable else 0))
 

@@ -28,10 +28,10 @@ static void cholgs_impl(dftfe_ham h, double* X, int64_t ld, int ncol, bool mixed
     double* part = (double*)ws_get(h, "gram_part", sizeof(double) * (size_t)nsplit * N * N);
     gram_lower(h, X, ld, X, ld, m->M, N, S, part, nsplit);
   }
-  potrf(h->stream, S, N, st);
+  cholesky_blocked(h, S, N, st);
   const int s = read_status(h, st);
   if (s == DFTFE_ERR_NOT_SPD) throw Error(DFTFE_ERR_NOT_SPD, "overlap matrix is not positive definite");
-  trtri_lower_to_upper_t(h->stream, S, Z, N);
+  tri_inverse_blocked(h, S, Z, N);
   if (mixed) rotate_inplace_mixed(h, X, ld, m->M, N, Z, true);
   else rotate_inplace(h, X, ld, m->M, N, Z, true);
 }
@@ -206,6 +206,15 @@ extern "C" dftfe_status dftfe_chfsi_pass(dftfe_ham h, double* X, int64_t ld, int
     }
   }
   chfsi_pass_tail(h, X, ld, ncol, inout, evals, resid, prec);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_ham_set_wait_test(dftfe_ham h, int64_t spin_limit, int withhold_arrival) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h, "null ham");
+  DFTFE_REQUIRE(spin_limit >= 0 && (withhold_arrival == 0 || withhold_arrival == 1), "bad wait-test arguments");
+  h->wait_limit = (long long)spin_limit;
+  h->wait_missing = withhold_arrival;
   ABI_END
 }
 

@@ -283,7 +283,19 @@ struct Barrier {
   unsigned int gen;
   int abort;
   unsigned int reads;   // CTAs that have read the rotation inputs, summed over rounds
+  long long limit;      // spin iterations before a wait gives up
+  unsigned int missing; // arrivals the barrier expects beyond the grid (0; 1 only in the wait test)
 };
+
+// every call starts from a cleared barrier with its spin limit and expected arrivals
+__global__ void k_bar_init(Barrier* b, long long limit, unsigned int missing) {
+  b->count = 0;
+  b->gen = 0;
+  b->abort = 0;
+  b->reads = 0;
+  b->limit = limit > 0 ? limit : (long long)kBarrierSpins;
+  b->missing = missing;
+}
 
 // split barrier: the rotation inputs of a round (A_pp, A_qq, A_pq of every pair) may be
 // overwritten only once every CTA has read them
@@ -301,9 +313,10 @@ __device__ bool wait_reads(Barrier* b, unsigned int target, int* status) {
     ok = 1;
     volatile unsigned int* vr = &b->reads;
     volatile int* vabort = &b->abort;
-    long it = 0;
+    const long long lim = b->limit;
+    long long it = 0;
     while (*vr < target) {
-      if (*vabort || ++it > kBarrierSpins) {
+      if (*vabort || ++it > lim) {
         ok = 0;
         atomicExch(&b->abort, 1);
         atomicCAS(status, 0, (int)DFTFE_ERR_TIMEOUT);
@@ -327,15 +340,16 @@ __device__ bool grid_barrier(Barrier* b, int* status) {
     volatile unsigned int* vgen = &b->gen;
     volatile int* vabort = &b->abort;
     const unsigned int g = *vgen;
+    const long long lim = b->limit;
     __threadfence();
-    if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(&b->count, 1u) == gridDim.x - 1 + b->missing) {
       atomicExch(&b->count, 0u);
       __threadfence();
       atomicAdd(&b->gen, 1u);
     } else {
-      long it = 0;
+      long long it = 0;
       while (*vgen == g) {
-        if (*vabort || ++it > kBarrierSpins) {
+        if (*vabort || ++it > lim) {
           ok = 0;
           atomicExch(&b->abort, 1);
           atomicCAS(status, 0, (int)DFTFE_ERR_TIMEOUT);
@@ -757,12 +771,19 @@ void tridiag_ql(cudaStream_t s, double* d, double* e, double* Z, int N, int* d_s
 
 // ascending order (ties by index) and the sign convention: the largest-|.| entry of each
 // eigenvector (first one on ties) is made positive.
+// ascending order by a strict total order (NaN after every number, ties by index), so perm
+// is a permutation whatever d holds (an eigensolver that gave up leaves d unspecified)
 __global__ void k_rank(const double* d, int N, int* perm, double* evals) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double di = d[i];
+  const bool ni = isnan(di);
   int r = 0;
-  for (int j = 0; j < N; ++j) r += (d[j] < di) || (d[j] == di && j < i);
+  for (int j = 0; j < N; ++j) {
+    const double dj = d[j];
+    const bool nj = isnan(dj);
+    r += ni ? (!nj || j < i) : (!nj && (dj < di || (dj == di && j < i)));
+  }
   perm[r] = i;
   evals[r] = di;
 }
@@ -773,7 +794,8 @@ __global__ void __launch_bounds__(256) k_sign_copy(const double* __restrict__ Z,
   __shared__ double bv[256];
   __shared__ int bi[256];
   const int c = blockIdx.x;
-  const int src = perm[c];
+  int src = perm[c];
+  if (src < 0 || src >= N) src = c;               // defensive: perm comes from k_rank
   double best = -1.0;
   int bidx = N;
   for (int r = threadIdx.x; r < N; r += 256) {
@@ -821,7 +843,7 @@ void syevd(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_statu
   // enough CTAs for the widest round, never more than can be co-resident
   const int want = (int)std::min<int64_t>(h->sm_count, ((int64_t)NP * N + 255) / 256);
   int grid = std::max(1, want);
-  DFTFE_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(jac::Barrier), s));
+  DFTFE_LAUNCH(jac::k_bar_init, 1, 1, 0, s, bar, h->wait_limit, (unsigned int)h->wait_missing);
   DFTFE_CHECK_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
   DFTFE_LAUNCH(k_fro_norm, 1, 256, 0, s, A, N, anorm);
   int maxs = 60;
@@ -839,7 +861,8 @@ __global__ void __launch_bounds__(256) k_phase_copy_z(const double2* __restrict_
   __shared__ double bv[256];
   __shared__ int bi[256];
   const int c = blockIdx.x;
-  const int src = perm[c];
+  int src = perm[c];
+  if (src < 0 || src >= N) src = c;               // defensive: perm comes from k_rank
   double best = -1.0;
   int bidx = N;
   for (int r = threadIdx.x; r < N; r += 256) {
@@ -891,7 +914,7 @@ void syevd_z(dftfe_ham h, double* Ad, int N, double* evals, double* Qd, int* d_s
   if (per_sm < 1) throw Error(DFTFE_ERR_CUDA, "dense eigensolver: kernel does not fit on an SM");
   const int want = (int)std::min<int64_t>(h->sm_count, ((int64_t)NP * N + 255) / 256);
   int grid = std::max(1, want);
-  DFTFE_CHECK_CUDA(cudaMemsetAsync(bar, 0, sizeof(jac::Barrier), s));
+  DFTFE_LAUNCH(jac::k_bar_init, 1, 1, 0, s, bar, h->wait_limit, (unsigned int)h->wait_missing);
   DFTFE_CHECK_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), s));
   DFTFE_LAUNCH(k_fro_norm_z, 1, 256, 0, s, A, N, anorm);
   int maxs = 60;

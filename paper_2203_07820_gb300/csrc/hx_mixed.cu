@@ -343,6 +343,305 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
 }
 
+// ------------------------------------------------------------ TF32x3 from one FP32 plane
+// The TF32x3 form streams the cell matrices as ONE FP32 plane (4 bytes per entry, rounded to
+// nearest from FP64) and splits every tile into its hi and lo TF32 terms in shared memory:
+//   plane layout: per (cell, K-chunk of 32 columns) the M-tiles of 128 rows in order, each a
+//   K-major 128-byte-swizzled tile of 128 x 32 floats; the last M-tile holds only its rows in
+//   8-row atoms (88 of 128 for p = 6), so a cell streams (nmt - 1) x 16 KB + rows8 x 128 B per
+//   K-chunk -- the nc x nc matrix plus the K padding, nothing else.
+// Warp roles (448 threads):
+//   warp 0        A producer: one bulk copy per tile into the landing slot (3-stage ring)
+//   warp 1        TMEM owner and MMA issuer (one elected lane)
+//   warps 2-5     B producers: cp.async gather of the cell's rows of X (each warp 32 columns,
+//                 into its own 4 KB slice of the stage's lo slot, two chunks ahead), then the
+//                 split of the chunk into the swizzled hi and lo B tiles (3-stage ring)
+//   warps 6-9     epilogue (tcgen05.ld of the accumulators, stores of the rows of Y^c)
+//   warps 10-13   A converters: hi = rn_tf32(f) in place, lo = rn_tf32(f - hi) beside it
+// Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its own
+// copies and MMAs (bounded), frees its tensor memory and returns.
+namespace mp {
+constexpr int kThreads = 448;
+constexpr int kStagesA = 3, kStagesB = 3;
+constexpr int kTile = 16384;
+constexpr int kStage = 2 * kTile;                  // hi (landing) | lo
+constexpr int kMaxMTiles = 4;
+struct Shared {
+  uint64_t a_full[kStagesA], a_conv[kStagesA], a_empty[kStagesA];
+  uint64_t b_full[kStagesB], b_empty[kStagesB];
+  uint64_t acc_full, acc_empty[kMaxMTiles], drain;
+  uint32_t tmem;
+  int abort;
+};
+constexpr size_t smem_bytes() {
+  return 1024 + (size_t)kStagesA * kStage + (size_t)kStagesB * kStage + mx::kPatchBytes + sizeof(Shared);
+}
+__host__ __device__ inline int64_t kc_block_bytes(int nmt, int rows8) {
+  return (int64_t)(nmt - 1) * kTile + (int64_t)rows8 * 128;
+}
+}  // namespace mp
+
+// Set-up: the FP32 plane in the tile order above (written in physical order, so the stores
+// are coalesced; each physical position is mapped back through the swizzle).
+__global__ void k_plane_cells(const double* __restrict__ Hc, float* __restrict__ A, int64_t Nc, int nc, int nkc,
+                              int nmt, int rows8) {
+  const int64_t per_kc = mp::kc_block_bytes(nmt, rows8) / 4;      // floats per (cell, K-chunk)
+  const int64_t total = Nc * nkc * per_kc;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blk = t / per_kc;
+    const int w = (int)(t - blk * per_kc);
+    const int64_t cell = blk / nkc;
+    const int kc = (int)(blk - cell * nkc);
+    const int mt = w >> 12;                                        // 4096 floats per tile
+    const uint32_t p = (uint32_t)(w & 4095) * 4u;                  // physical byte in the tile
+    const uint32_t r = p >> 7;
+    const uint32_t lchunk = ((p >> 4) & 7u) ^ (r & 7u);
+    const int e = (int)(lchunk * 4u + ((p & 15u) >> 2));
+    const int m = mt * 128 + (int)r, k = kc * 32 + e;
+    A[t] = (m < nc && k < nc) ? __double2float_rn(Hc[(cell * nc + m) * (int64_t)nc + k]) : 0.0f;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
+    const uint8_t* __restrict__ A, const int32_t* __restrict__ map, int ncells, int nc, int nkc, int nmt,
+    const float* __restrict__ X, int64_t ldx, float* __restrict__ Yc, int col0, int ncol, int* err) {
+  using namespace mp;
+  using tc::mbar_arrive;
+  using tc::mbar_init;
+  using tc::mbar_wait;
+  using tc::sdesc;
+  using tc::smem_u32;
+  using tc::sw128;
+  using tc::tc_commit;
+  auto cell_of = [&](int64_t i) -> int64_t { return blockIdx.x + i * gridDim.x; };
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = sA + kStagesA * kStage;
+  uint8_t* sP = sB + kStagesB * kStage;
+  Shared* sh = (Shared*)(sP + mx::kPatchBytes);
+  volatile int* abort = &sh->abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStagesA; ++s) {
+      mbar_init(&sh->a_full[s], 1);
+      mbar_init(&sh->a_conv[s], 128);
+      mbar_init(&sh->a_empty[s], 1);
+    }
+    for (int s = 0; s < kStagesB; ++s) { mbar_init(&sh->b_full[s], 128); mbar_init(&sh->b_empty[s], 1); }
+    mbar_init(&sh->acc_full, 1);
+    for (int t = 0; t < kMaxMTiles; ++t) mbar_init(&sh->acc_empty[t], 128);
+    mbar_init(&sh->drain, 1);
+    sh->abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(smem_u32(&sh->tmem)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh->tmem;
+  const int my_cells = ncells > (int)blockIdx.x ? (ncells - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int rows8 = ((nc - 128 * (nmt - 1)) + 7) / 8 * 8;   // rows of the last M-tile, in atoms
+  const int64_t kcb = kc_block_bytes(nmt, rows8);
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ A producer
+    if (lane == 0) {
+      uint32_t ta = 0;
+      bool go = true;
+      for (int i = 0; i < my_cells && go; ++i) {
+        const int64_t cell = cell_of(i);
+        for (int kc = 0; kc < nkc && go; ++kc)
+          for (int mt = 0; mt < nmt; ++mt, ++ta) {
+            const int s = ta % kStagesA;
+            if (!mbar_wait(&sh->a_empty[s], ((ta / kStagesA) & 1) ^ 1, abort, err)) { go = false; break; }
+            const uint32_t full = smem_u32(&sh->a_full[s]);
+            const uint32_t bytes = mt == nmt - 1 ? (uint32_t)rows8 * 128u : (uint32_t)kTile;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(bytes) : "memory");
+            const uint8_t* src = A + (cell * nkc + kc) * kcb + (int64_t)mt * kTile;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_u32(sA + s * kStage)), "l"(src), "r"(bytes), "r"(full) : "memory");
+          }
+      }
+      // drain: every issued copy has landed before the CTA may exit
+      for (uint32_t t = (ta > (uint32_t)kStagesA ? ta - kStagesA : 0); t < ta; ++t) {
+        volatile int no_abort = 0;
+        mbar_wait(&sh->a_full[t % kStagesA], (t / kStagesA) & 1, &no_abort, err);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t ta = 0, tb = 0;
+      bool go = true;
+      for (int i = 0; i < my_cells && go; ++i) {
+        for (int kc = 0; kc < nkc && go; ++kc, ++tb) {
+          const int sb = tb % kStagesB;
+          if (!mbar_wait(&sh->b_full[sb], (tb / kStagesB) & 1, abort, err)) { go = false; break; }
+          const uint32_t bhi = smem_u32(sB + sb * kStage), blo = bhi + kTile;
+          for (int mt = 0; mt < nmt; ++mt, ++ta) {
+            const int sa = ta % kStagesA;
+            if (kc == 0 && !mbar_wait(&sh->acc_empty[mt], (i & 1) ^ 1, abort, err)) { go = false; break; }
+            if (!mbar_wait(&sh->a_conv[sa], (ta / kStagesA) & 1, abort, err)) { go = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ahi = smem_u32(sA + sa * kStage), alo = ahi + kTile;
+            const uint32_t d = tmem + (uint32_t)(mt * 128);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint32_t o = ks * 32;
+              mx::mma<true>(d, sdesc(ahi + o), sdesc(bhi + o), (kc > 0 || ks > 0) ? 1u : 0u);
+              mx::mma<true>(d, sdesc(ahi + o), sdesc(blo + o), 1u);
+              mx::mma<true>(d, sdesc(alo + o), sdesc(bhi + o), 1u);
+            }
+            tc_commit(&sh->a_empty[sa]);
+          }
+          if (go) tc_commit(&sh->b_empty[sb]);
+        }
+        if (go) tc_commit(&sh->acc_full);
+      }
+      // drain: all issued MMAs complete before tensor memory is released
+      tc_commit(&sh->drain);
+      volatile int no_abort = 0;
+      mbar_wait(&sh->drain, 0, &no_abort, err);
+    }
+  } else if (warp >= 2 && warp < 6) {
+    // ------------------------------------------------------------ B producers
+    // warp w gathers columns col0 + 32 w .. +31 of the chunk's 32 rows into its 4 KB slice of
+    // the stage's lo slot (row i of the chunk at byte 128 i), each lane copying 16 bytes of
+    // one row per instruction; the slice is exactly where the warp's 32 rows of the lo B
+    // tile go, so the split overwrites only what the warp itself staged
+    const int w = warp - 2;
+    const int n = 32 * w + lane;
+    const uint32_t nchunks = (uint32_t)my_cells * (uint32_t)nkc;
+    auto issue = [&](uint32_t t) -> bool {
+      const int sb = t % kStagesB;
+      if (!mbar_wait(&sh->b_empty[sb], ((t / kStagesB) & 1) ^ 1, abort, err)) return false;
+      const int64_t cell = cell_of(t / nkc);
+      const int kc = (int)(t % nkc);
+      const int32_t* cm = map + cell * nc;
+      const uint32_t dst = smem_u32(sB + sb * kStage + kTile + w * 4096);
+      const int seg = lane & 7;
+      const int c = col0 + 32 * w + 4 * seg;
+      const int cvalid = min(max(ncol - c, 0), 4) * 4;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int row = 4 * j + (lane >> 3);
+        const int k = kc * 32 + row;
+        const bool ok = k < nc && cvalid > 0;
+        const float* src = ok ? X + (int64_t)__ldg(cm + k) * ldx + c : X;
+        cp_async16(dst + row * 128 + seg * 16, src, ok ? (uint32_t)cvalid : 0u);
+      }
+      return true;
+    };
+    bool go = true;
+    for (uint32_t t = 0; t < 2; ++t) {
+      if (go && t < nchunks) go = issue(t);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (uint32_t tb = 0; tb < nchunks && go; ++tb) {
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      __syncwarp();
+      const int sb = tb % kStagesB;
+      uint8_t* bhi = sB + sb * kStage;
+      uint8_t* blo = bhi + kTile;
+      const float* raw = reinterpret_cast<const float*>(blo + w * 4096);
+      float v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = raw[k * 32 + lane];
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint4 hi, lo;
+        tc::split_tf32_bits(__float_as_uint(v[4 * q]), hi.x, lo.x);
+        tc::split_tf32_bits(__float_as_uint(v[4 * q + 1]), hi.y, lo.y);
+        tc::split_tf32_bits(__float_as_uint(v[4 * q + 2]), hi.z, lo.z);
+        tc::split_tf32_bits(__float_as_uint(v[4 * q + 3]), hi.w, lo.w);
+        const uint32_t off = sw128((uint32_t)n, (uint32_t)(q * 16));
+        *reinterpret_cast<uint4*>(bhi + off) = hi;
+        *reinterpret_cast<uint4*>(blo + off) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&sh->b_full[sb]);
+      if (tb + 2 < nchunks) go = issue(tb + 2);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (warp >= 6 && warp < 10) {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;                       // TMEM lane quadrant of this warp
+    float* patch = reinterpret_cast<float*>(sP) + q * (32 * mx::kPatchLd);
+    for (int i = 0; i < my_cells; ++i) {
+      if (!mbar_wait(&sh->acc_full, i & 1, abort, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t cell = cell_of(i);
+      for (int mt = 0; mt < nmt; ++mt) {
+        const int row0 = mt * 128 + q * 32;
+        for (int cb = 0; cb < 4; ++cb) {
+          uint32_t r[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128 + cb * 32), r);
+          if (row0 >= nc) continue;               // whole patch is padding (warp-uniform)
+#pragma unroll
+          for (int j = 0; j < 32; j += 4)
+            *reinterpret_cast<uint4*>(patch + lane * mx::kPatchLd + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+          __syncwarp();
+#pragma unroll
+          for (int it = 0; it < 8; ++it) {
+            const int rl = it * 4 + (lane >> 3);
+            const int row = row0 + rl;
+            const float4 val = *reinterpret_cast<const float4*>(patch + rl * mx::kPatchLd + 4 * (lane & 7));
+            if (row < nc)
+              *reinterpret_cast<float4*>(Yc + (cell * nc + row) * (int64_t)128 + cb * 32 + 4 * (lane & 7)) = val;
+          }
+          __syncwarp();
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&sh->acc_empty[mt]);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ A converters
+    const int tid = threadIdx.x - 320;            // 0 .. 127
+    uint32_t ta = 0;
+    bool go = true;
+    for (int i = 0; i < my_cells && go; ++i)
+      for (int kc = 0; kc < nkc && go; ++kc)
+        for (int mt = 0; mt < nmt; ++mt, ++ta) {
+          const int s = ta % kStagesA;
+          if (!mbar_wait(&sh->a_full[s], (ta / kStagesA) & 1, abort, err)) { go = false; break; }
+          const int nchunk16 = (mt == nmt - 1 ? rows8 : 128) * 8;
+          uint4* hi = reinterpret_cast<uint4*>(sA + s * kStage);
+          uint4* lo = reinterpret_cast<uint4*>(sA + s * kStage + kTile);
+          for (int c = tid; c < nchunk16; c += 128) {
+            const uint4 u = hi[c];
+            uint4 h4, l4;
+            tc::split_tf32_bits(u.x, h4.x, l4.x);
+            tc::split_tf32_bits(u.y, h4.y, l4.y);
+            tc::split_tf32_bits(u.z, h4.z, l4.z);
+            tc::split_tf32_bits(u.w, h4.w, l4.w);
+            hi[c] = h4;
+            lo[c] = l4;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(&sh->a_conv[s]);
+        }
+  }
+  __syncwarp();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
 // ------------------------------------------------------------ FP32 helpers
 
 __global__ void k_to_f32(const double* __restrict__ X, int64_t ldx, float* __restrict__ Y, int64_t ldy,
@@ -430,7 +729,19 @@ static uint8_t* mixed_tiles(dftfe_ham h, bool tf32, int* nkc_out, int* nmt_out) 
   *nmt_out = nmt;
   if (nmt > mx::kMaxMTiles) throw Error(DFTFE_ERR_ARG, "mixed precision supports at most 512 nodes per cell (p <= 7)");
   const int fmt = tf32 ? 1 : 0;
-  const char* name = tf32 ? "mixed_tiles_tf32" : "mixed_tiles_bf16";
+  if (tf32) {
+    // TF32x3: one FP32 plane, split in shared memory by the kernel
+    const int rows8 = ((m->nc - 128 * (nmt - 1)) + 7) / 8 * 8;
+    const size_t bytes = (size_t)m->Nc * nkc * (size_t)mp::kc_block_bytes(nmt, rows8);
+    uint8_t* A = (uint8_t*)ws_get(h, "mixed_plane_tf32", bytes);
+    if (h->mixed_version[fmt] != h->potential_version) {
+      DFTFE_LAUNCH(k_plane_cells, h->sm_count * 16, 256, 0, h->stream, h->d_Hc, (float*)A, m->Nc, m->nc, nkc, nmt,
+                   rows8);
+      h->mixed_version[fmt] = h->potential_version;
+    }
+    return A;
+  }
+  const char* name = "mixed_tiles_bf16";
   const size_t bytes = (size_t)m->Nc * nkc * nmt * 2 * mx::kTile;
   uint8_t* A = (uint8_t*)ws_get(h, name, bytes);
   if (h->mixed_version[fmt] != h->potential_version) {
@@ -553,7 +864,7 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
     {
       ProfScope ps(h, tf32 ? "cell_gemm_tf32x3" : "cell_gemm_bf16x3");
       if (tf32)
-        DFTFE_LAUNCH(k_cell_mixed<true>, grid, mx::kThreads, sh, h->stream, A, h->d_map, (int)m->Nc, m->nc,
+        DFTFE_LAUNCH(k_cell_tf32p, grid, mp::kThreads, mp::smem_bytes(), h->stream, A, h->d_map, (int)m->Nc, m->nc,
                      nkc, nmt, X, ldx, Yc, col0, ncol, err);
       else
         DFTFE_LAUNCH(k_cell_mixed<false>, grid, mx::kThreads, sh, h->stream, A, h->d_map, (int)m->Nc, m->nc,
@@ -575,7 +886,7 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
   if (degree <= 0 || ncol <= 0) return;
   auto* m = h->mesh;
   if (!g_mixed_attr) {
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp::smem_bytes()));
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
     g_mixed_attr = true;
   }
@@ -631,7 +942,7 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
 void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32, bool kpoint) {
   auto* m = h->mesh;
   if (!g_mixed_attr) {
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp::smem_bytes()));
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
     g_mixed_attr = true;
   }

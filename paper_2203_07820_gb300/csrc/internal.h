@@ -170,6 +170,11 @@ struct dftfe_ham_s {
   // autotuner (dftfe_ham_autotune): FP64 cell-kernel shape per real column count
   bool autotune = false;
   std::map<int, dftfe::TunedShape> tuned_fp64;
+  // bounded device waits (dftfe_ham_set_wait_test): spin limit of the eigensolver's grid
+  // barrier (0 = the built-in limit of about a second) and arrivals withheld from it (a test
+  // makes the wait run out with 1)
+  long long wait_limit = 0;
+  int wait_missing = 0;
   // workspace
   std::map<std::string, dftfe::DevBuf> ws;
   // profiling
@@ -241,6 +246,11 @@ void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int6
 int gram_nsplit(dftfe_ham h, int64_t M, int N);
 void potrf(cudaStream_t s, double* A, int N, int* d_status);
 void trtri_lower_to_upper_t(cudaStream_t s, const double* L, double* Z, int N);
+// chol.cu: blocked multi-CTA forms of the two above (the lower triangle of A is factored in
+// place, its strict upper triangle zeroed; d_status cleared, then DFTFE_ERR_NOT_SPD on a bad
+// pivot; Z = L^-T upper triangular)
+void cholesky_blocked(dftfe_ham h, double* A, int N, int* d_status);
+void tri_inverse_blocked(dftfe_ham h, double* L, double* Z, int N);
 void rotate_inplace(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z,
                     bool upper);
 void syevd(dftfe_ham h, double* A, int N, double* evals, double* Q, int* d_status);

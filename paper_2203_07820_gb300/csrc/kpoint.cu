@@ -497,10 +497,10 @@ static void cholgs_z(dftfe_ham h, double* X, int64_t ld, int ncol, bool mixed) {
   int* st = (int*)ws_get(h, "status", sizeof(int) * 4);
   real_view_gram(h, X, 2 * ld, X, 2 * ld, N2, S, mixed);
   DFTFE_LAUNCH(k_herm_expand, nblk((int64_t)ncol * ncol), 256, 0, h->stream, S, ncol);
-  potrf(h->stream, S, N2, st);
+  cholesky_blocked(h, S, N2, st);
   if (read_status_z(h, st) == DFTFE_ERR_NOT_SPD)
     throw Error(DFTFE_ERR_NOT_SPD, "overlap matrix is not positive definite");
-  trtri_lower_to_upper_t(h->stream, S, Z, N2);
+  tri_inverse_blocked(h, S, Z, N2);
   if (mixed) rotate_inplace_mixed(h, X, 2 * ld, m->M, N2, Z, true);
   else rotate_inplace(h, X, 2 * ld, m->M, N2, Z, true);
 }

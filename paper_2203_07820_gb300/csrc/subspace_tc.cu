@@ -117,8 +117,8 @@ __global__ void k_rot_tiles(const double* __restrict__ Z, int N, int upper, int 
 }
 
 __global__ void __launch_bounds__(st::kThreads, 1) k_rot_tc(const double* __restrict__ X, int64_t ld, int64_t M,
-                                                            int N, const uint8_t* __restrict__ Bt, int nkc, int nt,
-                                                            float* __restrict__ Yo, int64_t ldo, int* err) {
+                                                            int N, const uint8_t* __restrict__ Bt, int nkc_all, int nt,
+                                                            int upper, float* __restrict__ Yo, int64_t ldo, int* err) {
   using namespace st;
   using namespace tc;
   extern __shared__ uint8_t smem_raw[];
@@ -128,6 +128,9 @@ __global__ void __launch_bounds__(st::kThreads, 1) k_rot_tc(const double* __rest
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ct = (int)(blockIdx.x % nt);               // output column tile
   const int64_t m0 = (int64_t)(blockIdx.x / nt) * 128;
+  // an upper triangular Z (strict part) has no entries below row 128 ct + 127 in column
+  // tile ct: its chunks kc > 4 ct + 3 are zero and are skipped
+  const int nkc = upper ? min(nkc_all, 4 * ct + 4) : nkc_all;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -449,17 +452,25 @@ bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, con
   DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
   DFTFE_LAUNCH(k_rot_tiles, nblk_tc((int64_t)nkc * nt * 128 * 32), 256, 0, h->stream, Z, N, upper ? 1 : 0, nkc, nt,
                Bt, zd);
+  // the FP32 product X offdiag(Z) goes through a buffer of at most 2 GiB: row slabs of a
+  // multiple of 128 rows, each rotated and then given its FP64 diagonal part in place
   const int64_t ldo = (N + 3) / 4 * 4;
-  float* Yo = (float*)ws_get(h, "rot_tc_out", sizeof(float) * (size_t)M * ldo);
-  {
-    ProfScope ps(h, "rotate_tc");
-    DFTFE_LAUNCH(k_rot_tc, (unsigned)(((M + 127) / 128) * nt), st::kThreads, st::smem_bytes(), h->stream, X, ld, M, N,
-                 Bt, nkc, nt, Yo, ldo, err);
-  }
-  {
-    ProfScope ps(h, "rotate_diag");
-    DFTFE_LAUNCH(k_rot_diag, (unsigned)std::min<int64_t>((int64_t)h->sm_count * 16, nblk_tc(M * ((N + 1) / 2))), 256, 0,
-                 h->stream, X, ld, Yo, ldo, M, N, zd);
+  const int64_t cap_rows = std::max<int64_t>(128, ((int64_t)(2LL << 30) / (ldo * 4)) / 128 * 128);
+  const int64_t slab = std::min<int64_t>((M + 127) / 128 * 128, cap_rows);
+  float* Yo = (float*)ws_get(h, "rot_tc_out", sizeof(float) * (size_t)slab * ldo);
+  for (int64_t r0 = 0; r0 < M; r0 += slab) {
+    const int64_t ms = std::min<int64_t>(slab, M - r0);
+    double* Xs = X + r0 * ld;
+    {
+      ProfScope ps(h, "rotate_tc");
+      DFTFE_LAUNCH(k_rot_tc, (unsigned)(((ms + 127) / 128) * nt), st::kThreads, st::smem_bytes(), h->stream, Xs, ld, ms,
+                   N, Bt, nkc, nt, upper ? 1 : 0, Yo, ldo, err);
+    }
+    {
+      ProfScope ps(h, "rotate_diag");
+      DFTFE_LAUNCH(k_rot_diag, (unsigned)std::min<int64_t>((int64_t)h->sm_count * 16, nblk_tc(ms * ((N + 1) / 2))), 256,
+                   0, h->stream, Xs, ld, Yo, ldo, ms, N, zd);
+    }
   }
   int herr = 0;
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));

@@ -80,6 +80,18 @@ __device__ __forceinline__ uint32_t tf32_rn(float x) {
   return r;
 }
 
+// the same rounding (to 10 explicit mantissa bits, nearest, ties away from zero) on the bit
+// pattern with two integer operations: adding half of the dropped unit carries into the kept
+// bits exactly when the dropped part is at least half (and into the exponent on overflow);
+// identical to cvt.rna.tf32.f32 for every finite input
+__device__ __forceinline__ uint32_t tf32_rn_bits(uint32_t u) { return (u + 0x1000u) & 0xFFFFE000u; }
+
+// FP32 value -> TF32 hi + TF32 lo by integer rounding (f - hi is exact in FP32)
+__device__ __forceinline__ void split_tf32_bits(uint32_t u, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rn_bits(u);
+  lo = tf32_rn_bits(__float_as_uint(__uint_as_float(u) - __uint_as_float(hi)));
+}
+
 // FP64 value -> TF32 hi + TF32 lo (each rounded to nearest, ties away)
 __device__ __forceinline__ void split_tf32(double v, uint32_t& hi, uint32_t& lo) {
   const float f = __double2float_rn(v);

@@ -1,15 +1,18 @@
 """Batched passes over independent systems of uneven mesh size, degree, state count and block
 size: every system's result must be bit-identical to a pass of that system alone (same
-operations in the same order), over two consecutive passes; a timing comparison on sixteen
-small systems is printed."""
+operations in the same order), over two consecutive passes, and every item (Gamma point and
+k-point) must match two passes of the FP64 oracle; a timing comparison on sixteen small
+systems is printed."""
 import math
 import time
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from systems import gpu_system, small_case
+from oracle import kpoint
+from systems import gpu_system, oracle_system, small_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -275,3 +278,71 @@ def test_graphed_batched_pass_is_bit_identical(dg):
         for mesh, ham, *_ in made1 + made2:
             dg.dftfe_ham_destroy(ham)
             dg.dftfe_mesh_destroy(mesh)
+
+
+def _oracle_gamma(spec):
+    seed, n, p, L, nl, N, block, deg, scaled = spec
+    c = small_case(seed, n=n, p=p, L=L, nl=nl)
+    om, oh = oracle_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    tmin, _, b = oracle.lanczos_bounds(oh.apply, synth.counter_uniform(7 + seed, om.ndofs), 20)
+    bd = oracle.first_pass_bounds(tmin, b, N, om.ndofs)
+    if not scaled:
+        bd = oracle.Bounds(bd.a, bd.b)
+    return c, om, oh, synth.random_block(100 + seed, om.ndofs, N), bd
+
+
+def _oracle_kpoint(spec):
+    seed, n, p, L, N, block, deg, k = spec
+    c = small_case(seed, n=n, p=p, L=L, nl=True)
+    om, oh = oracle_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], None)
+    bh = kpoint.BlochHamiltonian(oh, k)
+    cent, w, rc, hc = c["proj"]
+    rp, nd, chi = synth.projector_csr(om.node_xyz(), cent, w, rc, c["L"])
+    bh.set_nonlocal(hc, rp, nd, chi, synth.projector_disp(om.node_xyz(), cent, rc, c["L"]))
+    tmin, _, b = kpoint.spectrum_bounds(bh, synth.counter_uniform(9 + seed, 2 * om.ndofs), 20)
+    bd = oracle.first_pass_bounds(tmin, b, N, om.ndofs)
+    Z0 = synth.random_block(300 + seed, om.ndofs, 2 * N).view(np.complex128)
+    return c, om, bh, Z0, bd
+
+
+def test_batched_passes_match_the_oracle(dg):
+    """Every item of a batch (five Gamma-point systems -- degree 0, blocks of 7 and 30, a
+    narrow-kernel tail -- and four k-point items, two of them k-points of one system) against
+    two passes of the FP64 oracles from the same seeded start and the oracle's own bounds:
+    Ritz values within 1e-9 Ha and the same bounds updates."""
+    items = []
+    for spec in SYSTEMS:
+        c, om, oh, X0, bd = _oracle_gamma(spec)
+        mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+        items.append(dict(mesh=mesh, ham=ham, X=torch.from_numpy(X0).cuda(), X0=X0, bd=bd, oracle=oh, cplx=False,
+                          block=spec[6], deg=spec[7]))
+    for spec in KSYSTEMS:
+        c, om, bh, Z0, bd = _oracle_kpoint(spec)
+        mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+        nxyz, _ = dg.dftfe_mesh_coords(mesh, quad=False)
+        cent, w, rc, hc = c["proj"]
+        dg.dftfe_ham_set_kpoint(ham, spec[7], synth.projector_disp(nxyz, cent, rc, c["L"]))
+        items.append(dict(mesh=mesh, ham=ham, X=torch.from_numpy(Z0.copy()).cuda(), X0=Z0, bd=bd, oracle=bh,
+                          cplx=True, block=spec[5], deg=spec[6]))
+    batch = dg.dftfe_batch_create([it["ham"] for it in items])
+    try:
+        gbs = [dg.make_bounds(it["bd"].a, it["bd"].b, it["bd"].a0) for it in items]
+        evs = [torch.empty(it["X"].shape[1], dtype=torch.float64, device="cuda") for it in items]
+        rss = [torch.empty_like(e) for e in evs]
+        Xo = [it["X0"] for it in items]
+        obs = [it["bd"] for it in items]
+        for _ in range(2):
+            dg.dftfe_batch_chfsi_pass(batch, [it["X"] for it in items], [it["block"] for it in items],
+                                      [it["deg"] for it in items], gbs, evs, rss)
+            torch.cuda.synchronize()
+            for i, it in enumerate(items):
+                run = kpoint.chfsi_pass if it["cplx"] else oracle.chfsi_pass
+                Xo[i], _, theta, _, obs[i] = run(it["oracle"], Xo[i], it["block"], it["deg"], obs[i])
+                assert np.abs(evs[i].cpu().numpy() - theta).max() < 1e-9, i
+                assert abs(gbs[i].a - obs[i].a) < 1e-9, i
+                assert (math.isnan(gbs[i].a0) and math.isnan(obs[i].a0)) or abs(gbs[i].a0 - obs[i].a0) < 1e-9, i
+    finally:
+        dg.dftfe_batch_destroy(batch)
+        for it in items:
+            dg.dftfe_ham_destroy(it["ham"])
+            dg.dftfe_mesh_destroy(it["mesh"])

@@ -1,11 +1,13 @@
 """CUDA graphs of the pass's filter phase and the FP64 cell-kernel autotuner: both change only
-how the work is launched, so every result must be bit-identical to the plain launches."""
+how the work is launched, so every result must be bit-identical to the plain launches, and
+graphed and autotuned passes must match the FP64 oracle."""
 import math
 import numpy as np
 import pytest
 
+import oracle
 import synth
-from systems import gpu_system, small_case
+from systems import gpu_system, oracle_system, small_case
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -160,3 +162,38 @@ def test_autotuned_graphed_complex_pass_matches_plain(dg):
     for h, m in ((h1, m1), (h2, m2)):
         dg.dftfe_ham_destroy(h)
         dg.dftfe_mesh_destroy(m)
+
+
+@pytest.mark.parametrize("mode", ["graphed", "autotuned", "graphed+autotuned"])
+def test_graphed_and_autotuned_passes_match_the_oracle(dg, mode):
+    """Three passes with the graphed filter phase and/or the autotuned FP64 cell kernel against
+    three passes of the FP64 oracle from the same seeded start and the oracle's own bounds:
+    Ritz values within 1e-9 Ha, bounds updates within 1e-9 Ha."""
+    c = small_case(0, n=(4, 3, 2), p=4, L=8.0, nl=True)
+    om, oh = oracle_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    mesh, ham = _sys(dg, c)
+    try:
+        dg.dftfe_ham_use_graphs(ham, "graphed" in mode)
+        dg.dftfe_ham_autotune(ham, "autotuned" in mode)
+        N, blk, deg = 20, 8, 9
+        X0 = synth.random_block(15, om.ndofs, N)
+        tmin, _, b = oracle.lanczos_bounds(oh.apply, synth.counter_uniform(16, om.ndofs), 20)
+        bo = oracle.first_pass_bounds(tmin, b, N, om.ndofs)
+        bg = dg.make_bounds(bo.a, bo.b, bo.a0)
+        X = torch.from_numpy(X0).cuda()
+        ev = torch.empty(N, dtype=torch.float64, device="cuda")
+        rs = torch.empty_like(ev)
+        Xo = X0
+        for it in range(3):
+            dg.dftfe_chfsi_pass(ham, X, blk, deg, bg, ev, rs)
+            Xo, _, theta, r, bo = oracle.chfsi_pass(oh, Xo, blk, deg, bo)
+            assert np.abs(ev.cpu().numpy() - theta).max() < 1e-9, it
+            assert abs(bg.a - bo.a) < 1e-9 and abs(bg.a0 - bo.a0) < 1e-9, it
+        if "graphed" in mode:
+            assert dg.dftfe_graph_query(ham)[0] == 2           # passes 2 and 3 replayed the graph
+        if "autotuned" in mode:
+            rows, best, heur = dg.dftfe_autotune_query(ham, blk)
+            assert best > 0.0
+    finally:
+        dg.dftfe_ham_destroy(ham)
+        dg.dftfe_mesh_destroy(mesh)
