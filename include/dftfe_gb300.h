@@ -408,8 +408,16 @@ typedef struct {
  * keeps pointers to them (destroy the batch first).  Potentials may change between passes. */
 dftfe_status dftfe_batch_create(const dftfe_ham* hams, int nsys, dftfe_batch* out);
 
-/* One pass for every system; items[i] belongs to hams[i].  prec must be DFTFE_FP64.
- * Errors as for dftfe_chfsi_pass (checked for all items before any work). */
+/* One pass for every system; items[i] belongs to hams[i].  prec is DFTFE_FP64 (shared FP64
+ * launches as above) or DFTFE_MIXED_TF32X3: the split-precision filter of Sec. 4.3's cell
+ * products on the tensor cores, where per Chebyshev step ONE persistent cell-product launch
+ * per FE degree covers every cell of every system still filtering (a work list of
+ * (system, cell) pairs; complex items as complex64 through their real view), the assembly
+ * with the recurrence, the nonlocal and k-point terms run per system, and CholGS /
+ * Rayleigh-Ritz as dftfe_chfsi_pass in that precision.  Either way the results are
+ * bit-identical to the single-system passes in the same precision.  Errors as for
+ * dftfe_chfsi_pass (checked for all items before any work); DFTFE_ERR_TIMEOUT if a bounded
+ * wait of the tensor-core kernel gave up. */
 dftfe_status dftfe_batch_chfsi_pass(dftfe_batch batch, dftfe_batch_item* items, dftfe_precision prec);
 
 /* Synchronise the batch's stream and free it (NULL is a no-op). */

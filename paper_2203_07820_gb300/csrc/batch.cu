@@ -50,6 +50,9 @@ struct dftfe_batch_s {
   void* d_steps = nullptr;                  // per-step system descriptors
   size_t steps_bytes = 0;
   std::vector<dftfe::bt::SysStep> host_steps;   // their host copy (kept until the next pass)
+  // descriptors of the batched split-precision filter (device buffer and its host staging)
+  dftfe::DevBuf mixed_desc;
+  std::vector<uint8_t> mixed_host;
   // CUDA graph of the filter phase (dftfe_batch_use_graphs)
   bool use_graphs = false;
   std::map<std::string, dftfe::GraphSlot> graphs;
@@ -279,6 +282,47 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
   capture_and_launch(slot, bt->stream, bt->capture_stream, streams, prof, enqueue);
 }
 
+// The split-precision (TF32x3) filter phase of a batched pass: rounds j = block j of every
+// system, each round's cell products in one persistent launch per step and degree group over
+// all systems' cells (plan_mixed_batch); optionally one CUDA graph for the whole phase.
+static void batch_filter_mixed(dftfe_batch bt, dftfe_batch_item* items, int* err) {
+  const int ns = (int)bt->hams.size();
+  int rounds = 0;
+  for (int s = 0; s < ns; ++s) rounds = std::max(rounds, (items[s].ncol + items[s].block - 1) / items[s].block);
+  std::vector<std::vector<MixedBlock>> plan(rounds);
+  for (int j = 0; j < rounds; ++j)
+    for (int s = 0; s < ns; ++s) {
+      const int cw = items[s].kpoint ? 2 : 1;
+      const int nb = std::min(items[s].block, items[s].ncol - j * items[s].block);
+      if (nb <= 0 || items[s].degree <= 0) continue;
+      plan[j].push_back(MixedBlock{bt->hams[s], items[s].X + (int64_t)cw * j * items[s].block, cw * items[s].ld,
+                                   cw * nb, items[s].degree, items[s].bounds, items[s].kpoint != 0});
+    }
+  auto enqueue = plan_mixed_batch(plan, bt->stream, err, bt->mixed_desc, bt->mixed_host);
+  if (!bt->use_graphs) {
+    enqueue();
+    return;
+  }
+  std::string key = "batch_tf32x3";
+  for (int s = 0; s < ns; ++s)
+    key += "/" + std::to_string(items[s].ncol) + "," + std::to_string(items[s].block) + "," +
+           std::to_string(items[s].degree) + "," + std::to_string(items[s].kpoint);
+  GraphSlot& slot = bt->graphs[key];
+  if (!slot.warm) {
+    enqueue();
+    slot.warm = true;
+    return;
+  }
+  if (!bt->capture_stream) DFTFE_CHECK_CUDA(cudaStreamCreateWithFlags(&bt->capture_stream, cudaStreamNonBlocking));
+  std::vector<cudaStream_t*> streams = {&bt->stream};
+  std::vector<bool*> prof;
+  for (auto h : bt->hams) {
+    streams.push_back(&h->stream);
+    prof.push_back(&h->profiling);
+  }
+  capture_and_launch(slot, bt->stream, bt->capture_stream, streams, prof, enqueue);
+}
+
 }  // namespace dftfe
 
 using namespace dftfe;
@@ -355,7 +399,7 @@ extern "C" dftfe_status dftfe_batch_destroy(dftfe_batch b) {
 extern "C" dftfe_status dftfe_batch_chfsi_pass(dftfe_batch b, dftfe_batch_item* items, dftfe_precision prec) {
   ABI_BEGIN
   DFTFE_REQUIRE(b && items, "null argument");
-  DFTFE_REQUIRE(prec == DFTFE_FP64, "batched passes are FP64");
+  DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_TF32X3, "batched passes are FP64 or TF32x3");
   const int ns = (int)b->hams.size();
   for (int s = 0; s < ns; ++s) {
     const dftfe_batch_item& it = items[s];
@@ -373,7 +417,17 @@ extern "C" dftfe_status dftfe_batch_chfsi_pass(dftfe_batch b, dftfe_batch_item* 
   }
   {
     ProfScope ps(b->hams[0], "batch_filter");
-    batch_filter(b, items);
+    if (prec == DFTFE_FP64) {
+      batch_filter(b, items);
+    } else {
+      int* err = (int*)ws_get(b->hams[0], "mx_err_batch", sizeof(int));
+      DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), b->stream));
+      batch_filter_mixed(b, items, err);
+      int herr = 0;
+      DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+      DFTFE_CHECK_CUDA(cudaStreamSynchronize(b->stream));
+      if (herr) throw Error(DFTFE_ERR_TIMEOUT, "batched mixed cell kernel: a bounded wait timed out");
+    }
   }
   for (int s = 0; s < ns; ++s)
     if (items[s].kpoint)

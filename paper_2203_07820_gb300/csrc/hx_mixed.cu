@@ -29,6 +29,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
 
 namespace dftfe {
 
@@ -350,35 +354,51 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
 //   K-major 128-byte-swizzled tile of 128 x 32 floats; the last M-tile holds only its rows in
 //   8-row atoms (88 of 128 for p = 6), so a cell streams (nmt - 1) x 16 KB + rows8 x 128 B per
 //   K-chunk -- the nc x nc matrix plus the K padding, nothing else.
+// The FP32 tiles land in a 4-slot ring that is released as soon as a tile is converted, so
+// three to four 16 KB bulk copies stay in flight per SM (the HBM latency at the rate the
+// tensor cores consume tiles); the hi/lo pairs go to a 2-slot ring that the MMAs read.
 // Warp roles (448 threads):
-//   warp 0        A producer: one bulk copy per tile into the landing slot (3-stage ring)
+//   warp 0        A producer: one bulk copy per tile into the landing ring
 //   warp 1        TMEM owner and MMA issuer (one elected lane)
 //   warps 2-5     B producers: cp.async gather of the cell's rows of X (each warp 32 columns,
-//                 into its own 4 KB slice of the stage's lo slot, two chunks ahead), then the
-//                 split of the chunk into the swizzled hi and lo B tiles (3-stage ring)
-//   warps 6-9     epilogue (tcgen05.ld of the accumulators, stores of the rows of Y^c)
-//   warps 10-13   A converters: hi = rn_tf32(f) in place, lo = rn_tf32(f - hi) beside it
+//                 into its own 4 KB slice of the stage's lo slot, two chunks ahead; the cell
+//                 map entries of the next chunk are loaded one chunk ahead), then the split
+//                 of the chunk into the swizzled hi and lo B tiles (3-stage ring)
+//   warps 6-9     epilogue (tcgen05.ld of the accumulators, 16-byte stores of the rows of Y^c)
+//   warps 10-13   A converters: landing tile -> hi = rn_tf32(f), lo = rn_tf32(f - hi)
 // Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its own
 // copies and MMAs (bounded), frees its tensor memory and returns.
 namespace mp {
 constexpr int kThreads = 448;
-constexpr int kStagesA = 3, kStagesB = 3;
+constexpr int kLand = 4, kConv = 2, kStagesB = 3;
 constexpr int kTile = 16384;
-constexpr int kStage = 2 * kTile;                  // hi (landing) | lo
+constexpr int kStage = 2 * kTile;                  // hi | lo
 constexpr int kMaxMTiles = 4;
 struct Shared {
-  uint64_t a_full[kStagesA], a_conv[kStagesA], a_empty[kStagesA];
+  uint64_t land_full[kLand], land_empty[kLand];
+  uint64_t conv_full[kConv], conv_empty[kConv];
   uint64_t b_full[kStagesB], b_empty[kStagesB];
   uint64_t acc_full, acc_empty[kMaxMTiles], drain;
   uint32_t tmem;
   int abort;
 };
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)kStagesA * kStage + (size_t)kStagesB * kStage + mx::kPatchBytes + sizeof(Shared);
+  return 1024 + (size_t)kLand * kTile + (size_t)kConv * kStage + (size_t)kStagesB * kStage + sizeof(Shared);
 }
 __host__ __device__ inline int64_t kc_block_bytes(int nmt, int rows8) {
   return (int64_t)(nmt - 1) * kTile + (int64_t)rows8 * 128;
 }
+// the operands of one system in a launch: its FP32 plane, cell map, FP32 block (ld a multiple
+// of 32 floats) with the launch's columns col0 .. col0 + 127 (ncol in all), and its
+// per-cell product buffer
+struct Item {
+  const uint8_t* A;
+  const int32_t* map;
+  const float* X;
+  float* Yc;
+  int64_t ldx;
+  int col0, ncol;
+};
 }  // namespace mp
 
 // Set-up: the FP32 plane in the tile order above (written in physical order, so the stores
@@ -407,9 +427,12 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(bytes) : "memory");
 }
 
-__global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
-    const uint8_t* __restrict__ A, const int32_t* __restrict__ map, int ncells, int nc, int nkc, int nmt,
-    const float* __restrict__ X, int64_t ldx, float* __restrict__ Yc, int col0, int ncol, int* err) {
+// Work item g of a launch: cell g of `single` (work == NULL), or the (system, cell) pair
+// work[g] of the systems `items` (all of one degree: nc, nkc, nmt are the launch's).  Items
+// are dealt round-robin over the persistent grid.
+__global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single, const mp::Item* __restrict__ items,
+                                                                const int2* __restrict__ work, int nwork, int nc,
+                                                                int nkc, int nmt, int* err) {
   using namespace mp;
   using tc::mbar_arrive;
   using tc::mbar_init;
@@ -418,21 +441,34 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
   using tc::smem_u32;
   using tc::sw128;
   using tc::tc_commit;
-  auto cell_of = [&](int64_t i) -> int64_t { return blockIdx.x + i * gridDim.x; };
+  // the CTA's i-th work item: its system's operands and its cell
+  auto item_of = [&](int64_t i, int64_t& cell) -> Item {
+    const int64_t g = blockIdx.x + i * gridDim.x;
+    if (!work) {
+      cell = g;
+      return single;
+    }
+    const int2 w = work[g];
+    cell = w.y;
+    return items[w.x];
+  };
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = base;
-  uint8_t* sB = sA + kStagesA * kStage;
-  uint8_t* sP = sB + kStagesB * kStage;
-  Shared* sh = (Shared*)(sP + mx::kPatchBytes);
+  uint8_t* sL = base;                                   // landing ring: kLand x 16 KB FP32
+  uint8_t* sC = sL + kLand * kTile;                     // converted ring: kConv x (hi | lo)
+  uint8_t* sB = sC + kConv * kStage;                    // B ring: kStagesB x (hi | lo)
+  Shared* sh = (Shared*)(sB + kStagesB * kStage);
   volatile int* abort = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStagesA; ++s) {
-      mbar_init(&sh->a_full[s], 1);
-      mbar_init(&sh->a_conv[s], 128);
-      mbar_init(&sh->a_empty[s], 1);
+    for (int s = 0; s < kLand; ++s) {
+      mbar_init(&sh->land_full[s], 1);
+      mbar_init(&sh->land_empty[s], 128);
+    }
+    for (int s = 0; s < kConv; ++s) {
+      mbar_init(&sh->conv_full[s], 128);
+      mbar_init(&sh->conv_empty[s], 1);
     }
     for (int s = 0; s < kStagesB; ++s) { mbar_init(&sh->b_full[s], 128); mbar_init(&sh->b_empty[s], 1); }
     mbar_init(&sh->acc_full, 1);
@@ -450,7 +486,7 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh->tmem;
-  const int my_cells = ncells > (int)blockIdx.x ? (ncells - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int my_cells = nwork > (int)blockIdx.x ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int rows8 = ((nc - 128 * (nmt - 1)) + 7) / 8 * 8;   // rows of the last M-tile, in atoms
   const int64_t kcb = kc_block_bytes(nmt, rows8);
 
@@ -460,23 +496,24 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
       uint32_t ta = 0;
       bool go = true;
       for (int i = 0; i < my_cells && go; ++i) {
-        const int64_t cell = cell_of(i);
+        int64_t cell;
+        const uint8_t* A = item_of(i, cell).A;
         for (int kc = 0; kc < nkc && go; ++kc)
           for (int mt = 0; mt < nmt; ++mt, ++ta) {
-            const int s = ta % kStagesA;
-            if (!mbar_wait(&sh->a_empty[s], ((ta / kStagesA) & 1) ^ 1, abort, err)) { go = false; break; }
-            const uint32_t full = smem_u32(&sh->a_full[s]);
+            const int s = ta % kLand;
+            if (!mbar_wait(&sh->land_empty[s], ((ta / kLand) & 1) ^ 1, abort, err)) { go = false; break; }
+            const uint32_t full = smem_u32(&sh->land_full[s]);
             const uint32_t bytes = mt == nmt - 1 ? (uint32_t)rows8 * 128u : (uint32_t)kTile;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(full), "r"(bytes) : "memory");
             const uint8_t* src = A + (cell * nkc + kc) * kcb + (int64_t)mt * kTile;
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         :: "r"(smem_u32(sA + s * kStage)), "l"(src), "r"(bytes), "r"(full) : "memory");
+                         :: "r"(smem_u32(sL + s * kTile)), "l"(src), "r"(bytes), "r"(full) : "memory");
           }
       }
       // drain: every issued copy has landed before the CTA may exit
-      for (uint32_t t = (ta > (uint32_t)kStagesA ? ta - kStagesA : 0); t < ta; ++t) {
+      for (uint32_t t = (ta > (uint32_t)kLand ? ta - kLand : 0); t < ta; ++t) {
         volatile int no_abort = 0;
-        mbar_wait(&sh->a_full[t % kStagesA], (t / kStagesA) & 1, &no_abort, err);
+        mbar_wait(&sh->land_full[t % kLand], (t / kLand) & 1, &no_abort, err);
       }
     }
   } else if (warp == 1) {
@@ -490,11 +527,11 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
           if (!mbar_wait(&sh->b_full[sb], (tb / kStagesB) & 1, abort, err)) { go = false; break; }
           const uint32_t bhi = smem_u32(sB + sb * kStage), blo = bhi + kTile;
           for (int mt = 0; mt < nmt; ++mt, ++ta) {
-            const int sa = ta % kStagesA;
+            const int sa = ta % kConv;
             if (kc == 0 && !mbar_wait(&sh->acc_empty[mt], (i & 1) ^ 1, abort, err)) { go = false; break; }
-            if (!mbar_wait(&sh->a_conv[sa], (ta / kStagesA) & 1, abort, err)) { go = false; break; }
+            if (!mbar_wait(&sh->conv_full[sa], (ta / kConv) & 1, abort, err)) { go = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = smem_u32(sA + sa * kStage), alo = ahi + kTile;
+            const uint32_t ahi = smem_u32(sC + sa * kStage), alo = ahi + kTile;
             const uint32_t d = tmem + (uint32_t)(mt * 128);
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
@@ -503,7 +540,7 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
               mx::mma<true>(d, sdesc(ahi + o), sdesc(blo + o), 1u);
               mx::mma<true>(d, sdesc(alo + o), sdesc(bhi + o), 1u);
             }
-            tc_commit(&sh->a_empty[sa]);
+            tc_commit(&sh->conv_empty[sa]);
           }
           if (go) tc_commit(&sh->b_empty[sb]);
         }
@@ -519,26 +556,38 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
     // warp w gathers columns col0 + 32 w .. +31 of the chunk's 32 rows into its 4 KB slice of
     // the stage's lo slot (row i of the chunk at byte 128 i), each lane copying 16 bytes of
     // one row per instruction; the slice is exactly where the warp's 32 rows of the lo B
-    // tile go, so the split overwrites only what the warp itself staged
+    // tile go, so the split overwrites only what the warp itself staged.  Lane l holds the
+    // node of row l of the next chunk to issue (loaded one chunk ahead) and hands it to the
+    // lanes that copy that row by a shuffle.
     const int w = warp - 2;
     const int n = 32 * w + lane;
     const uint32_t nchunks = (uint32_t)my_cells * (uint32_t)nkc;
+    auto node_of = [&](uint32_t t) -> int {
+      if (t >= nchunks) return 0;
+      int64_t cell;
+      const Item it = item_of(t / nkc, cell);
+      const int k = (int)(t % nkc) * 32 + lane;
+      return k < nc ? __ldg(it.map + cell * nc + k) : 0;
+    };
+    int node_next = node_of(0);
     auto issue = [&](uint32_t t) -> bool {
       const int sb = t % kStagesB;
+      const int node_t = node_next;
+      node_next = node_of(t + 1);                       // the next chunk's nodes, in flight
       if (!mbar_wait(&sh->b_empty[sb], ((t / kStagesB) & 1) ^ 1, abort, err)) return false;
-      const int64_t cell = cell_of(t / nkc);
+      int64_t cell;
+      const Item it = item_of(t / nkc, cell);
       const int kc = (int)(t % nkc);
-      const int32_t* cm = map + cell * nc;
       const uint32_t dst = smem_u32(sB + sb * kStage + kTile + w * 4096);
       const int seg = lane & 7;
-      const int c = col0 + 32 * w + 4 * seg;
-      const int cvalid = min(max(ncol - c, 0), 4) * 4;
+      const int c = it.col0 + 32 * w + 4 * seg;
+      const int cvalid = min(max(it.ncol - c, 0), 4) * 4;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int row = 4 * j + (lane >> 3);
-        const int k = kc * 32 + row;
-        const bool ok = k < nc && cvalid > 0;
-        const float* src = ok ? X + (int64_t)__ldg(cm + k) * ldx + c : X;
+        const int node = __shfl_sync(0xffffffffu, node_t, row);
+        const bool ok = kc * 32 + row < nc && cvalid > 0;
+        const float* src = ok ? it.X + (int64_t)node * it.ldx + c : it.X;
         cp_async16(dst + row * 128 + seg * 16, src, ok ? (uint32_t)cvalid : 0u);
       }
       return true;
@@ -578,31 +627,28 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
     asm volatile("cp.async.wait_all;" ::: "memory");
   } else if (warp >= 6 && warp < 10) {
     // ------------------------------------------------------------ epilogue
+    // lane = accumulator row: 32 consecutive columns of the row per tcgen05.ld, written as
+    // four 32-byte stores (one full sector each) into the row of Y^c
     const int q = warp & 3;                       // TMEM lane quadrant of this warp
-    float* patch = reinterpret_cast<float*>(sP) + q * (32 * mx::kPatchLd);
     for (int i = 0; i < my_cells; ++i) {
       if (!mbar_wait(&sh->acc_full, i & 1, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t cell = cell_of(i);
+      int64_t cell;
+      float* Yc = item_of(i, cell).Yc;
       for (int mt = 0; mt < nmt; ++mt) {
-        const int row0 = mt * 128 + q * 32;
-        for (int cb = 0; cb < 4; ++cb) {
+        const int row = mt * 128 + q * 32 + lane;
+        const bool any = mt * 128 + q * 32 < nc;  // warp-uniform: the quadrant holds rows
+        for (int cb = 0; cb < 4 && any; ++cb) {
           uint32_t r[32];
           tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(mt * 128 + cb * 32), r);
-          if (row0 >= nc) continue;               // whole patch is padding (warp-uniform)
+          if (row < nc) {
+            float* y = Yc + (cell * nc + row) * (int64_t)128 + cb * 32;
 #pragma unroll
-          for (int j = 0; j < 32; j += 4)
-            *reinterpret_cast<uint4*>(patch + lane * mx::kPatchLd + j) = make_uint4(r[j], r[j + 1], r[j + 2], r[j + 3]);
-          __syncwarp();
-#pragma unroll
-          for (int it = 0; it < 8; ++it) {
-            const int rl = it * 4 + (lane >> 3);
-            const int row = row0 + rl;
-            const float4 val = *reinterpret_cast<const float4*>(patch + rl * mx::kPatchLd + 4 * (lane & 7));
-            if (row < nc)
-              *reinterpret_cast<float4*>(Yc + (cell * nc + row) * (int64_t)128 + cb * 32 + 4 * (lane & 7)) = val;
+            for (int j = 0; j < 32; j += 8)
+              asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                           :: "l"(y + j), "r"(r[j]), "r"(r[j + 1]), "r"(r[j + 2]), "r"(r[j + 3]), "r"(r[j + 4]),
+                              "r"(r[j + 5]), "r"(r[j + 6]), "r"(r[j + 7]) : "memory");
           }
-          __syncwarp();
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&sh->acc_empty[mt]);
@@ -616,23 +662,35 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(
     for (int i = 0; i < my_cells && go; ++i)
       for (int kc = 0; kc < nkc && go; ++kc)
         for (int mt = 0; mt < nmt; ++mt, ++ta) {
-          const int s = ta % kStagesA;
-          if (!mbar_wait(&sh->a_full[s], (ta / kStagesA) & 1, abort, err)) { go = false; break; }
+          const int s = ta % kLand, sc = ta % kConv;
+          if (!mbar_wait(&sh->land_full[s], (ta / kLand) & 1, abort, err)) { go = false; break; }
+          if (!mbar_wait(&sh->conv_empty[sc], ((ta / kConv) & 1) ^ 1, abort, err)) { go = false; break; }
           const int nchunk16 = (mt == nmt - 1 ? rows8 : 128) * 8;
-          uint4* hi = reinterpret_cast<uint4*>(sA + s * kStage);
-          uint4* lo = reinterpret_cast<uint4*>(sA + s * kStage + kTile);
-          for (int c = tid; c < nchunk16; c += 128) {
-            const uint4 u = hi[c];
-            uint4 h4, l4;
-            tc::split_tf32_bits(u.x, h4.x, l4.x);
-            tc::split_tf32_bits(u.y, h4.y, l4.y);
-            tc::split_tf32_bits(u.z, h4.z, l4.z);
-            tc::split_tf32_bits(u.w, h4.w, l4.w);
-            hi[c] = h4;
-            lo[c] = l4;
+          const uint4* src = reinterpret_cast<const uint4*>(sL + s * kTile);
+          uint4* hi = reinterpret_cast<uint4*>(sC + sc * kStage);
+          uint4* lo = reinterpret_cast<uint4*>(sC + sc * kStage + kTile);
+          uint4 u[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = tid + 128 * j;
+            if (c < nchunk16) u[j] = src[c];
+          }
+          mbar_arrive(&sh->land_empty[s]);          // the landing slot may take the next copy
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = tid + 128 * j;
+            if (c < nchunk16) {
+              uint4 h4, l4;
+              tc::split_tf32_bits(u[j].x, h4.x, l4.x);
+              tc::split_tf32_bits(u[j].y, h4.y, l4.y);
+              tc::split_tf32_bits(u[j].z, h4.z, l4.z);
+              tc::split_tf32_bits(u[j].w, h4.w, l4.w);
+              hi[c] = h4;
+              lo[c] = l4;
+            }
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(&sh->a_conv[s]);
+          mbar_arrive(&sh->conv_full[sc]);
         }
   }
   __syncwarp();
@@ -863,10 +921,11 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
   for (int col0 = 0; col0 < ncol; col0 += 128) {
     {
       ProfScope ps(h, tf32 ? "cell_gemm_tf32x3" : "cell_gemm_bf16x3");
-      if (tf32)
-        DFTFE_LAUNCH(k_cell_tf32p, grid, mp::kThreads, mp::smem_bytes(), h->stream, A, h->d_map, (int)m->Nc, m->nc,
-                     nkc, nmt, X, ldx, Yc, col0, ncol, err);
-      else
+      if (tf32) {
+        const mp::Item one{A, h->d_map, X, Yc, ldx, col0, ncol};
+        DFTFE_LAUNCH(k_cell_tf32p, grid, mp::kThreads, mp::smem_bytes(), h->stream, one, nullptr, nullptr,
+                     (int)m->Nc, m->nc, nkc, nmt, err);
+      } else
         DFTFE_LAUNCH(k_cell_mixed<false>, grid, mx::kThreads, sh, h->stream, A, h->d_map, (int)m->Nc, m->nc,
                      nkc, nmt, X, ldx, Yc, col0, ncol, err);
     }
@@ -936,6 +995,262 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
   if (herr) throw Error(DFTFE_ERR_TIMEOUT, "mixed cell kernel: a bounded wait timed out");
+}
+
+// Batched TF32x3 filter: per round, one block of every system (X_s, ld_s, ncol_s real
+// columns -- the real view of a complex block for a k-point item), each with its own degree
+// and bounds.  Per Chebyshev step and 128-column tile, ONE persistent cell-product launch per
+// degree group covers every cell of every system still filtering (a work list of
+// (system, cell) pairs); the nonlocal coefficients, the assembly fused with the recurrence
+// and the k-point terms run per system.  Each system's operations, and their order, are
+// those of its single-system filter, so the results are bit-identical to it.  Planning forms
+// the launch descriptors of every round on the host and uploads them once; the returned
+// closure enqueues all launches with no host work in between (it can be captured as one
+// CUDA graph).
+namespace {
+struct MixedRoundPlan {
+  struct Sys {
+    const uint8_t* A = nullptr;
+    int nkc = 0, nmt = 0;
+    const int32_t *nptr = nullptr, *nslot = nullptr;
+    float* Yc = nullptr;
+    float* buf[3] = {nullptr, nullptr, nullptr};
+    int64_t ld32 = 0;
+  };
+  struct StepSys {
+    int cur, prev, out;
+    float alpha, s1, s2;
+  };
+  struct CellLaunch {
+    int k, tile, nc, nkc, nmt;
+    size_t item_off, work_off;
+    int nwork;
+  };
+  std::vector<MixedBlock> blk;
+  std::vector<Sys> sy;
+  std::vector<std::vector<StepSys>> steps;
+  std::vector<CellLaunch> launches;
+  int maxdeg = 0, ntiles = 0;
+  size_t item_base = 0, work_base = 0;     // element offsets of the round in the uploads
+};
+}  // namespace
+
+static void plan_mixed_round(MixedRoundPlan& R, std::vector<mp::Item>& items, std::vector<int2>& work) {
+  std::vector<MixedBlock>& blk = R.blk;
+  const int ns = (int)blk.size();
+  if (!g_mixed_attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp::smem_bytes()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
+    g_mixed_attr = true;
+  }
+  using Sys = MixedRoundPlan::Sys;
+  using StepSys = MixedRoundPlan::StepSys;
+  using CellLaunch = MixedRoundPlan::CellLaunch;
+  std::vector<Sys>& sy = R.sy;
+  sy.assign(ns, Sys{});
+  int& maxdeg = R.maxdeg;
+  int& ntiles = R.ntiles;
+  for (int s = 0; s < ns; ++s) {
+    const MixedBlock& b = blk[s];
+    if (b.degree <= 0 || b.ncol <= 0) continue;
+    dftfe_ham h = b.h;
+    auto* m = h->mesh;
+    Sys& y = sy[s];
+    y.A = mixed_tiles(h, true, &y.nkc, &y.nmt);
+    node_slots(h, &y.nptr, &y.nslot);
+    y.Yc = (float*)ws_get(h, "mx_yc", sizeof(float) * (size_t)m->Nc * m->nc * 128);
+    y.ld32 = (b.ncol + 31) / 32 * 32;
+    y.buf[0] = (float*)ws_get(h, "mx_v0", sizeof(float) * m->M * (size_t)y.ld32);
+    y.buf[1] = (float*)ws_get(h, "mx_v1", sizeof(float) * m->M * (size_t)y.ld32);
+    y.buf[2] = (float*)ws_get(h, "mx_v2", sizeof(float) * m->M * (size_t)y.ld32);
+    maxdeg = std::max(maxdeg, b.degree);
+    ntiles = std::max(ntiles, (b.ncol + 127) / 128);
+  }
+  // buffer rotation and recurrence coefficients of every system and step, as the single filter
+  // forms them
+  std::vector<std::vector<StepSys>>& steps = R.steps;
+  steps.assign(ns, {});
+  for (int s = 0; s < ns; ++s) {
+    const MixedBlock& bb = blk[s];
+    if (bb.degree <= 0 || bb.ncol <= 0) continue;
+    const dftfe_bounds& b = bb.b;
+    const double e = (b.b - b.a) / 2.0, c = (b.b + b.a) / 2.0;
+    const bool scaled = !std::isnan(b.a0);
+    double sigma = scaled ? e / (b.a0 - c) : 0.0;
+    const double sigma1 = sigma, gamma = scaled ? 2.0 / sigma1 : 0.0;
+    int cur = 0, prev = -1;
+    for (int k = 1; k <= bb.degree; ++k) {
+      int out = 0;
+      while (out == cur || out == prev) ++out;
+      double alpha, s1, s2 = 0.0;
+      if (k == 1) {
+        alpha = scaled ? sigma1 / e : 1.0 / e;
+        s1 = -c * alpha;
+      } else if (scaled) {
+        const double sigma2 = 1.0 / (gamma - sigma);
+        alpha = 2.0 * sigma2 / e;
+        s1 = -c * alpha;
+        s2 = -sigma * sigma2;
+        sigma = sigma2;
+      } else {
+        alpha = 2.0 / e;
+        s1 = -c * alpha;
+        s2 = -1.0;
+      }
+      StepSys st{cur, prev, out, (float)alpha, (float)s1, (float)s2};
+      if (bb.kpoint) {
+        const double* kv = bb.h->kvec;
+        const double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+        st.s1 += (float)(0.5 * (double)st.alpha * k2);
+      }
+      steps[s].push_back(st);
+      prev = cur;
+      cur = out;
+    }
+  }
+  // launch descriptors: per (step, tile, degree group) the items of the systems still
+  // filtering, and one work list per distinct set of systems
+  std::map<std::vector<int>, std::pair<size_t, int>> lists;
+  std::vector<CellLaunch>& launches = R.launches;
+  launches.clear();
+  std::vector<int> ncs;
+  for (int s = 0; s < ns; ++s)
+    if (!steps[s].empty() && std::find(ncs.begin(), ncs.end(), blk[s].h->mesh->nc) == ncs.end())
+      ncs.push_back(blk[s].h->mesh->nc);
+  for (int k = 1; k <= maxdeg; ++k)
+    for (int t = 0; t < ntiles; ++t)
+      for (int nc : ncs) {
+        std::vector<int> act;
+        for (int s = 0; s < ns; ++s)
+          if ((int)steps[s].size() >= k && blk[s].h->mesh->nc == nc && blk[s].ncol > 128 * t) act.push_back(s);
+        if (act.empty()) continue;
+        CellLaunch L{k, t, nc, sy[act[0]].nkc, sy[act[0]].nmt, items.size() - R.item_base, 0, 0};
+        for (int s : act) {
+          const StepSys& st = steps[s][k - 1];
+          items.push_back(mp::Item{sy[s].A, blk[s].h->d_map, sy[s].buf[st.cur], sy[s].Yc, sy[s].ld32, 128 * t,
+                                   blk[s].ncol});
+        }
+        auto it = lists.find(act);
+        if (it == lists.end()) {
+          const size_t off = work.size() - R.work_base;
+          for (int li = 0; li < (int)act.size(); ++li) {
+            const int64_t Nc = blk[act[li]].h->mesh->Nc;
+            for (int64_t cidx = 0; cidx < Nc; ++cidx) work.push_back(make_int2(li, (int)cidx));
+          }
+          it = lists.emplace(act, std::make_pair(off, (int)(work.size() - R.work_base - off))).first;
+        }
+        L.work_off = it->second.first;
+        L.nwork = it->second.second;
+        launches.push_back(L);
+      }
+}
+
+static void enqueue_mixed_round(const MixedRoundPlan& R, cudaStream_t stream, int* err, const mp::Item* d_items,
+                                const int2* d_work) {
+  using StepSys = MixedRoundPlan::StepSys;
+  using CellLaunch = MixedRoundPlan::CellLaunch;
+  const std::vector<MixedBlock>& blk = R.blk;
+  const int ns = (int)blk.size();
+  const auto& sy = R.sy;
+  const auto& steps = R.steps;
+  const auto& launches = R.launches;
+  const int maxdeg = R.maxdeg, ntiles = R.ntiles;
+  if (maxdeg == 0) return;
+  const int sm = blk[0].h->sm_count;
+
+  for (int s = 0; s < ns; ++s)
+    if (!steps[s].empty()) {
+      auto* m = blk[s].h->mesh;
+      DFTFE_LAUNCH(k_to_f32, nblk(m->M * blk[s].ncol), 256, 0, stream, blk[s].X, blk[s].ld, sy[s].buf[0], sy[s].ld32,
+                   m->M, blk[s].ncol);
+    }
+  size_t li = 0;
+  for (int k = 1; k <= maxdeg; ++k) {
+    // nonlocal coefficients P = h (C~^T X) of the Gamma-point systems with projectors
+    std::vector<float*> P(ns, nullptr);
+    std::vector<int> ldP(ns, 0);
+    for (int s = 0; s < ns; ++s) {
+      if ((int)steps[s].size() < k) continue;
+      dftfe_ham h = blk[s].h;
+      if (h->nproj <= 0 || blk[s].kpoint) continue;
+      const int ncol = blk[s].ncol;
+      ldP[s] = (ncol + 3) / 4 * 4;
+      P[s] = (float*)ws_get(h, "nl_coef32", sizeof(float) * h->nproj * (size_t)ldP[s]);
+      float* Pp = (float*)ws_get(h, "nl_coef32_part", sizeof(float) * h->nproj * (size_t)kNlSplits * ncol);
+      const StepSys& st = steps[s][k - 1];
+      dim3 g1((unsigned)(h->nproj * kNlSplits), (unsigned)((ncol + 127) / 128));
+      DFTFE_LAUNCH(k_nl_coef32_part, g1, 256, 0, stream, sy[s].buf[st.cur], sy[s].ld32, ncol, h->d_prow, h->d_pnode,
+                   h->d_pval, Pp);
+      DFTFE_LAUNCH(k_nl_coef32_reduce, nblk((int64_t)h->nproj * ncol), 256, 0, stream, Pp, h->d_h, h->nproj, ncol,
+                   P[s], ldP[s]);
+    }
+    for (int t = 0; t < ntiles; ++t) {
+      for (; li < launches.size() && launches[li].k == k && launches[li].tile == t; ++li) {
+        const CellLaunch& L = launches[li];
+        ProfScope ps(blk[0].h, "batch_cell_tf32x3");
+        const mp::Item none{};
+        DFTFE_LAUNCH(k_cell_tf32p, (unsigned)std::min(L.nwork, sm), mp::kThreads, mp::smem_bytes(), stream, none,
+                     d_items + R.item_base + L.item_off, d_work + R.work_base + L.work_off, L.nwork, L.nc, L.nkc,
+                     L.nmt, err);
+      }
+      for (int s = 0; s < ns; ++s) {
+        if ((int)steps[s].size() < k || blk[s].ncol <= 128 * t) continue;
+        dftfe_ham h = blk[s].h;
+        auto* m = h->mesh;
+        const StepSys& st = steps[s][k - 1];
+        float* const* b3 = sy[s].buf;
+        const int64_t l = sy[s].ld32;
+        DFTFE_LAUNCH(k_assemble32, nblk((m->M + 7) / 8 * 256), 256, 0, stream, b3[st.out], l, b3[st.cur], l,
+                     st.prev >= 0 ? b3[st.prev] : nullptr, l, sy[s].Yc, sy[s].nptr, sy[s].nslot,
+                     P[s] ? h->d_nptr_all : nullptr, h->d_sproj, h->d_sval, P[s], ldP[s], m->M, 128 * t, blk[s].ncol,
+                     st.alpha, st.s1, st.s2);
+      }
+    }
+    for (int s = 0; s < ns; ++s) {
+      if ((int)steps[s].size() < k || !blk[s].kpoint) continue;
+      const StepSys& st = steps[s][k - 1];
+      kpoint_add32(blk[s].h, sy[s].buf[st.cur], sy[s].ld32, sy[s].buf[st.out], sy[s].ld32, blk[s].ncol / 2, st.alpha);
+    }
+  }
+  for (int s = 0; s < ns; ++s)
+    if (!steps[s].empty()) {
+      auto* m = blk[s].h->mesh;
+      DFTFE_LAUNCH(k_to_f64, nblk(m->M * blk[s].ncol), 256, 0, stream, sy[s].buf[steps[s].back().out], sy[s].ld32,
+                   blk[s].X, blk[s].ld, m->M, blk[s].ncol);
+    }
+}
+
+std::function<void()> plan_mixed_batch(const std::vector<std::vector<MixedBlock>>& rounds, cudaStream_t stream,
+                                       int* err, DevBuf& desc, std::vector<uint8_t>& host_desc) {
+  if (!g_mixed_attr) {
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp::smem_bytes()));
+    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
+    g_mixed_attr = true;
+  }
+  auto plans = std::make_shared<std::vector<MixedRoundPlan>>(rounds.size());
+  std::vector<mp::Item> items;
+  std::vector<int2> work;
+  for (size_t j = 0; j < rounds.size(); ++j) {
+    MixedRoundPlan& R = (*plans)[j];
+    R.blk = rounds[j];
+    R.item_base = items.size();
+    R.work_base = work.size();
+    plan_mixed_round(R, items, work);
+  }
+  const size_t ib = items.size() * sizeof(mp::Item), wb = work.size() * sizeof(int2);
+  const size_t woff = (ib + 255) / 256 * 256;
+  host_desc.resize(std::max<size_t>(woff + wb, 1));
+  if (ib) std::memcpy(host_desc.data(), items.data(), ib);
+  if (wb) std::memcpy(host_desc.data() + woff, work.data(), wb);
+  uint8_t* ddesc = (uint8_t*)desc.get(host_desc.size());
+  // from pageable memory: the call returns once the data is staged, so the host copy may be
+  // rewritten by the next pass
+  DFTFE_CHECK_CUDA(cudaMemcpyAsync(ddesc, host_desc.data(), host_desc.size(), cudaMemcpyHostToDevice, stream));
+  const mp::Item* d_items = reinterpret_cast<const mp::Item*>(ddesc);
+  const int2* d_work = reinterpret_cast<const int2*>(ddesc + woff);
+  return [plans, stream, err, d_items, d_work]() {
+    for (const MixedRoundPlan& R : *plans) enqueue_mixed_round(R, stream, err, d_items, d_work);
+  };
 }
 
 // Y = H~ X with the mixed cell products (FP64 in and out, FP32 inside); for parity tests.

@@ -213,6 +213,22 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
                             const dftfe_bounds& b, bool tf32, int* ext_err = nullptr, bool kpoint = false);
 void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32,
                  bool kpoint = false);
+// one block of one system in a batched TF32x3 filter round (kpoint: X is the real view of a
+// complex block, ncol real columns, at the ham's k-point)
+struct MixedBlock {
+  dftfe_ham h;
+  double* X;
+  int64_t ld;
+  int ncol, degree;
+  dftfe_bounds b;
+  bool kpoint;
+};
+// the batched filter: per round the blocks of every system, with one cell-product launch per
+// step, tile and degree group over all systems' cells.  Plans every round (workspaces, host
+// descriptors uploaded into desc, staged through host_desc) and returns the closure that
+// enqueues all launches on `stream`; err is zeroed and read by the caller.
+std::function<void()> plan_mixed_batch(const std::vector<std::vector<MixedBlock>>& rounds, cudaStream_t stream,
+                                       int* err, DevBuf& desc, std::vector<uint8_t>& host_desc);
 // with_nl = false: the local part only (real view of a complex block)
 void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl = true);
 // kpoint.cu: Z += alpha (-i k.grad X + H~_nl^k X) on FP32 complex blocks given by their real

@@ -13,10 +13,10 @@ the proposer.
 
 Training targets come from the solver itself (`search_step`): at a potential change, passes
 with each candidate degree and the standard bounds are run from a copy of the state until the
-tolerance is met, and the target is the smallest degree that needs no more passes than the
-standard degree (so the proposal saves filter applications without adding passes, whose
-orthonormalisation and projection cost the same at any degree).  Inputs: seeded sequences
-of potentials whose atoms move 0.05 bohr per step, mixed 0.3 old / 0.7 new.
+tolerance is met, each roll-out timed on the GPU, and the target is the degree with the least
+time to the tolerance (its filter applications plus the fixed orthonormalisation and
+projection cost of every pass it needs; fewer applications break near-ties).  Inputs: seeded
+sequences of potentials whose atoms move 0.05 bohr per step, mixed 0.3 old / 0.7 new.
 
 Host logic only chooses parameters; the passes, the Lanczos runs and the network run on the
 GPU through the C ABI.
@@ -32,7 +32,7 @@ from . import (dftfe_chfsi_pass, dftfe_lanczos, dftfe_mlp_adam, dftfe_mlp_forwar
 N_IN, N_H, N_OUT = 19, 64, 3
 SHAPE = (N_IN, N_H, N_OUT)
 FALLBACK_DEGREE = 40
-CANDIDATES = (12, 16, 20, 24, 32)
+CANDIDATES = (8, 12, 16, 20, 24, 32, 48)
 LANCZOS_K = 20
 B_MARGIN = 1.01            # safety factor on a proposed upper bound
 DEG_MIN, DEG_MAX = 4, 64
@@ -264,9 +264,10 @@ def run_sequence(dg, ham, wl, qxyz, X, ctrl, seed, steps, tol=1e-5, max_passes=3
 
 def search_step(ham, wl, X, ctrl, tol, prec, max_rollout=12):
     """Targets at a potential change: from a copy of the state, each candidate degree is run
-    with the standard bounds (fresh Lanczos bound, a = theta_N) until the tolerance is met;
-    the target degree is the smallest one that needs no more passes than degree 40.  Returns
-    it and the sample (features, targets)."""
+    with the standard bounds (fresh Lanczos bound, a = theta_N) until the tolerance is met,
+    timed with the device synchronised on both sides; the target degree is the one with the
+    least time to the tolerance (within 3 % of the least, the fewest filter applications).
+    Returns it and the sample (features, targets)."""
     import torch
     last = ctrl.hist[-1]
     F = features(ctrl.hist, True)
@@ -279,11 +280,14 @@ def search_step(ham, wl, X, ctrl, tol, prec, max_rollout=12):
     rs = torch.empty_like(ev)
     nconv = max(1, int(math.ceil(CONVERGED_FRACTION * N)))
     runs = {}
+    nblk = (N + wl.block - 1) // wl.block
     for m in sorted(set(CANDIDATES) | {FALLBACK_DEGREE}):
         Xc = X.clone()
         a, a0 = last.evals[-1], last.evals[0]
         tn1 = None
         n = None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         for k in range(max_rollout):
             dftfe_chfsi_pass(ham, Xc, wl.block, m, make_bounds(a, ctrl.b, a0), ev, rs, prec)
             evh = ev.cpu().numpy()
@@ -293,15 +297,16 @@ def search_step(ham, wl, X, ctrl, tol, prec, max_rollout=12):
             if float(rs[:nconv].max().item()) <= tol:
                 n = k + 1
                 break
-        runs[m] = (n, tn1)
+        torch.cuda.synchronize()
+        runs[m] = (n, tn1, time.perf_counter() - t0, (n or max_rollout) * m * nblk)
         del Xc
-    ref = runs[FALLBACK_DEGREE][0] or max_rollout
-    choice = FALLBACK_DEGREE
-    for m in sorted(runs):
-        n = runs[m][0]
-        if n is not None and n <= ref:
-            choice = m
-            break
+    done = {m: r for m, r in runs.items() if r[0] is not None}
+    if not done:
+        choice = FALLBACK_DEGREE
+    else:
+        best = min(r[2] for r in done.values())
+        near = [m for m, r in done.items() if r[2] <= 1.03 * best]
+        choice = min(near, key=lambda m: (done[m][3], m))
     spread = max(last.evals[-1] - last.evals[0], 1e-12)
     target = np.array([math.log2(choice / 16.0), (runs[choice][1] - last.evals[-1]) / spread,
                        math.log(ctrl.b / b_prev)])

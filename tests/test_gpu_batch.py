@@ -95,7 +95,7 @@ def test_batch_rejects_bad_input(dg):
         with pytest.raises(dg.DftfeError):
             dg.dftfe_batch_chfsi_pass(batch, [X], [block], [deg], [dg.make_bounds(bd.b, bd.a)], [ev], [rs])
         with pytest.raises(dg.DftfeError):
-            dg.dftfe_batch_chfsi_pass(batch, [X], [block], [deg], [bd], [ev], [rs], prec=2)
+            dg.dftfe_batch_chfsi_pass(batch, [X], [block], [deg], [bd], [ev], [rs], prec=dg.DFTFE_MIXED_BF16X3)
         dg.dftfe_batch_destroy(batch)
     finally:
         dg.dftfe_ham_destroy(ham)
@@ -346,3 +346,68 @@ def test_batched_passes_match_the_oracle(dg):
         for it in items:
             dg.dftfe_ham_destroy(it["ham"])
             dg.dftfe_mesh_destroy(it["mesh"])
+
+
+def test_batched_tf32x3_passes_are_bit_identical_and_match_the_oracle(dg):
+    """The split-precision batched pass (one persistent cell-product launch per step and degree
+    over every system's cells): Gamma-point items of degrees p = 4, 6, 3 (degree 0 among them,
+    blocks of 7, 8, 16, 24 and 30) and k-point items (complex64) give the bits of single TF32x3
+    passes, over two passes; and after twelve passes the Ritz values of the lower half of every
+    item are within 1e-6 Ha of twelve FP64 oracle passes from the same start."""
+    items = []
+    for spec in SYSTEMS:
+        c, om, oh, X0, bd = _oracle_gamma(spec)
+        made = [gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+                for _ in range(2)]
+        items.append(dict(sys=made, X0=X0, bd=bd, oracle=oh, cplx=False, block=spec[6], deg=spec[7]))
+    for spec in KSYSTEMS:
+        c, om, bh, Z0, bd = _oracle_kpoint(spec)
+        made = []
+        for _ in range(2):
+            mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+            nxyz, _ = dg.dftfe_mesh_coords(mesh, quad=False)
+            cent, w, rc, hc = c["proj"]
+            dg.dftfe_ham_set_kpoint(ham, spec[7], synth.projector_disp(nxyz, cent, rc, c["L"]))
+            made.append((mesh, ham))
+        items.append(dict(sys=made, X0=Z0, bd=bd, oracle=bh, cplx=True, block=spec[5], deg=spec[6]))
+    prec = dg.DFTFE_MIXED_TF32X3
+    batch = dg.dftfe_batch_create([it["sys"][0][1] for it in items])
+    try:
+        Xb = [torch.from_numpy(it["X0"].copy()).cuda() for it in items]
+        Xs = [x.clone() for x in Xb]
+        bb = [dg.make_bounds(it["bd"].a, it["bd"].b, it["bd"].a0) for it in items]
+        bs = [dg.make_bounds(it["bd"].a, it["bd"].b, it["bd"].a0) for it in items]
+        evb = [torch.empty(x.shape[1], dtype=torch.float64, device="cuda") for x in Xb]
+        rsb = [torch.empty_like(e) for e in evb]
+        evs = [torch.empty_like(e) for e in evb]
+        rss = [torch.empty_like(e) for e in evb]
+        Xo = [it["X0"] for it in items]
+        obs = [it["bd"] for it in items]
+        thetas = [None] * len(items)
+        for p_ in range(12):
+            dg.dftfe_batch_chfsi_pass(batch, Xb, [it["block"] for it in items], [it["deg"] for it in items], bb,
+                                      evb, rsb, prec)
+            for i, it in enumerate(items):
+                ham = it["sys"][1][1]
+                if p_ < 2 and it["cplx"]:
+                    dg.dftfe_chfsi_pass_z(ham, Xs[i], it["block"], it["deg"], bs[i], evs[i], rss[i], prec)
+                elif p_ < 2:
+                    dg.dftfe_chfsi_pass(ham, Xs[i], it["block"], it["deg"], bs[i], evs[i], rss[i], prec)
+                run = kpoint.chfsi_pass if it["cplx"] else oracle.chfsi_pass
+                Xo[i], _, thetas[i], _, obs[i] = run(it["oracle"], Xo[i], it["block"], it["deg"], obs[i])
+            torch.cuda.synchronize()
+            for i in range(len(items)):
+                if p_ < 2:
+                    assert torch.equal(Xb[i], Xs[i]), (p_, i)
+                    assert torch.equal(evb[i], evs[i]) and torch.equal(rsb[i], rss[i]), (p_, i)
+        for i, it in enumerate(items):
+            if it["deg"] == 0:          # never filtered: not the mixed scheme's converged regime
+                continue
+            n2 = evb[i].shape[0] // 2
+            assert np.abs(evb[i].cpu().numpy()[:n2] - thetas[i][:n2]).max() < 1e-6, i
+    finally:
+        dg.dftfe_batch_destroy(batch)
+        for it in items:
+            for mesh, ham in it["sys"]:
+                dg.dftfe_ham_destroy(ham)
+                dg.dftfe_mesh_destroy(mesh)
