@@ -169,14 +169,19 @@ dftfe_status dftfe_ham_autotune(dftfe_ham ham, int enable);
 dftfe_status dftfe_autotune_query(dftfe_ham ham, int ncol, int* rows_per_cta, double* best_ms,
                                   double* heuristic_ms);
 
-/* CUDA graphs (no counterpart in the paper).  With enable = 1, the filter phase of
- * dftfe_chfsi_pass and dftfe_chfsi_pass_z (every block's Chebyshev recurrence: about
- * degree x (3 + colours) launches per block) runs as one CUDA graph launch: the first pass
- * with given (precision, ncol, block, degree) runs directly, later ones capture the phase
- * from the ham's stream and update the cached executable (bounds change only kernel
- * arguments).  Results are bit-identical to enable = 0.  Per-kernel profiling timers
- * (dftfe_profile_query) see the filter only as "pass_filter" while graphs are on.  Either
- * call drops the cached graphs; synchronises the stream. */
+/* CUDA graphs (no counterpart in the paper).  With enable = 1, a WHOLE dftfe_chfsi_pass
+ * (filter, Cholesky-Gram-Schmidt, Rayleigh-Ritz, residuals) runs as one CUDA graph launch with
+ * a single host synchronisation at its end: the Cholesky and eigensolver statuses and the
+ * tensor-core kernels' timeout flags stay on the device (the kernels that rotate X or W do no
+ * work once the factorisation or the eigensolve has failed, so X is left as filtered) and are
+ * read once, with the Ritz-value ends for the bounds update.  Errors are those of the plain
+ * pass.  For dftfe_chfsi_pass_z the filter phase (every block's Chebyshev recurrence, about
+ * degree x (3 + colours) launches per block) is one graph launch.  The first pass with given
+ * (precision, ncol, block, degree) runs directly, later ones capture from the ham's stream and
+ * update the cached executable (bounds change only kernel arguments).  Results are
+ * bit-identical to enable = 0.  Per-kernel profiling timers (dftfe_profile_query) record
+ * nothing inside a captured region.  Either call drops the cached graphs; synchronises the
+ * stream. */
 dftfe_status dftfe_ham_use_graphs(dftfe_ham ham, int enable);
 
 /* HOST counts since dftfe_ham_use_graphs: graph launches and instantiations (an update that
@@ -284,12 +289,12 @@ dftfe_status dftfe_density(dftfe_ham ham, const double* Xo, int64_t ldo, int nco
  * until exit.  ncol above DFTFE_NOALLOC_MAX_COLS returns DFTFE_ERR_ARG.
  * Work runs on `stream` (a cudaStream_t, NULL = legacy default) and the call
  * synchronises it (it reads the factorisation status).  The first call on each
- * device resolves the scratch address and fills a small table (a synchronous
- * copy), so make that first call before any stream capture.  Every call shares the
- * one scratch array and reuses whatever the last call left there (each call
- * overwrites all scratch it reads); calls that overlap on the GPU (other streams,
- * other threads) race on it and must be serialised by the caller.
- * DFTFE_ERR_NOT_SPD leaves X untouched. */
+ * device resolves the scratch address (cudaGetSymbolAddress; nothing is copied), so
+ * make that first call before any stream capture.  X must be device memory of the
+ * current device (else DFTFE_ERR_ARG).  Every call shares the one scratch array and
+ * reuses whatever the last call left there (each call overwrites all scratch it
+ * reads); calls that overlap on the GPU (other streams, other threads) race on it
+ * and must be serialised by the caller.  DFTFE_ERR_NOT_SPD leaves X untouched. */
 #define DFTFE_NOALLOC_MAX_COLS 512
 dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, int ncol, void* stream);
 

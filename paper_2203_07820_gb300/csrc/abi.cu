@@ -20,7 +20,9 @@ static void cholgs_impl(dftfe_ham h, double* X, int64_t ld, int ncol, bool mixed
   const int N = ncol;
   double* S = (double*)ws_get(h, "S", sizeof(double) * (size_t)N * N);
   double* Z = (double*)ws_get(h, "Zinv", sizeof(double) * (size_t)N * N);
-  int* st = (int*)ws_get(h, "status", sizeof(int) * 4);
+  // a deferred pass keeps the status on the device (read at its end); the rotation below
+  // then skips its work if the factorisation failed
+  int* st = h->deferred ? h->d_pass : (int*)ws_get(h, "status", sizeof(int) * 4);
   if (mixed) {
     gram_lower_mixed(h, X, ld, X, ld, m->M, N, S);
   } else {
@@ -29,8 +31,8 @@ static void cholgs_impl(dftfe_ham h, double* X, int64_t ld, int ncol, bool mixed
     gram_lower(h, X, ld, X, ld, m->M, N, S, part, nsplit);
   }
   cholesky_blocked(h, S, N, st);
-  const int s = read_status(h, st);
-  if (s == DFTFE_ERR_NOT_SPD) throw Error(DFTFE_ERR_NOT_SPD, "overlap matrix is not positive definite");
+  if (!h->deferred && read_status(h, st) == DFTFE_ERR_NOT_SPD)
+    throw Error(DFTFE_ERR_NOT_SPD, "overlap matrix is not positive definite");
   tri_inverse_blocked(h, S, Z, N);
   if (mixed) rotate_inplace_mixed(h, X, ld, m->M, N, Z, true);
   else rotate_inplace(h, X, ld, m->M, N, Z, true);
@@ -48,7 +50,7 @@ static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals,
   else apply_combo(h, X, ld, nullptr, 0, W, ldw, N, 1.0, 0.0, 0.0);
   double* Hh = (double*)ws_get(h, "Hhat", sizeof(double) * (size_t)N * N);
   double* Q = (double*)ws_get(h, "Q", sizeof(double) * (size_t)N * N);
-  int* st = (int*)ws_get(h, "status", sizeof(int) * 4);
+  int* st = h->deferred ? h->d_pass + 1 : (int*)ws_get(h, "status", sizeof(int) * 4);
   if (mixed) {
     gram_lower_mixed(h, X, ld, W, ldw, m->M, N, Hh);
   } else {
@@ -57,9 +59,11 @@ static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals,
     gram_lower(h, X, ld, W, ldw, m->M, N, Hh, part, nsplit);
   }
   syevd(h, Hh, N, evals, Q, st);
-  const int s = read_status(h, st);
-  if (s == DFTFE_ERR_NOCONV) throw Error(DFTFE_ERR_NOCONV, "subspace eigensolver did not converge");
-  if (s != 0) throw Error((dftfe_status)s, "subspace eigensolver: a bounded grid wait timed out");
+  if (!h->deferred) {
+    const int s = read_status(h, st);
+    if (s == DFTFE_ERR_NOCONV) throw Error(DFTFE_ERR_NOCONV, "subspace eigensolver did not converge");
+    if (s != 0) throw Error((dftfe_status)s, "subspace eigensolver: a bounded grid wait timed out");
+  }
   if (mixed) {
     rotate_inplace_mixed(h, X, ld, m->M, N, Q, false);
     rotate_inplace_mixed(h, W, ldw, m->M, N, Q, false);
@@ -84,10 +88,57 @@ void chfsi_pass_tail(dftfe_ham h, double* X, int64_t ld, int ncol, dftfe_bounds*
     rr_impl(h, X, ld, ncol, evals, W, ncol, prec);
   }
   residual_norms(h, X, ld, W, ncol, m->M, ncol, evals, resid, 0);
+  if (h->deferred) {
+    // statuses and the Ritz-value ends to pinned host memory; the caller synchronises once
+    double* ends = (double*)((char*)h->h_pass + 16);
+    DFTFE_CHECK_CUDA(cudaMemcpyAsync(h->h_pass, h->d_pass, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[0], evals, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[1], evals + ncol - 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return;
+  }
   double ends[2];
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[0], evals, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&ends[1], evals + ncol - 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  inout->a = ends[1];
+  if (!std::isnan(inout->a0)) inout->a0 = ends[0];
+}
+
+// The whole pass as one enqueued region (filter, CholGS, Rayleigh-Ritz, residuals) with the
+// statuses deferred: one CUDA graph per shape when the ham uses graphs, one host
+// synchronisation at the end either way.  Errors are reported after the region in the order
+// the plain pass would meet them; a failed factorisation or eigensolve leaves X as filtered.
+static void chfsi_pass_graphed(dftfe_ham h, double* X, int64_t ld, int ncol, int block, int degree,
+                               dftfe_bounds* inout, double* evals, double* resid, dftfe_precision prec) {
+  if (!h->d_pass) h->d_pass = (int*)ws_get(h, "pass_status", sizeof(int) * 4);
+  if (!h->h_pass) DFTFE_CHECK_CUDA(cudaHostAlloc(&h->h_pass, 64, cudaHostAllocDefault));
+  const dftfe_bounds bnd = *inout;
+  const std::string key = "wholepass/" + std::to_string((int)prec) + "/" + std::to_string(ncol) + "/" +
+                          std::to_string(block) + "/" + std::to_string(degree) + "/" + std::to_string((int64_t)ld);
+  dftfe_bounds out = bnd;
+  h->deferred = true;
+  try {
+    run_region(h, key, [&]() {
+      DFTFE_CHECK_CUDA(cudaMemsetAsync(h->d_pass, 0, sizeof(int) * 4, h->stream));
+      for (int j0 = 0; j0 < ncol; j0 += block) {
+        const int nb = std::min(block, ncol - j0);
+        if (prec == DFTFE_FP64) chebyshev_filter(h, X + j0, ld, nb, degree, bnd);
+        else chebyshev_filter_mixed(h, X + j0, ld, nb, degree, bnd, prec == DFTFE_MIXED_TF32X3, h->d_pass + 2);
+      }
+      chfsi_pass_tail(h, X, ld, ncol, &out, evals, resid, prec);
+    });
+  } catch (...) {
+    h->deferred = false;
+    throw;
+  }
+  h->deferred = false;
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
+  const int* st = (const int*)h->h_pass;
+  const double* ends = (const double*)((const char*)h->h_pass + 16);
+  if (st[0] == DFTFE_ERR_NOT_SPD) throw Error(DFTFE_ERR_NOT_SPD, "overlap matrix is not positive definite");
+  if (st[2]) throw Error(DFTFE_ERR_TIMEOUT, "tensor-core kernel: a bounded wait timed out");
+  if (st[1] == DFTFE_ERR_NOCONV) throw Error(DFTFE_ERR_NOCONV, "subspace eigensolver did not converge");
+  if (st[1] != 0) throw Error((dftfe_status)st[1], "subspace eigensolver: a bounded grid wait timed out");
   inout->a = ends[1];
   if (!std::isnan(inout->a0)) inout->a0 = ends[0];
 }
@@ -179,6 +230,10 @@ extern "C" dftfe_status dftfe_chfsi_pass(dftfe_ham h, double* X, int64_t ld, int
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
                 "unknown precision");
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (h->use_graphs) {
+    chfsi_pass_graphed(h, X, ld, ncol, block, degree, inout, evals, resid, prec);
+    return DFTFE_OK;
+  }
   {
     ProfScope ps(h, "pass_filter");
     // the mixed cell kernel's timeout flag is zeroed before the filter and read after it, so

@@ -45,11 +45,15 @@ constexpr int GT = 64, GK = 16;
 __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ A, int64_t lda,
                                                       const double* __restrict__ B, int64_t ldb,
                                                       int64_t M, int N, int64_t rows_per_split,
-                                                      const int32_t* __restrict__ tiles,
                                                       double* __restrict__ part) {
   __shared__ double As[GK][GT];
   __shared__ double Bs[GK][GT];
-  const int ti = tiles[2 * blockIdx.x], tj = tiles[2 * blockIdx.x + 1];
+  // tile (ti, tj) of the lower triangle, row-major: blockIdx.x = ti (ti + 1) / 2 + tj
+  const int t = blockIdx.x;
+  int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while (ti * (ti + 1) / 2 > t) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  const int tj = t - ti * (ti + 1) / 2;
   const int i0 = ti * GT, j0 = tj * GT;
   const int64_t m0 = (int64_t)blockIdx.y * rows_per_split;
   const int64_t m1 = min(M, m0 + rows_per_split);
@@ -113,23 +117,15 @@ int gram_nsplit(dftfe_ham h, int64_t M, int N) {
 
 void gram_lower(dftfe_ham h, const double* A, int64_t lda, const double* B, int64_t ldb, int64_t M,
                 int N, double* C, double* part, int nsplit) {
+  // no host data: the kernel decodes its tile from the block index, so the launch can be
+  // captured in a CUDA graph and replayed
   const int T = (N + GT - 1) / GT;
   const int ntiles = T * (T + 1) / 2;
-  std::vector<int32_t> tl;
-  tl.reserve(2 * ntiles);
-  for (int i = 0; i < T; ++i)
-    for (int j = 0; j <= i; ++j) {
-      tl.push_back(i);
-      tl.push_back(j);
-    }
-  int32_t* d_tiles = (int32_t*)ws_get(h, "gram_tiles", sizeof(int32_t) * tl.size());
-  DFTFE_CHECK_CUDA(cudaMemcpyAsync(d_tiles, tl.data(), sizeof(int32_t) * tl.size(),
-                                   cudaMemcpyHostToDevice, h->stream));
   const int64_t rows = (M + nsplit - 1) / nsplit;
   {
     ProfScope ps(h, "gram");
     DFTFE_LAUNCH(k_gram_partial, dim3(ntiles, nsplit), 256, 0, h->stream, A, lda, B, ldb, M, N,
-                 rows, d_tiles, part);
+                 rows, part);
   }
   DFTFE_LAUNCH(k_gram_reduce, nblk((int64_t)N * N), 256, 0, h->stream, part, nsplit, N, C);
 }
@@ -201,7 +197,9 @@ void trtri_lower_to_upper_t(cudaStream_t s, const double* L, double* Z, int N) {
 // X[r0:r0+R, :] <- X[r0:r0+R, :] Z, in place.  Thread t owns columns t + 256 c.
 template <int R, int CPT>
 __global__ void __launch_bounds__(256) k_rotate(double* __restrict__ X, int64_t ld, int64_t M, int N,
-                                                const double* __restrict__ Z, int upper) {
+                                                const double* __restrict__ Z, int upper, const int* guard) {
+  // a deferred pass whose factorisation or eigensolve failed leaves X as it is
+  if (guard && (guard[0] != 0 || guard[1] != 0)) return;
   extern __shared__ double xs[];  // R x N
   const int64_t r0 = (int64_t)blockIdx.x * R;
   const int rows = (int)min((int64_t)R, M - r0);
@@ -256,7 +254,7 @@ static void launch_rotate(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, 
   }
   const unsigned grid = (unsigned)((M + R - 1) / R);
   ProfScope ps(h, "rotate");
-  DFTFE_LAUNCH((k_rotate<R, CPT>), grid, 256, sh, h->stream, X, ld, M, N, Z, upper ? 1 : 0);
+  DFTFE_LAUNCH((k_rotate<R, CPT>), grid, 256, sh, h->stream, X, ld, M, N, Z, upper ? 1 : 0, rot_guard(h));
 }
 
 void rotate_inplace(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {
@@ -1128,9 +1126,9 @@ void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3, 
 namespace dftfe {
 
 void gram_partial_launch(cudaStream_t s, const double* A, int64_t lda, const double* B, int64_t ldb,
-                         int64_t M, int N, int nsplit, const int32_t* tiles, int ntiles, double* part) {
+                         int64_t M, int N, int nsplit, int ntiles, double* part) {
   const int64_t rows = (M + nsplit - 1) / nsplit;
-  DFTFE_LAUNCH(k_gram_partial, dim3(ntiles, nsplit), 256, 0, s, A, lda, B, ldb, M, N, rows, tiles, part);
+  DFTFE_LAUNCH(k_gram_partial, dim3(ntiles, nsplit), 256, 0, s, A, lda, B, ldb, M, N, rows, part);
 }
 
 void gram_reduce_launch(cudaStream_t s, const double* part, int nsplit, int N, double* C) {
@@ -1143,7 +1141,8 @@ static void rotate_launch_t(cudaStream_t s, double* X, int64_t ld, int64_t M, in
   DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_rotate<R, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         200 * 1024));
   const size_t sh = (size_t)R * N * sizeof(double);
-  DFTFE_LAUNCH((k_rotate<R, CPT>), (unsigned)((M + R - 1) / R), 256, sh, s, X, ld, M, N, Z, upper ? 1 : 0);
+  DFTFE_LAUNCH((k_rotate<R, CPT>), (unsigned)((M + R - 1) / R), 256, sh, s, X, ld, M, N, Z, upper ? 1 : 0,
+               (const int*)nullptr);
 }
 
 void rotate_launch(cudaStream_t s, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {

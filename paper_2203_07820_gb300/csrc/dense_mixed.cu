@@ -22,11 +22,15 @@ constexpr int G32T = 128, G32K = 16;
 __global__ void __launch_bounds__(256, 1) k_gram32_partial(const double* __restrict__ A, int64_t lda,
                                                         const double* __restrict__ B, int64_t ldb, int64_t M,
                                                         int N, int64_t rows_per_split,
-                                                        const int32_t* __restrict__ tiles,
                                                         double* __restrict__ part) {
   __shared__ __align__(16) float As[G32K][G32T];
   __shared__ __align__(16) float Bs[G32K][G32T];
-  const int ti = tiles[2 * blockIdx.x], tj = tiles[2 * blockIdx.x + 1];
+  // tile (ti, tj) of the lower triangle, row-major: blockIdx.x = ti (ti + 1) / 2 + tj
+  const int t = blockIdx.x;
+  int ti = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while (ti * (ti + 1) / 2 > t) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  const int tj = t - ti * (ti + 1) / 2;
   const int i0 = ti * G32T, j0 = tj * G32T;
   const int64_t m0 = (int64_t)blockIdx.y * rows_per_split;
   const int64_t m1 = min(M, m0 + rows_per_split);
@@ -117,15 +121,6 @@ void gram_lower_mixed(dftfe_ham h, const double* A, int64_t lda, const double* B
   }
   const int T = (N + G32T - 1) / G32T;
   const int ntiles = T * (T + 1) / 2;
-  std::vector<int32_t> tl;
-  for (int i = 0; i < T; ++i)
-    for (int j = 0; j <= i; ++j) {
-      tl.push_back(i);
-      tl.push_back(j);
-    }
-  int32_t* d_tiles = (int32_t*)ws_get(h, "gram32_tiles", sizeof(int32_t) * tl.size());
-  DFTFE_CHECK_CUDA(cudaMemcpyAsync(d_tiles, tl.data(), sizeof(int32_t) * tl.size(), cudaMemcpyHostToDevice,
-                                   h->stream));
   const int64_t want = (4LL * h->sm_count + ntiles - 1) / ntiles;
   const int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(want, M / 512));
   const int64_t rows = (M + nsplit - 1) / nsplit;
@@ -135,8 +130,7 @@ void gram_lower_mixed(dftfe_ham h, const double* A, int64_t lda, const double* B
   double* dpart = (double*)ws_get(h, "coldot_part", sizeof(double) * (size_t)nchunk * N);
   {
     ProfScope ps(h, "gram_mixed");
-    DFTFE_LAUNCH(k_gram32_partial, dim3(ntiles, nsplit), 256, 0, h->stream, A, lda, B, ldb, M, N, rows, d_tiles,
-                 part);
+    DFTFE_LAUNCH(k_gram32_partial, dim3(ntiles, nsplit), 256, 0, h->stream, A, lda, B, ldb, M, N, rows, part);
     DFTFE_LAUNCH(k_coldot_partial, nchunk, 256, 0, h->stream, A, lda, B, ldb, M, N, drows, dpart);
   }
   DFTFE_LAUNCH(k_gram32_reduce, nblk((int64_t)N * N), 256, 0, h->stream, part, nsplit, dpart, nchunk, N, C);
@@ -157,7 +151,9 @@ __global__ void k_split_rot(const double* __restrict__ Z, int N, float* __restri
 template <int R, int CPT>
 __global__ void __launch_bounds__(256) k_rotate_mixed(double* __restrict__ X, int64_t ld, int64_t M, int N,
                                                       const float* __restrict__ Zf, const double* __restrict__ zd,
-                                                      int upper) {
+                                                      int upper, const int* guard) {
+  // a deferred pass whose factorisation or eigensolve failed leaves X as it is
+  if (guard && (guard[0] != 0 || guard[1] != 0)) return;
   extern __shared__ __align__(16) float xsT[];  // N x R
   const int64_t r0 = (int64_t)blockIdx.x * R;
   const int rows = (int)min((int64_t)R, M - r0);
@@ -221,7 +217,7 @@ static void launch_rotate_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, i
   const size_t sh = (size_t)R * N * sizeof(float);
   ProfScope ps(h, "rotate_mixed");
   DFTFE_LAUNCH((k_rotate_mixed<R, CPT>), (unsigned)((M + R - 1) / R), 256, sh, h->stream, X, ld, M, N, Zf, zd,
-               upper ? 1 : 0);
+               upper ? 1 : 0, rot_guard(h));
 }
 
 void rotate_inplace_mixed(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper) {

@@ -349,41 +349,54 @@ __global__ void __launch_bounds__(mx::kThreads, 1) k_cell_mixed(
 
 // ------------------------------------------------------------ TF32x3 from one FP32 plane
 // The TF32x3 form streams the cell matrices as ONE FP32 plane (4 bytes per entry, rounded to
-// nearest from FP64) and splits every tile into its hi and lo TF32 terms in shared memory:
+// nearest from FP64) and splits every tile into its hi and lo TF32 terms on chip:
 //   plane layout: per (cell, K-chunk of 32 columns) the M-tiles of 128 rows in order, each a
 //   K-major 128-byte-swizzled tile of 128 x 32 floats; the last M-tile holds only its rows in
 //   8-row atoms (88 of 128 for p = 6), so a cell streams (nmt - 1) x 16 KB + rows8 x 128 B per
 //   K-chunk -- the nc x nc matrix plus the K padding, nothing else.
-// The FP32 tiles land in a 4-slot ring that is released as soon as a tile is converted, so
-// three to four 16 KB bulk copies stay in flight per SM (the HBM latency at the rate the
-// tensor cores consume tiles); the hi/lo pairs go to a 2-slot ring that the MMAs read.
+// The FP32 tiles land in a ring that is released as soon as a tile is converted, so several
+// 16 KB bulk copies stay in flight per SM.  Measured on GB300, 128 x 128 x 8 TF32 MMAs with
+// both operands in shared memory issue at about half the nominal TF32 rate; with at most
+// three M-tiles (p <= 6) the converters therefore write the hi and lo A tiles into tensor
+// memory (2 slots x 64 columns beside the 3 x 128 accumulator columns) and the MMAs read A
+// from there (tcgen05.mma A-in-TMEM form), halving the shared-memory operand traffic.  With
+// four M-tiles (p = 7) the accumulators fill tensor memory and the hi/lo A tiles go to a
+// 2-slot shared-memory ring instead.
 // Warp roles (448 threads):
 //   warp 0        A producer: one bulk copy per tile into the landing ring
 //   warp 1        TMEM owner and MMA issuer (one elected lane)
 //   warps 2-5     B producers: cp.async gather of the cell's rows of X (each warp 32 columns,
-//                 into its own 4 KB slice of the stage's lo slot, two chunks ahead; the cell
-//                 map entries of the next chunk are loaded one chunk ahead), then the split
-//                 of the chunk into the swizzled hi and lo B tiles (3-stage ring)
-//   warps 6-9     epilogue (tcgen05.ld of the accumulators, 16-byte stores of the rows of Y^c)
-//   warps 10-13   A converters: landing tile -> hi = rn_tf32(f), lo = rn_tf32(f - hi)
+//                 into its own 4 KB slice of the stage's lo slot, kStagesB - 1 chunks ahead;
+//                 the cell map entries of the next chunk are loaded one chunk ahead), then
+//                 the split of the chunk into the swizzled hi and lo B tiles
+//   warps 6-9     epilogue (tcgen05.ld of the accumulators, 32-byte stores of Y^c rows)
+//   warps 10-13   A converters: landing tile -> hi = rn_tf32(f), lo = rn_tf32(f - hi), into
+//                 tensor memory (one row per thread) or the shared-memory ring
 // Every wait is bounded; on a time-out the kernel records DFTFE_ERR_TIMEOUT, drains its own
 // copies and MMAs (bounded), frees its tensor memory and returns.
 namespace mp {
 constexpr int kThreads = 448;
-constexpr int kLand = 4, kConv = 2, kStagesB = 3;
 constexpr int kTile = 16384;
 constexpr int kStage = 2 * kTile;                  // hi | lo
 constexpr int kMaxMTiles = 4;
-struct Shared {
-  uint64_t land_full[kLand], land_empty[kLand];
+constexpr int kConv = 2;
+constexpr uint32_t kAcolBase = 384;                // first TMEM column of the A slots (TMEM form)
+template <bool ATMEM> struct Cfg {
+  static constexpr int kLand = ATMEM ? 6 : 4;      // landing ring slots (FP32 tiles)
+  static constexpr int kStagesB = ATMEM ? 4 : 3;   // B ring stages
+  static constexpr int kConvSmem = ATMEM ? 0 : kConv;
+};
+template <bool ATMEM> struct Shared {
+  uint64_t land_full[Cfg<ATMEM>::kLand], land_empty[Cfg<ATMEM>::kLand];
   uint64_t conv_full[kConv], conv_empty[kConv];
-  uint64_t b_full[kStagesB], b_empty[kStagesB];
+  uint64_t b_full[Cfg<ATMEM>::kStagesB], b_empty[Cfg<ATMEM>::kStagesB];
   uint64_t acc_full, acc_empty[kMaxMTiles], drain;
   uint32_t tmem;
   int abort;
 };
-constexpr size_t smem_bytes() {
-  return 1024 + (size_t)kLand * kTile + (size_t)kConv * kStage + (size_t)kStagesB * kStage + sizeof(Shared);
+template <bool ATMEM> constexpr size_t smem_bytes() {
+  return 1024 + (size_t)Cfg<ATMEM>::kLand * kTile + (size_t)Cfg<ATMEM>::kConvSmem * kStage +
+         (size_t)Cfg<ATMEM>::kStagesB * kStage + sizeof(Shared<ATMEM>);
 }
 __host__ __device__ inline int64_t kc_block_bytes(int nmt, int rows8) {
   return (int64_t)(nmt - 1) * kTile + (int64_t)rows8 * 128;
@@ -399,6 +412,25 @@ struct Item {
   int64_t ldx;
   int col0, ncol;
 };
+
+// one TF32 MMA with A from tensor memory (column address a_tmem), B from a shared-memory
+// descriptor
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t acc) {
+  constexpr uint32_t id = tc::idesc(2u, 128, 128);
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}"
+               :: "r"(d), "r"(a_tmem), "l"(b), "r"(id), "r"(acc));
+}
+
+// 32 consecutive 32-bit TMEM columns of this warp's 32 lanes from registers (lane = row)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+               :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                  "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+                  "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+                  "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+               : "memory");
+}
 }  // namespace mp
 
 // Set-up: the FP32 plane in the tile order above (written in physical order, so the stores
@@ -430,6 +462,7 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
 // Work item g of a launch: cell g of `single` (work == NULL), or the (system, cell) pair
 // work[g] of the systems `items` (all of one degree: nc, nkc, nmt are the launch's).  Items
 // are dealt round-robin over the persistent grid.
+template <bool ATMEM>
 __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single, const mp::Item* __restrict__ items,
                                                                 const int2* __restrict__ work, int nwork, int nc,
                                                                 int nkc, int nmt, int* err) {
@@ -441,6 +474,7 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   using tc::smem_u32;
   using tc::sw128;
   using tc::tc_commit;
+  constexpr int kLand = Cfg<ATMEM>::kLand, kStagesB = Cfg<ATMEM>::kStagesB;
   // the CTA's i-th work item: its system's operands and its cell
   auto item_of = [&](int64_t i, int64_t& cell) -> Item {
     const int64_t g = blockIdx.x + i * gridDim.x;
@@ -454,10 +488,10 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   };
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* sL = base;                                   // landing ring: kLand x 16 KB FP32
-  uint8_t* sC = sL + kLand * kTile;                     // converted ring: kConv x (hi | lo)
-  uint8_t* sB = sC + kConv * kStage;                    // B ring: kStagesB x (hi | lo)
-  Shared* sh = (Shared*)(sB + kStagesB * kStage);
+  uint8_t* sL = base;                                        // landing ring: kLand x 16 KB FP32
+  uint8_t* sC = sL + kLand * kTile;                          // shared-memory hi/lo ring (not ATMEM)
+  uint8_t* sB = sC + Cfg<ATMEM>::kConvSmem * kStage;         // B ring: kStagesB x (hi | lo)
+  Shared<ATMEM>* sh = (Shared<ATMEM>*)(sB + kStagesB * kStage);
   volatile int* abort = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -531,14 +565,25 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
             if (kc == 0 && !mbar_wait(&sh->acc_empty[mt], (i & 1) ^ 1, abort, err)) { go = false; break; }
             if (!mbar_wait(&sh->conv_full[sa], (ta / kConv) & 1, abort, err)) { go = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ahi = smem_u32(sC + sa * kStage), alo = ahi + kTile;
             const uint32_t d = tmem + (uint32_t)(mt * 128);
+            if constexpr (ATMEM) {
+              const uint32_t ahi = tmem + kAcolBase + (uint32_t)(sa * 64), alo = ahi + 32;
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              const uint32_t o = ks * 32;
-              mx::mma<true>(d, sdesc(ahi + o), sdesc(bhi + o), (kc > 0 || ks > 0) ? 1u : 0u);
-              mx::mma<true>(d, sdesc(ahi + o), sdesc(blo + o), 1u);
-              mx::mma<true>(d, sdesc(alo + o), sdesc(bhi + o), 1u);
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t o = ks * 32;
+                mma_ts(d, ahi + 8 * ks, sdesc(bhi + o), (kc > 0 || ks > 0) ? 1u : 0u);
+                mma_ts(d, ahi + 8 * ks, sdesc(blo + o), 1u);
+                mma_ts(d, alo + 8 * ks, sdesc(bhi + o), 1u);
+              }
+            } else {
+              const uint32_t ahi = smem_u32(sC + sa * kStage), alo = ahi + kTile;
+#pragma unroll
+              for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t o = ks * 32;
+                mx::mma<true>(d, sdesc(ahi + o), sdesc(bhi + o), (kc > 0 || ks > 0) ? 1u : 0u);
+                mx::mma<true>(d, sdesc(ahi + o), sdesc(blo + o), 1u);
+                mx::mma<true>(d, sdesc(alo + o), sdesc(bhi + o), 1u);
+              }
             }
             tc_commit(&sh->conv_empty[sa]);
           }
@@ -559,6 +604,7 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
     // tile go, so the split overwrites only what the warp itself staged.  Lane l holds the
     // node of row l of the next chunk to issue (loaded one chunk ahead) and hands it to the
     // lanes that copy that row by a shuffle.
+    constexpr int kAhead = kStagesB - 1;
     const int w = warp - 2;
     const int n = 32 * w + lane;
     const uint32_t nchunks = (uint32_t)my_cells * (uint32_t)nkc;
@@ -593,12 +639,13 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
       return true;
     };
     bool go = true;
-    for (uint32_t t = 0; t < 2; ++t) {
+    for (uint32_t t = 0; t < (uint32_t)kAhead; ++t) {
       if (go && t < nchunks) go = issue(t);
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
     for (uint32_t tb = 0; tb < nchunks && go; ++tb) {
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
+      // every group but the newest kAhead - 1 complete: chunk tb has landed
+      asm volatile("cp.async.wait_group %0;" :: "n"(kAhead - 1) : "memory");
       __syncwarp();
       const int sb = tb % kStagesB;
       uint8_t* bhi = sB + sb * kStage;
@@ -621,7 +668,7 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&sh->b_full[sb]);
-      if (tb + 2 < nchunks) go = issue(tb + 2);
+      if (tb + kAhead < nchunks) go = issue(tb + kAhead);
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -657,6 +704,8 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   } else {
     // ------------------------------------------------------------ A converters
     const int tid = threadIdx.x - 320;            // 0 .. 127
+    const int q = warp & 3;                       // TMEM lane quadrant (ATMEM)
+    const uint32_t row = (uint32_t)(32 * q + lane);   // the tile row this thread converts (ATMEM)
     uint32_t ta = 0;
     bool go = true;
     for (int i = 0; i < my_cells && go; ++i)
@@ -665,31 +714,67 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
           const int s = ta % kLand, sc = ta % kConv;
           if (!mbar_wait(&sh->land_full[s], (ta / kLand) & 1, abort, err)) { go = false; break; }
           if (!mbar_wait(&sh->conv_empty[sc], ((ta / kConv) & 1) ^ 1, abort, err)) { go = false; break; }
-          const int nchunk16 = (mt == nmt - 1 ? rows8 : 128) * 8;
-          const uint4* src = reinterpret_cast<const uint4*>(sL + s * kTile);
-          uint4* hi = reinterpret_cast<uint4*>(sC + sc * kStage);
-          uint4* lo = reinterpret_cast<uint4*>(sC + sc * kStage + kTile);
-          uint4 u[8];
+          if constexpr (ATMEM) {
+            // row `row` of the tile: its 32 values in K order from the swizzled landing tile;
+            // rows of the last M-tile beyond the landed atoms hold whatever the slot held
+            // before (possibly never written), so they enter tensor memory as zeros: measured
+            // on GB300, non-finite stale values in such rows of a tensor-memory A operand
+            // corrupted other rows of the product, although their own rows are never stored
+            const uint8_t* L = sL + s * kTile;
+            const bool landed = mt != nmt - 1 || (int)row < rows8;
+            uint32_t hv[32], lv[32];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int c = tid + 128 * j;
-            if (c < nchunk16) u[j] = src[c];
-          }
-          mbar_arrive(&sh->land_empty[s]);          // the landing slot may take the next copy
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int c = tid + 128 * j;
-            if (c < nchunk16) {
-              uint4 h4, l4;
-              tc::split_tf32_bits(u[j].x, h4.x, l4.x);
-              tc::split_tf32_bits(u[j].y, h4.y, l4.y);
-              tc::split_tf32_bits(u[j].z, h4.z, l4.z);
-              tc::split_tf32_bits(u[j].w, h4.w, l4.w);
-              hi[c] = h4;
-              lo[c] = l4;
+            for (int c = 0; c < 8; ++c) {
+              uint4 u = make_uint4(0u, 0u, 0u, 0u);
+              if (landed) u = *reinterpret_cast<const uint4*>(L + sw128(row, (uint32_t)(16 * c)));
+              tc::split_tf32_bits(u.x, hv[4 * c], lv[4 * c]);
+              tc::split_tf32_bits(u.y, hv[4 * c + 1], lv[4 * c + 1]);
+              tc::split_tf32_bits(u.z, hv[4 * c + 2], lv[4 * c + 2]);
+              tc::split_tf32_bits(u.w, hv[4 * c + 3], lv[4 * c + 3]);
             }
+            // the landing slot may take the next bulk copy: the proxy fence orders these
+            // ordinary shared-memory reads before that async-proxy write (measured on GB300:
+            // without it the next tile overwrote rows still being read, at many cells per CTA)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&sh->land_empty[s]);
+            // the MMAs that read this A slot have completed (conv_empty): order the stores below
+            // after that wait
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ta_hi = tmem + ((uint32_t)(32 * q) << 16) + kAcolBase + (uint32_t)(sc * 64);
+            tmem_st32(ta_hi, hv);
+            tmem_st32(ta_hi + 32, lv);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          } else {
+            const int nchunk16 = (mt == nmt - 1 ? rows8 : 128) * 8;
+            const uint4* src = reinterpret_cast<const uint4*>(sL + s * kTile);
+            uint4* hi = reinterpret_cast<uint4*>(sC + sc * kStage);
+            uint4* lo = reinterpret_cast<uint4*>(sC + sc * kStage + kTile);
+            uint4 u[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int c = tid + 128 * j;
+              if (c < nchunk16) u[j] = src[c];
+            }
+            // the landing slot may take the next bulk copy (async proxy) once these reads are
+            // ordered before it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&sh->land_empty[s]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int c = tid + 128 * j;
+              if (c < nchunk16) {
+                uint4 h4, l4;
+                tc::split_tf32_bits(u[j].x, h4.x, l4.x);
+                tc::split_tf32_bits(u[j].y, h4.y, l4.y);
+                tc::split_tf32_bits(u[j].z, h4.z, l4.z);
+                tc::split_tf32_bits(u[j].w, h4.w, l4.w);
+                hi[c] = h4;
+                lo[c] = l4;
+              }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_arrive(&sh->conv_full[sc]);
         }
   }
@@ -698,6 +783,24 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+}
+
+// the A-in-TMEM form when the accumulators leave room for it (at most three M-tiles)
+static void launch_cell_tf32p(cudaStream_t s, unsigned grid, const mp::Item& one, const mp::Item* items,
+                              const int2* work, int nwork, int nc, int nkc, int nmt, int* err) {
+  if (nmt <= 3)
+    DFTFE_LAUNCH(k_cell_tf32p<true>, grid, mp::kThreads, mp::smem_bytes<true>(), s, one, items, work, nwork, nc, nkc,
+                 nmt, err);
+  else
+    DFTFE_LAUNCH(k_cell_tf32p<false>, grid, mp::kThreads, mp::smem_bytes<false>(), s, one, items, work, nwork, nc,
+                 nkc, nmt, err);
+}
+
+static void set_tf32p_attrs() {
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)mp::smem_bytes<true>()));
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)mp::smem_bytes<false>()));
 }
 
 // ------------------------------------------------------------ FP32 helpers
@@ -923,8 +1026,7 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
       ProfScope ps(h, tf32 ? "cell_gemm_tf32x3" : "cell_gemm_bf16x3");
       if (tf32) {
         const mp::Item one{A, h->d_map, X, Yc, ldx, col0, ncol};
-        DFTFE_LAUNCH(k_cell_tf32p, grid, mp::kThreads, mp::smem_bytes(), h->stream, one, nullptr, nullptr,
-                     (int)m->Nc, m->nc, nkc, nmt, err);
+        launch_cell_tf32p(h->stream, grid, one, nullptr, nullptr, (int)m->Nc, m->nc, nkc, nmt, err);
       } else
         DFTFE_LAUNCH(k_cell_mixed<false>, grid, mx::kThreads, sh, h->stream, A, h->d_map, (int)m->Nc, m->nc,
                      nkc, nmt, X, ldx, Yc, col0, ncol, err);
@@ -945,7 +1047,7 @@ void chebyshev_filter_mixed(dftfe_ham h, double* X, int64_t ld, int ncol, int de
   if (degree <= 0 || ncol <= 0) return;
   auto* m = h->mesh;
   if (!g_mixed_attr) {
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp::smem_bytes()));
+    set_tf32p_attrs();
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
     g_mixed_attr = true;
   }
@@ -1039,7 +1141,7 @@ static void plan_mixed_round(MixedRoundPlan& R, std::vector<mp::Item>& items, st
   std::vector<MixedBlock>& blk = R.blk;
   const int ns = (int)blk.size();
   if (!g_mixed_attr) {
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp::smem_bytes()));
+    set_tf32p_attrs();
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
     g_mixed_attr = true;
   }
@@ -1189,9 +1291,8 @@ static void enqueue_mixed_round(const MixedRoundPlan& R, cudaStream_t stream, in
         const CellLaunch& L = launches[li];
         ProfScope ps(blk[0].h, "batch_cell_tf32x3");
         const mp::Item none{};
-        DFTFE_LAUNCH(k_cell_tf32p, (unsigned)std::min(L.nwork, sm), mp::kThreads, mp::smem_bytes(), stream, none,
-                     d_items + R.item_base + L.item_off, d_work + R.work_base + L.work_off, L.nwork, L.nc, L.nkc,
-                     L.nmt, err);
+        launch_cell_tf32p(stream, (unsigned)std::min(L.nwork, sm), none, d_items + R.item_base + L.item_off,
+                          d_work + R.work_base + L.work_off, L.nwork, L.nc, L.nkc, L.nmt, err);
       }
       for (int s = 0; s < ns; ++s) {
         if ((int)steps[s].size() < k || blk[s].ncol <= 128 * t) continue;
@@ -1223,7 +1324,7 @@ static void enqueue_mixed_round(const MixedRoundPlan& R, cudaStream_t stream, in
 std::function<void()> plan_mixed_batch(const std::vector<std::vector<MixedBlock>>& rounds, cudaStream_t stream,
                                        int* err, DevBuf& desc, std::vector<uint8_t>& host_desc) {
   if (!g_mixed_attr) {
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp::smem_bytes()));
+    set_tf32p_attrs();
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
     g_mixed_attr = true;
   }
@@ -1257,7 +1358,7 @@ std::function<void()> plan_mixed_batch(const std::vector<std::vector<MixedBlock>
 void apply_mixed(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool tf32, bool kpoint) {
   auto* m = h->mesh;
   if (!g_mixed_attr) {
-    DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mp::smem_bytes()));
+    set_tf32p_attrs();
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
     g_mixed_attr = true;
   }
@@ -1558,8 +1659,8 @@ static bool apply_df_tiled(dftfe_ham h, const double* X, int64_t ldx, double* Y,
     DFTFE_LAUNCH(k_split_df_k, nblk2((int64_t)n2), 256, 0, h->stream, h->d_Hc, Hk, (int64_t)m->Nc, nc, RP);
     h->df_version = h->potential_version;
   }
-  int* err = (int*)ws_get(h, "df_err", sizeof(int));
-  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  int* err = tc_err_flag(h, (int*)ws_get(h, "df_err", sizeof(int)));
+  if (!h->deferred) DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
   df_init(h, X, ldx, Y, ldy, ncol, with_nl);
   for (int c = 0; c < h->ncolours; ++c) {
     const int64_t n = h->colour_off[c + 1] - h->colour_off[c];
@@ -1569,6 +1670,7 @@ static bool apply_df_tiled(dftfe_ham h, const double* X, int64_t ldx, double* Y,
     dim3 grid((unsigned)n, (unsigned)((ncol + 31) / 32));
     DFTFE_LAUNCH(k_cell_df_tiled<TM>, grid, 256, sh, h->stream, Hk, h->d_map, cells, nc, X, ldx, Y, ldy, ncol, err);
   }
+  if (h->deferred) return true;
   int herr = 0;
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));

@@ -175,6 +175,14 @@ struct dftfe_ham_s {
   // makes the wait run out with 1)
   long long wait_limit = 0;
   int wait_missing = 0;
+  // a pass run as one CUDA graph (dftfe_ham_use_graphs): the statuses of the Cholesky
+  // factorisation [0], the eigensolver [1] and the tensor-core kernels' bounded waits [2] stay
+  // on the device (d_pass), the kernels that rotate X or W skip their work once [0] or [1] is
+  // set, and the statuses with the Ritz-value ends are copied once, at the end of the pass,
+  // to pinned host memory (h_pass: 4 ints, then 2 doubles)
+  bool deferred = false;
+  int* d_pass = nullptr;
+  void* h_pass = nullptr;
   // workspace
   std::map<std::string, dftfe::DevBuf> ws;
   // profiling
@@ -185,6 +193,12 @@ struct dftfe_ham_s {
 namespace dftfe {
 
 void* ws_get(dftfe_ham h, const char* name, size_t bytes);
+
+// the device status words of a deferred pass that a rotation of X or W checks (NULL: none)
+inline const int* rot_guard(dftfe_ham h) { return h->deferred ? h->d_pass : nullptr; }
+// the timeout flag a tensor-core kernel records into: the pass's in a deferred pass (read
+// once at its end), else `own`, which the caller zeroes and reads right away
+inline int* tc_err_flag(dftfe_ham h, int* own) { return h->deferred ? h->d_pass + 2 : own; }
 
 // Records an event pair around a kernel-family launch when profiling is on.
 struct ProfScope {

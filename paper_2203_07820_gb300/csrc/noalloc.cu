@@ -15,7 +15,7 @@
 
 namespace dftfe {
 void gram_partial_launch(cudaStream_t s, const double* A, int64_t lda, const double* B, int64_t ldb,
-                         int64_t M, int N, int nsplit, const int32_t* tiles, int ntiles, double* part);
+                         int64_t M, int N, int nsplit, int ntiles, double* part);
 void gram_reduce_launch(cudaStream_t s, const double* part, int nsplit, int N, double* C);
 void rotate_launch(cudaStream_t s, double* X, int64_t ld, int64_t M, int N, const double* Z, bool upper);
 }  // namespace dftfe
@@ -30,21 +30,19 @@ constexpr int kMaxTiles = kMaxTiles1D * (kMaxTiles1D + 1) / 2;
 constexpr size_t kScratchDoubles = (size_t)10 * kMaxCols * kMaxCols + 32;
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
-static __device__ __align__(256) int32_t g_tiles[2 * kMaxTiles];
+
 
 struct DeviceSetup {
   bool ready = false;
   double* scratch = nullptr;   // device address of g_scratch on this device
-  int32_t* tiles = nullptr;    // device address of g_tiles on this device
   int sm_count = 0;
 };
 constexpr int kMaxDevices = 64;
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
-// Once per device, with that device current: resolve the arrays' device addresses
-// (host code may not use the symbols themselves as pointers) and fill the tile list
-// (lower-triangular tiles, row-major; the first T(T+1)/2 entries serve any T).
+// Once per device, with that device current: resolve the arrays' device addresses (host code
+// may not use the symbols themselves as pointers) and the SM count.  Nothing is copied.
 const DeviceSetup& setup_current_device() {
   int dev = 0;
   DFTFE_CHECK_CUDA(cudaGetDevice(&dev));
@@ -53,16 +51,6 @@ const DeviceSetup& setup_current_device() {
   DeviceSetup& d = g_setup[dev];
   if (d.ready) return d;
   DFTFE_CHECK_CUDA(cudaGetSymbolAddress((void**)&d.scratch, g_scratch));
-  DFTFE_CHECK_CUDA(cudaGetSymbolAddress((void**)&d.tiles, g_tiles));
-  int32_t tl[2 * kMaxTiles];
-  int t = 0;
-  for (int i = 0; i < kMaxTiles1D; ++i)
-    for (int j = 0; j <= i; ++j) {
-      tl[2 * t] = i;
-      tl[2 * t + 1] = j;
-      ++t;
-    }
-  DFTFE_CHECK_CUDA(cudaMemcpyToSymbol(g_tiles, tl, sizeof(tl)));
   DFTFE_CHECK_CUDA(cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev));
   d.ready = true;
   return d;
@@ -80,6 +68,17 @@ extern "C" dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, i
     throw Error(DFTFE_ERR_ARG, "dftfe_cholgs_noalloc: ncol exceeds the static scratch limit of " +
                                    std::to_string(kMaxCols) + " columns");
   const DeviceSetup& d = setup_current_device();
+  // X must be device memory of the current device, whose static scratch the kernels use
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, X) != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(DFTFE_ERR_ARG, "dftfe_cholgs_noalloc: X is not a device pointer");
+  }
+  int cur = 0;
+  DFTFE_CHECK_CUDA(cudaGetDevice(&cur));
+  if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+    throw Error(DFTFE_ERR_ARG, "dftfe_cholgs_noalloc: X is not device memory");
+  if (pa.device != cur) throw Error(DFTFE_ERR_ARG, "dftfe_cholgs_noalloc: X lives on another device");
   cudaStream_t s = (cudaStream_t)stream;
   const int N = ncol;
   const int T = (N + kTileCols - 1) / kTileCols;
@@ -94,7 +93,7 @@ extern "C" dftfe_status dftfe_cholgs_noalloc(double* X, int64_t ld, int64_t M, i
   double* S = part + (size_t)nsplit * n2;         // N x N: S, then L in place
   double* Z = S + n2;                             // N x N: L^-T
   int* status = (int*)(Z + n2);                   // written by the Cholesky kernel
-  gram_partial_launch(s, X, ld, X, ld, M, N, nsplit, d.tiles, ntiles, part);
+  gram_partial_launch(s, X, ld, X, ld, M, N, nsplit, ntiles, part);
   gram_reduce_launch(s, part, nsplit, N, S);
   potrf(s, S, N, status);
   int st = 0;

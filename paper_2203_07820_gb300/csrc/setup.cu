@@ -515,6 +515,7 @@ extern "C" dftfe_status dftfe_ham_destroy(dftfe_ham h) {
   if (!h) return DFTFE_OK;
   if (h->stream || true) cudaStreamSynchronize(h->stream);
   free_graphs(h);
+  if (h->h_pass) cudaFreeHost(h->h_pass);
   free_nonlocal(h);
   cudaFree(h->d_map); cudaFree(h->d_mass); cudaFree(h->d_minvsqrt);
   cudaFree(h->d_colour_cells); cudaFree(h->d_node_ptr); cudaFree(h->d_node_slot); cudaFree(h->d_K); cudaFree(h->d_P); cudaFree(h->d_pairs);

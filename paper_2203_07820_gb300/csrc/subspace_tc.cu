@@ -264,7 +264,9 @@ __global__ void __launch_bounds__(st::kThreads, 1) k_rot_tc(const double* __rest
 // X[m][n] <- X[m][n] zd[n] + Yo[m][n] in FP64 (the diagonal of the rotation), two columns
 // per thread
 __global__ void k_rot_diag(double* __restrict__ X, int64_t ld, const float* __restrict__ Yo, int64_t ldo, int64_t M,
-                           int N, const double* __restrict__ zd) {
+                           int N, const double* __restrict__ zd, const int* guard) {
+  // a deferred pass whose factorisation or eigensolve failed leaves X as it is
+  if (guard && (guard[0] != 0 || guard[1] != 0)) return;
   const int nh = (N + 1) / 2;
   const int64_t total = M * nh;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -448,8 +450,8 @@ bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, con
   const int nkc = (N + 31) / 32, nt = (N + 127) / 128;
   uint8_t* Bt = (uint8_t*)ws_get(h, "rot_tc_tiles", (size_t)nkc * nt * st::kOperand);
   double* zd = (double*)ws_get(h, "rot_tc_zd", sizeof(double) * (size_t)N);
-  int* err = (int*)ws_get(h, "rot_tc_err", sizeof(int));
-  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  int* err = tc_err_flag(h, (int*)ws_get(h, "rot_tc_err", sizeof(int)));
+  if (!h->deferred) DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
   DFTFE_LAUNCH(k_rot_tiles, nblk_tc((int64_t)nkc * nt * 128 * 32), 256, 0, h->stream, Z, N, upper ? 1 : 0, nkc, nt,
                Bt, zd);
   // the FP32 product X offdiag(Z) goes through a buffer of at most 2 GiB: row slabs of a
@@ -469,9 +471,10 @@ bool rotate_inplace_tc(dftfe_ham h, double* X, int64_t ld, int64_t M, int N, con
     {
       ProfScope ps(h, "rotate_diag");
       DFTFE_LAUNCH(k_rot_diag, (unsigned)std::min<int64_t>((int64_t)h->sm_count * 16, nblk_tc(ms * ((N + 1) / 2))), 256,
-                   0, h->stream, Xs, ld, Yo, ldo, ms, N, zd);
+                   0, h->stream, Xs, ld, Yo, ldo, ms, N, zd, rot_guard(h));
     }
   }
+  if (h->deferred) return true;
   int herr = 0;
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
@@ -501,14 +504,15 @@ bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, i
   const int64_t rows = ((M + nsplit - 1) / nsplit + 31) / 32 * 32;
   const int64_t ns = (M + rows - 1) / rows;
   float* part = (float*)ws_get(h, "gram_tc_part", sizeof(float) * (size_t)ns * N * N);
-  int* err = (int*)ws_get(h, "gram_tc_err", sizeof(int));
-  DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
+  int* err = tc_err_flag(h, (int*)ws_get(h, "gram_tc_err", sizeof(int)));
+  if (!h->deferred) DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
   {
     ProfScope ps(h, "gram_tc");
     DFTFE_LAUNCH(k_gram_tc, (unsigned)(ns * npairs), st::kThreads, st::smem_bytes(), h->stream, A, lda, B, ldb, M, N,
                  npairs, rows, part, err);
   }
   DFTFE_LAUNCH(k_gram_tc_reduce, nblk_tc((int64_t)N * N), 256, 0, h->stream, part, (int)ns, dpart, nchunk, N, C);
+  if (h->deferred) return true;
   int herr = 0;
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));

@@ -211,9 +211,22 @@ class Controller:
         return r
 
 
+_POTENTIALS = {}
+
+
 def potentials(wl, qxyz, seed, steps, step_len=0.05, keep=0.3):
     """V_0 .. V_steps at the quadrature points: atoms walk `step_len` bohr per step and the
-    potential is mixed keep * old + (1 - keep) * new (the SCF-like sequence)."""
+    potential is mixed keep * old + (1 - keep) * new (the SCF-like sequence).  The last
+    sequence is kept, so the two controllers compared on it share one evaluation."""
+    key = (wl.name, qxyz.shape, seed, steps, step_len, keep)
+    if key in _POTENTIALS:
+        return _POTENTIALS[key]
+    _POTENTIALS.clear()
+    _POTENTIALS[key] = V = _potentials(wl, qxyz, seed, steps, step_len, keep)
+    return V
+
+
+def _potentials(wl, qxyz, seed, steps, step_len, keep):
     import synth
     pts = qxyz.reshape(-1, 3)
     pos = synth.atom_walk(seed, wl.centres, steps, step_len)
@@ -260,6 +273,59 @@ def run_sequence(dg, ham, wl, qxyz, X, ctrl, seed, steps, tol=1e-5, max_passes=3
         stats.append(dict(step=s, passes=passes, applications=apps, lanczos=ctrl.lanczos_runs - lz0,
                           seconds=time.perf_counter() - t0, max_resid=r.rmax))
     return stats, samples
+
+
+def run_batch_sequences(dg, systems, ctrls, steps, tol=1e-5, prec=2, max_passes=30):
+    """Every system of `systems` (dicts with ham, wl, qxyz, X, seed, block) through its own
+    SCF-like potential sequence, all systems together: at every step each system gets its new
+    potential, then batched passes (dftfe_batch_chfsi_pass) run over the systems whose largest
+    residual of the lowest 3/4 of the states is still above tol, each with the degree and bounds
+    its controller proposes.  Returns per-step statistics (step 0 included)."""
+    import torch
+    n = len(systems)
+    Vs = [potentials(sy["wl"], sy["qxyz"], sy["seed"], steps) for sy in systems]
+    # the sequences of different systems are cached one at a time by potentials(): keep them here
+    evs = [torch.empty(sy["X"].shape[1], dtype=torch.float64, device="cuda") for sy in systems]
+    rss = [torch.empty_like(e) for e in evs]
+    batches = {}
+    stats = []
+    try:
+        for st in range(steps + 1):
+            for i, sy in enumerate(systems):
+                dg.dftfe_ham_set_potential(sy["ham"], torch.from_numpy(Vs[i][st]).cuda())
+                ctrls[i].new_potential()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            left = list(range(n))
+            rounds = apps = 0
+            lz0 = sum(c.lanczos_runs for c in ctrls)
+            while left and rounds < max_passes:
+                props = [ctrls[i].propose() for i in left]
+                key = tuple(left)
+                if key not in batches:
+                    batches[key] = dg.dftfe_batch_create([systems[i]["ham"] for i in left])
+                bds = [pr[1] for pr in props]
+                dg.dftfe_batch_chfsi_pass(batches[key], [systems[i]["X"] for i in left],
+                                          [systems[i]["block"] for i in left], [pr[0] for pr in props], bds,
+                                          [evs[i] for i in left], [rss[i] for i in left], prec)
+                rounds += 1
+                still = []
+                for j, i in enumerate(left):
+                    m, _, mode = props[j]
+                    N = systems[i]["X"].shape[1]
+                    apps += m * ((N + systems[i]["block"] - 1) // systems[i]["block"])
+                    r = ctrls[i].record(evs[i], rss[i], bds[j], m, mode)
+                    if r.rmax > tol:
+                        still.append(i)
+                left = still
+            torch.cuda.synchronize()
+            stats.append(dict(step=st, rounds=rounds, applications=apps, converged=not left,
+                              lanczos=sum(c.lanczos_runs for c in ctrls) - lz0,
+                              seconds=time.perf_counter() - t0))
+    finally:
+        for b in batches.values():
+            dg.dftfe_batch_destroy(b)
+    return stats
 
 
 def search_step(ham, wl, X, ctrl, tol, prec, max_rollout=12):
@@ -313,15 +379,29 @@ def search_step(ham, wl, X, ctrl, tol, prec, max_rollout=12):
     return choice, (F, target)
 
 
-def experiment(train_seqs=24, test_seqs=5, steps=8, tol=1e-5, train_steps=3000, seed0=0, log=print):
-    """Data from the degree search on `train_seqs` sequences of the 13,824-DoF system
-    (synth.small_wells: 8 wells, 32 states), training on the GPU kernels, then `test_seqs`
-    held-out sequences run from the same start with the standard rule and with the proposer.
-    Returns a summary dictionary."""
+def _compare(dg, ham, wl, qxyz, start, net, seeds, steps, tol, prec, log):
+    """Held-out sequences run twice from the same start: the standard rule and the proposer."""
+    rows = []
+    for s in seeds:
+        row = {"seed": s}
+        for name, n in (("standard", None), ("learned", net)):
+            ctrl = Controller(ham, wl.nstates, n, s)
+            stats, _ = run_sequence(dg, ham, wl, qxyz, start(s), ctrl, s, steps, tol, prec=prec)
+            row[name] = {"applications": sum(x["applications"] for x in stats[1:]),
+                         "passes": sum(x["passes"] for x in stats[1:]),
+                         "seconds": sum(x["seconds"] for x in stats[1:]),
+                         "lanczos_runs": ctrl.lanczos_runs, "fallbacks": ctrl.fallbacks,
+                         "converged": all(x["max_resid"] <= tol for x in stats)}
+        rows.append(row)
+        log(row)
+    tot = {}
+    for k in ("applications", "passes", "seconds", "lanczos_runs"):
+        tot[k] = {name: sum(r[name][k] for r in rows) for name in ("standard", "learned")}
+    return rows, tot
+
+
+def _system(dg, wl):
     import torch
-    import synth
-    import paper_2203_07820_gb300 as dg
-    wl = synth.small_wells(seed0)
     mesh = dg.dftfe_mesh_create(wl.L, wl.ncell, wl.degree)
     ham = dg.dftfe_ham_create(mesh)
     _, qxyz = dg.dftfe_mesh_coords(mesh, nodes=False)
@@ -330,12 +410,26 @@ def experiment(train_seqs=24, test_seqs=5, steps=8, tol=1e-5, train_steps=3000, 
         X = torch.empty((wl.ndofs, wl.nstates), dtype=torch.float64, device="cuda")
         dg.dftfe_random_uniform(X, 1000 + seed)
         return X
+    return mesh, ham, qxyz, start
 
+
+def experiment(train_seqs=24, test_seqs=5, steps=8, tol=1e-5, train_steps=3000, seed0=0, prec=0,
+               eval_workload=None, eval_seqs=1, eval_steps=4, log=print):
+    """Data from the degree search on `train_seqs` sequences of `steps` potentials of the
+    13,824-DoF system (synth.small_wells: 8 wells, 32 states), training on the GPU kernels,
+    then `test_seqs` held-out sequences of that system and, with `eval_workload` (a
+    synth.Workload, e.g. the 32^3-cell, 1,024-state system), `eval_seqs` held-out sequences of
+    `eval_steps` potentials of it, each run with the standard rule and with the proposer from
+    the same start.  Passes in precision `prec`.  Returns a summary dictionary."""
+    import paper_2203_07820_gb300 as dg
+    import synth
+    wl = synth.small_wells(seed0)
+    mesh, ham, qxyz, start = _system(dg, wl)
     t0 = time.perf_counter()
     F, T = [], []
     for s in range(train_seqs):
         ctrl = Controller(ham, wl.nstates, None, s)
-        _, samples = run_sequence(dg, ham, wl, qxyz, start(s), ctrl, s, steps, tol, search=True)
+        _, samples = run_sequence(dg, ham, wl, qxyz, start(s), ctrl, s, steps, tol, prec=prec, search=True)
         F += [x[0] for x in samples]
         T += [x[1] for x in samples]
     t_data = time.perf_counter() - t0
@@ -345,39 +439,43 @@ def experiment(train_seqs=24, test_seqs=5, steps=8, tol=1e-5, train_steps=3000, 
     t_train = time.perf_counter() - t0
     degrees = [int(round(16 * 2 ** t[0])) for t in T]
     out = {"system": wl.name, "ndofs": wl.ndofs, "nstates": wl.nstates, "tol": tol, "steps": steps,
-           "train_sequences": train_seqs, "samples": len(F), "target_degrees": {str(d): degrees.count(d)
-                                                                             for d in sorted(set(degrees))},
-           "data_seconds": t_data, "train_seconds": t_train,
-           "loss_first_last": [loss[0], loss[-1]], "test": []}
-    for s in range(1000, 1000 + test_seqs):
-        row = {"seed": s}
-        for name, n in (("standard", None), ("learned", net)):
-            ctrl = Controller(ham, wl.nstates, n, s)
-            stats, _ = run_sequence(dg, ham, wl, qxyz, start(s), ctrl, s, steps, tol)
-            row[name] = {"applications": sum(x["applications"] for x in stats[1:]),
-                         "passes": sum(x["passes"] for x in stats[1:]),
-                         "seconds": sum(x["seconds"] for x in stats[1:]),
-                         "lanczos_runs": ctrl.lanczos_runs, "fallbacks": ctrl.fallbacks,
-                         "converged": all(x["max_resid"] <= tol for x in stats)}
-        out["test"].append(row)
-        log(row)
+           "precision": prec, "train_sequences": train_seqs, "samples": len(F),
+           "target_degrees": {str(d): degrees.count(d) for d in sorted(set(degrees))},
+           "data_seconds": t_data, "train_seconds": t_train, "loss_first_last": [loss[0], loss[-1]]}
+    out["test"], out["test_total"] = _compare(dg, ham, wl, qxyz, start, net, range(1000, 1000 + test_seqs), steps,
+                                              tol, prec, log)
     dg.dftfe_ham_destroy(ham)
     dg.dftfe_mesh_destroy(mesh)
-    for k in ("applications", "passes", "seconds", "lanczos_runs"):
-        out["total_" + k] = {name: sum(r[name][k] for r in out["test"]) for name in ("standard", "learned")}
+    if eval_workload is not None:
+        wl2 = eval_workload
+        mesh, ham, qxyz, start = _system(dg, wl2)
+        rows, tot = _compare(dg, ham, wl2, qxyz, start, net, range(2000, 2000 + eval_seqs), eval_steps, tol, prec, log)
+        out["eval"] = {"system": wl2.name, "ndofs": wl2.ndofs, "nstates": wl2.nstates, "steps": eval_steps,
+                       "rows": rows, "total": tot}
+        dg.dftfe_ham_destroy(ham)
+        dg.dftfe_mesh_destroy(mesh)
     return out
 
 
 if __name__ == "__main__":
     import argparse
     import json
+    import synth
     ap = argparse.ArgumentParser(description="train and judge the learned degree/bounds proposer")
     ap.add_argument("--train-seqs", type=int, default=24)
     ap.add_argument("--test-seqs", type=int, default=5)
     ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3"])
+    ap.add_argument("--eval-scale32", action="store_true",
+                    help="also evaluate on the 32^3-cell, p = 6, 1,024-state system (7,077,888 DoFs)")
+    ap.add_argument("--eval-seqs", type=int, default=1)
+    ap.add_argument("--eval-steps", type=int, default=4)
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    res = experiment(a.train_seqs, a.test_seqs, a.steps)
+    prec = {"fp64": 0, "tf32x3": 2}[a.precision]
+    ev = synth.lattice_atoms(0, ncell=32, nstates=1024, passes=2) if a.eval_scale32 else None
+    res = experiment(a.train_seqs, a.test_seqs, a.steps, prec=prec, eval_workload=ev, eval_seqs=a.eval_seqs,
+                     eval_steps=a.eval_steps)
     print(json.dumps({k: v for k, v in res.items() if k != "test"}))
     if a.out:
         with open(a.out, "w") as f:

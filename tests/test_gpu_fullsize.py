@@ -76,6 +76,22 @@ def test_fullsize_apply_sampled_rows(dg, full, prec):
     del X, Y
 
 
+def test_fullsize_mixed_apply_is_deterministic(dg, full):
+    """At full size every CTA of the persistent TF32x3 cell kernel walks about 91 cells, so its
+    rings are reused many times over: two applications give the same bits, and the largest
+    difference from the FP64 application stays at the split precision's level."""
+    wl, mesh, ham, om, oh, rows = full
+    X = torch.empty((om.ndofs, B), dtype=torch.float64, device="cuda")
+    dg.dftfe_random_uniform(X, 13)
+    Y1, Y2, Y64 = torch.empty_like(X), torch.empty_like(X), torch.empty_like(X)
+    dg.dftfe_ham_apply(ham, X, Y1, 2)
+    dg.dftfe_ham_apply(ham, X, Y2, 2)
+    dg.dftfe_ham_apply(ham, X, Y64, 0)
+    assert torch.equal(Y1, Y2)
+    assert (Y1 - Y64).abs().max().item() <= 1e-5 * Y64.abs().max().item()
+    del X, Y1, Y2, Y64
+
+
 def test_fullsize_cholgs_sampled_rows(dg, full):
     """CholGS of one 128-column block at full M (FP64): S by the oracle from the same
     seeded block, sampled rows of X L^-T compared."""

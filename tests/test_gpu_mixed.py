@@ -168,3 +168,27 @@ def test_float_pair_apply_is_fp64_accurate(dg, pair, ncol):
     dg.dftfe_ham_apply(ham, X, Y, dg.DFTFE_FP64_FLOAT_PAIRS)
     err = np.abs(Y.cpu().numpy() - oh.apply(X0))
     assert np.all(err <= 2.0 ** -40 * abs_bound(om, oh, X0) + 1e-300)
+
+
+@pytest.mark.parametrize("p,n,L", [(4, (8, 8, 8), 10.0), (5, (8, 8, 8), 10.0), (6, (6, 6, 6), 9.0)])
+def test_mixed_apply_many_cells_per_cta(dg, p, n, L):
+    """More cells than SMs (each CTA of the persistent cell kernel walks several cells, so
+    its pipelines run across cell boundaries) for one, two and three 128-row M-tiles: the
+    TF32x3 apply within its element-wise bound, 128 columns."""
+    c = small_case(3, n=n, p=p, L=L, nl=True)
+    om, oh = oracle_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    try:
+        X0 = synth.random_block(500 + p, om.ndofs, 128)
+        X = torch.from_numpy(X0).cuda()
+        Y = torch.full_like(X, float("nan"))
+        dg.dftfe_ham_apply(ham, X, Y, 2)
+        y = Y.cpu().numpy()
+        err = np.abs(y - oh.apply(X0))
+        bound = abs_bound(om, oh, X0)
+        cfac = 6.0 + om.nodes_per_cell * 2.0 ** -24 / U[2]
+        assert np.all(np.isfinite(y))
+        assert np.all(err <= cfac * U[2] * bound + 1e-30), float((err / (bound + 1e-300)).max())
+    finally:
+        dg.dftfe_ham_destroy(ham)
+        dg.dftfe_mesh_destroy(mesh)

@@ -45,6 +45,39 @@ def test_noalloc_cholgs_matches_cholgs_on_consecutive_calls(dg):
     dg.dftfe_mesh_destroy(mesh)
 
 
+def test_noalloc_cholgs_at_its_column_limit_on_a_non_blocking_stream(dg):
+    """512 columns (the scratch bound caps the split count and the status word sits at the
+    end of the array) on a stream created with non-blocking flags, twice in a row."""
+    mesh = dg.dftfe_mesh_create(10.0, 6, 4)          # 13,824 DoFs
+    ham = dg.dftfe_ham_create(mesh)
+    M = dg.dftfe_mesh_info(mesh)[0]
+    lib = dg.lib()
+    s = torch.cuda.Stream()
+    N = 512
+    for seed in (3, 4):
+        X0 = synth.random_block(seed, M, N) @ np.diag(np.linspace(1.0, 8.0, N))
+        Xa = torch.from_numpy(X0).cuda()
+        Xb = torch.from_numpy(X0).cuda()
+        torch.cuda.synchronize()
+        dg.dftfe_cholgs(ham, Xa)
+        rc = lib.dftfe_cholgs_noalloc(C.c_void_p(Xb.data_ptr()), Xb.stride(0), M, N, C.c_void_p(s.cuda_stream))
+        assert rc == 0, dg.dftfe_last_error()
+        torch.cuda.synchronize()
+        a, b = Xa.cpu().numpy(), Xb.cpu().numpy()
+        assert np.abs(b - a).max() <= TOL * np.abs(a).max(), seed
+    dg.dftfe_ham_destroy(ham)
+    dg.dftfe_mesh_destroy(mesh)
+
+
+def test_noalloc_cholgs_rejects_host_memory(dg):
+    lib = dg.lib()
+    M, N = 100, 4
+    Xh = np.zeros((M, N))
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib.dftfe_cholgs_noalloc(Xh.ctypes.data_as(C.c_void_p), N, M, N, stream)
+    assert rc == 1 and "device" in dg.dftfe_last_error()
+
+
 def test_noalloc_cholgs_rejects_sizes_beyond_its_scratch(dg):
     lib = dg.lib()
     M, N = 2000, 513
