@@ -626,7 +626,7 @@ def torch_from(a, dev):
 
 
 FAMILIES = ("pass_filter", "pass_cholgs", "pass_rr", "cell_gemm_fp64", "cell_gemm_tf32x3", "cell_gemm_bf16x3",
-            "assemble32", "cell_gemm_df", "rotate_tc", "rotate_diag", "gram_tc", "coldot", "gram", "gram_mixed",
+            "assemble32", "cell_gemm_df", "cell_gemm_slices", "slices_digits", "rotate_tc", "rotate_diag", "gram_tc", "coldot", "gram", "gram_mixed",
             "rotate", "rotate_mixed", "syevd", "potrf", "trtri")
 
 
@@ -698,6 +698,25 @@ def rooflines(fam, wl, precision):
                                  "frac": a / (fp32_peak / 12.0),
                                  "peak_source": "derived: FP32 peak 152 SMs x 128 FMA/clk x 2 x 2.07 GHz / 12 "
                                                 "FP32 instructions per float-pair multiply-add"}
+    if "cell_gemm_slices" in fam:
+        # W = H~X from exact digit products: 21 bf16 digit products per multiply-add; the
+        # digit rows of the cell matrices (6 bf16 per entry) stream once per 128-column block,
+        # the X digits (6 bf16) are gathered per cell, Y is read and written per cell entry
+        t = fam["cell_gemm_slices"]["ms"] / 1e3
+        flops = 21 * 2.0 * Nc * nc * nc * N
+        byt = 12.0 * Nc * nc * nc * ((N + 127) // 128) + 12.0 * Nc * nc * N + 16.0 * Nc * nc * N
+        tb, tt = byt / (hbm_peak * 1e9), flops / (bf16_sust * 1e12)
+        tensor_bound = tt >= tb
+        roofs["cell_gemm_slices"] = {
+            "kernel": "k_cell_slices (W = H~X from exact bf16 digit products, tcgen05, TMEM accumulators)",
+            "bound": "tensor" if tensor_bound else "hbm",
+            "achieved": flops / t / 1e12 if tensor_bound else byt / t / 1e9,
+            "peak": bf16_sust if tensor_bound else hbm_peak,
+            "unit": "TFLOP/s" if tensor_bound else "GB/s", "frac": max(tb, tt) / t,
+            "peak_source": f"{src} bf16 sustained" if tensor_bound else f"{src} hbm_gbs",
+            "ms_per_w": t * 1e3, "algorithmic_flops_per_w": flops, "algorithmic_bytes_per_w": byt,
+            "tensor_frac": tt / t, "hbm_frac": tb / t,
+            "units": f"one W = H~X over {N} columns and all {Nc} cells (all launches of the family)"}
     # useful tensor work of the subspace GEMMs, six TF32 slice products per multiply-add: the
     # rotations X L^-T (triangular, M N^2), X Q and W Q (2 M N^2 each); S and H^ (lower 128 x 128
     # blocks, 2 M 128^2 each)
@@ -773,7 +792,9 @@ def run_ours(args, rank, world, local, tdist):
     fam = query_families(dg, ham, args.steps)
     dg.dftfe_profile_enable(ham, False)
     sec_per_pass = ms / 1e3 / args.steps
-    log(f"timed: {sec_per_pass:.3f} s/pass; memory in use {torch.cuda.mem_get_info()}")
+    free_b, total_b = torch.cuda.mem_get_info()
+    log(f"timed: {sec_per_pass:.3f} s/pass; device memory in use {(total_b - free_b) / 2**30:.1f} GiB "
+        f"of {total_b / 2**30:.1f}")
 
     nc = (wl.degree + 1) ** 3
     Nc = wl.ncell ** 3

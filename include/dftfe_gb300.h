@@ -59,15 +59,23 @@ typedef enum {
                               vectors; CholGS, Rayleigh-Ritz and residuals in FP64 */
   DFTFE_MIXED_TF32X3 = 2,  /* as above with 3-term TF32 splits (about 2^-21 relative per
                               product instead of 2^-16) */
-  DFTFE_FP64_FLOAT_PAIRS = 3 /* dftfe_ham_apply only: FP64-accurate cell products from pairs
-                              of floats (error-free products, TwoSum accumulation, about 44
-                              significant bits) on the FP32 pipes; FP64 in and out */
+  DFTFE_FP64_FLOAT_PAIRS = 3, /* dftfe_ham_apply(_z) only: FP64-accurate cell products from
+                              pairs of floats (error-free products, TwoSum accumulation, about
+                              44 significant bits) on the FP32 pipes; FP64 in and out */
+  DFTFE_FP64_SLICES = 4     /* dftfe_ham_apply(_z) only: FP64-accurate cell products on the
+                              tensor cores from exact digit products: each cell-matrix row and
+                              each column of X as 41-bit fixed point (relative to its largest
+                              entry) in six 7-bit bf16 digits, the 21 digit products of order
+                              <= 5 accumulated exactly in FP32 (each sum stays below 2^24),
+                              combined in 64-bit integers; error about 2^-39 |h|max |x|max per
+                              term.  Degree <= 7 (DFTFE_ERR_ARG beyond); FP64 in and out */
   /* In dftfe_cholgs, dftfe_rayleigh_ritz and the pass, either mixed value selects the
      mixed overlap / projection / rotation of Sec. 3.2: diagonal entries of S and H^ and
      the diagonal part of each rotation in FP64, off-diagonal parts in FP32; W = H~X
-     for the projection and the residuals uses the float-pair products of
-     DFTFE_FP64_FLOAT_PAIRS (split products there move the Ritz values by 1e-6 to
-     2e-6 Ha); the Cholesky factorisation and the eigensolve stay FP64. */
+     for the projection and the residuals uses the exact digit products of
+     DFTFE_FP64_SLICES (the float pairs of DFTFE_FP64_FLOAT_PAIRS beyond degree 7; split
+     products there would move the Ritz values by 1e-6 to 2e-6 Ha); the Cholesky
+     factorisation and the eigensolve stay FP64. */
 } dftfe_precision;
 
 typedef struct dftfe_mesh_s* dftfe_mesh; /* opaque, library-owned */
@@ -150,9 +158,10 @@ dftfe_status dftfe_ham_export(dftfe_ham ham, double* mass, int32_t* cell_map,
 
 /* Y = H~ X for an M x ncol block (a4 + a5; Eq. celldgemm and Alg. 4): gather to
  * cells, dense per-cell product, colour-ordered scatter-add, plus C~ h C~^T X.
- * X and Y in DEVICE memory, must not overlap.  prec selects the FP64 cell kernel or
- * the split-precision tensor-core kernel (FP32 inside, converted at both ends;
- * at most 512 nodes per cell, i.e. p <= 7). */
+ * X and Y in DEVICE memory, must not overlap.  prec selects the FP64 cell kernel, the
+ * split-precision tensor-core kernel (FP32 inside, converted at both ends; at most 512
+ * nodes per cell, i.e. p <= 7), or one of the two FP64-accurate forms used for W in the
+ * mixed passes (DFTFE_FP64_FLOAT_PAIRS; DFTFE_FP64_SLICES, p <= 7). */
 dftfe_status dftfe_ham_apply(dftfe_ham ham, const double* X, int64_t ldx,
                              double* Y, int64_t ldy, int ncol, dftfe_precision prec);
 
@@ -330,8 +339,9 @@ dftfe_status dftfe_ham_set_kpoint(dftfe_ham ham, const double* k, const double* 
 dftfe_status dftfe_mesh_kpoint_stencil(dftfe_mesh mesh, const double* k, double* table);
 
 /* Y = H~^k X for complex M x ncol blocks (X, Y DEVICE, not overlapping).  prec as in
- * dftfe_ham_apply: FP64; DFTFE_FP64_FLOAT_PAIRS (local part from float pairs, k terms and
- * projectors FP64: the W of a mixed complex pass); or a split precision (FP32 complex inside:
+ * dftfe_ham_apply: FP64; DFTFE_FP64_SLICES or DFTFE_FP64_FLOAT_PAIRS (local part from
+ * exact digit products or float pairs on the real view, k terms and projectors FP64: the
+ * W of a mixed complex pass uses the former); or a split precision (FP32 complex inside:
  * the split cell products act on the real view, the k terms and projectors in FP32). */
 dftfe_status dftfe_ham_apply_z(dftfe_ham ham, const double* X, int64_t ldx, double* Y,
                                int64_t ldy, int ncol, dftfe_precision prec);

@@ -43,6 +43,7 @@ DFTFE_FP64 = 0
 DFTFE_MIXED_BF16X3 = 1
 DFTFE_MIXED_TF32X3 = 2
 DFTFE_FP64_FLOAT_PAIRS = 3
+DFTFE_FP64_SLICES = 4
 
 STATUS = {0: "DFTFE_OK", 1: "DFTFE_ERR_ARG", 2: "DFTFE_ERR_OOM", 3: "DFTFE_ERR_CUDA",
           4: "DFTFE_ERR_NOT_SPD", 5: "DFTFE_ERR_NOCONV", 6: "DFTFE_ERR_TIMEOUT",

@@ -46,7 +46,7 @@ static void rr_impl(dftfe_ham h, double* X, int64_t ld, int ncol, double* evals,
   // W = H~X must be FP64-accurate in every precision (split-precision cell products here
   // move the Ritz values by 1e-6 to 2e-6 Ha, the size of the mixed tolerance): FP64 in
   // the FP64 pass, float pairs (about 44 bits) on the FP32 pipes in a mixed pass
-  if (mixed) apply_df(h, X, ld, W, ldw, N);
+  if (mixed) apply_w(h, X, ld, W, ldw, N);
   else apply_combo(h, X, ld, nullptr, 0, W, ldw, N, 1.0, 0.0, 0.0);
   double* Hh = (double*)ws_get(h, "Hhat", sizeof(double) * (size_t)N * N);
   double* Q = (double*)ws_get(h, "Q", sizeof(double) * (size_t)N * N);

@@ -205,7 +205,7 @@ extern "C" dftfe_status dftfe_rayleigh_ritz_split(dftfe_ham h, const double* X, 
   const int N = ncol;
   const bool mixed = prec != DFTFE_FP64;
   double* W = (double*)ws_get(h, "W", sizeof(double) * (size_t)m->M * N);
-  if (mixed) apply_df(h, X, ld, W, N, N);
+  if (mixed) apply_w(h, X, ld, W, N, N);
   else apply_combo(h, X, ld, nullptr, 0, W, N, N, 1.0, 0.0, 0.0);
   double* Hh = (double*)ws_get(h, "Hhat", sizeof(double) * (size_t)N * N);
   double* Q = (double*)ws_get(h, "Q", sizeof(double) * (size_t)N * N);

@@ -342,11 +342,14 @@ extern "C" dftfe_status dftfe_ham_apply(dftfe_ham h, const double* X, int64_t ld
   DFTFE_REQUIRE(h && X && Y, "null argument");
   DFTFE_REQUIRE(ncol >= 0 && ldx >= ncol && ldy >= ncol, "bad ncol / leading dimension");
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3 ||
-                    prec == DFTFE_FP64_FLOAT_PAIRS,
+                    prec == DFTFE_FP64_FLOAT_PAIRS || prec == DFTFE_FP64_SLICES,
                 "unknown precision");
   if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (prec == DFTFE_FP64_SLICES && !slices_applicable(h))
+    throw Error(DFTFE_ERR_ARG, "exact-slice products need at most 682 nodes per cell (degree <= 7)");
   if (prec == DFTFE_FP64) apply_combo(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
   else if (prec == DFTFE_FP64_FLOAT_PAIRS) apply_df(h, X, ldx, Y, ldy, ncol);
+  else if (prec == DFTFE_FP64_SLICES) apply_slices(h, X, ldx, Y, ldy, ncol);
   else apply_mixed(h, X, ldx, Y, ldy, ncol, prec == DFTFE_MIXED_TF32X3);
   ABI_END
 }

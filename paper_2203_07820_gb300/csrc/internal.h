@@ -143,6 +143,7 @@ struct dftfe_ham_s {
   int64_t potential_version = 0;   // bumped by every set_potential
   int64_t mixed_version[2] = {-1, -1};  // potential version of the split tiles (bf16, tf32)
   int64_t df_version = -1;              // potential version of the float-pair cell matrices
+  int64_t slices_version = -1;          // potential version of the digit rows (exact slices)
   // a3: nonlocal (CSR by projector and by node)
   int nproj = 0;
   double* d_h = nullptr;
@@ -245,6 +246,12 @@ std::function<void()> plan_mixed_batch(const std::vector<std::vector<MixedBlock>
                                        int* err, DevBuf& desc, std::vector<uint8_t>& host_desc);
 // with_nl = false: the local part only (real view of a complex block)
 void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl = true);
+// hx_slices.cu: Y = H~X from exact bf16 digit products on the tensor cores (FP64-accurate;
+// false when the mesh degree is beyond what the exact accumulation allows), and the W = H~X
+// of the mixed Rayleigh-Ritz step (those products where they apply, else float pairs)
+bool slices_applicable(dftfe_ham h);
+bool apply_slices(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl = true);
+void apply_w(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl = true);
 // kpoint.cu: Z += alpha (-i k.grad X + H~_nl^k X) on FP32 complex blocks given by their real
 // views (ld in floats, ncolz complex columns); 1/2|k|^2 is the caller's
 void kpoint_add32(dftfe_ham h, const float* X, int64_t ldx, float* Z, int64_t ldz, int ncolz, float alpha);

@@ -408,12 +408,15 @@ void kpoint_add32(dftfe_ham h, const float* X, int64_t ldx, float* Z, int64_t ld
   }
 }
 
-// W = H~^k X with the local part from float pairs (about 44 bits, FP32 pipes) on the real view
-// and the k-dependent and nonlocal terms in FP64: the W of a mixed complex Rayleigh-Ritz
-static void apply_z_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol) {
+// W = H~^k X with an FP64-accurate local part on the real view (prec: DFTFE_FP64_SLICES, the
+// exact digit products, or DFTFE_FP64_FLOAT_PAIRS) and the k-dependent and nonlocal terms in
+// FP64: the W of a mixed complex Rayleigh-Ritz
+static void apply_z_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol,
+                       dftfe_precision prec) {
   require_kpoint(h);
   auto* m = h->mesh;
-  apply_df(h, X, 2 * ldx, Y, 2 * ldy, 2 * ncol, false);
+  if (prec == DFTFE_FP64_SLICES) apply_w(h, X, 2 * ldx, Y, 2 * ldy, 2 * ncol, false);
+  else apply_df(h, X, 2 * ldx, Y, 2 * ldy, 2 * ncol, false);
   const double k2 = h->kvec[0] * h->kvec[0] + h->kvec[1] * h->kvec[1] + h->kvec[2] * h->kvec[2];
   const int p = m->p;
   {
@@ -511,7 +514,7 @@ static void rayleigh_ritz_z(dftfe_ham h, double* X, int64_t ld, int ncol, double
   auto* m = h->mesh;
   const int N2 = 2 * ncol;
   // W FP64-accurate in both precisions (float pairs for the local part of a mixed pass)
-  if (mixed) apply_z_df(h, X, ld, W, ldw, ncol);
+  if (mixed) apply_z_df(h, X, ld, W, ldw, ncol, DFTFE_FP64_SLICES);
   else apply_combo_z(h, X, ld, nullptr, 0, W, ldw, ncol, 1.0, 0.0, 0.0);
   double* G = (double*)ws_get(h, "Hhat", sizeof(double) * (size_t)N2 * N2);
   real_view_gram(h, X, 2 * ld, W, 2 * ldw, N2, G, mixed);
@@ -629,10 +632,13 @@ extern "C" dftfe_status dftfe_ham_apply_z(dftfe_ham h, const double* X, int64_t 
   ABI_BEGIN
   DFTFE_REQUIRE(h && X && Y, "null argument");
   DFTFE_REQUIRE(ncol >= 0 && ldx >= ncol && ldy >= ncol, "bad ncol / leading dimension");
-  DFTFE_REQUIRE(valid_prec(prec) || prec == DFTFE_FP64_FLOAT_PAIRS, "unknown precision");
+  DFTFE_REQUIRE(valid_prec(prec) || prec == DFTFE_FP64_FLOAT_PAIRS || prec == DFTFE_FP64_SLICES,
+                "unknown precision");
   require_kpoint(h);
+  if (prec == DFTFE_FP64_SLICES && !slices_applicable(h))
+    throw Error(DFTFE_ERR_ARG, "exact-slice products need at most 682 nodes per cell (degree <= 7)");
   if (prec == DFTFE_FP64) apply_combo_z(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
-  else if (prec == DFTFE_FP64_FLOAT_PAIRS) apply_z_df(h, X, ldx, Y, ldy, ncol);
+  else if (prec == DFTFE_FP64_FLOAT_PAIRS || prec == DFTFE_FP64_SLICES) apply_z_df(h, X, ldx, Y, ldy, ncol, prec);
   else apply_mixed(h, X, 2 * ldx, Y, 2 * ldy, 2 * ncol, prec == DFTFE_MIXED_TF32X3, true);
   ABI_END
 }

@@ -271,6 +271,26 @@ def test_float_pair_apply_z_is_fp64_accurate(dg, pair, ncol):
     assert np.all(err <= 2.0 ** -40 * _abs_bound(om, B, X0) + 1e-300)
 
 
+@pytest.mark.parametrize("ncol", [1, 33, 70])
+def test_slices_apply_z_is_fp64_accurate(dg, pair, ncol):
+    """DFTFE_FP64_SLICES on a complex block (the W of a mixed complex pass): exact digit
+    products on the real view (2 ncol real columns, per-column exponents of the real and
+    imaginary parts), k terms and projectors FP64.  Bound: 2^-36 n_c (row max |h|)(column max
+    of |Re x|, |Im x|) per assembled row, times sqrt(2) for the complex modulus."""
+    om, B, mesh, ham = pair
+    X0 = _zblock(520 + ncol, om.ndofs, ncol)
+    X = _t(X0)
+    Y = torch.full_like(X, complex("nan"))
+    dg.dftfe_ham_apply_z(ham, X, Y, dg.DFTFE_FP64_SLICES)
+    err = np.abs(Y.cpu().numpy() - B.apply(X0))
+    rowmax = np.abs(B.ham.cell_matrices()).max(axis=2)
+    colmax = np.maximum(np.abs(X0.real).max(axis=0), np.abs(X0.imag).max(axis=0))
+    nc = om.nodes_per_cell
+    Yc = (nc * rowmax)[:, :, None] * colmax[None, None, :]
+    bound = 2.0 ** -36 * math.sqrt(2.0) * (om.QT @ Yc.reshape(-1, ncol)) + 2.0 ** -44 * _abs_bound(om, B, X0)
+    assert np.all(err <= bound + 1e-300), float((err / (bound + 1e-300)).max())
+
+
 @pytest.mark.parametrize("prec", [2, 1])
 def test_mixed_cholgs_z_orthonormalises(dg, pair, prec):
     om, B, mesh, ham = pair

@@ -170,6 +170,77 @@ def test_float_pair_apply_is_fp64_accurate(dg, pair, ncol):
     assert np.all(err <= 2.0 ** -40 * abs_bound(om, oh, X0) + 1e-300)
 
 
+def slices_bound(om, oh, X):
+    """Error bound of DFTFE_FP64_SLICES: both operands are 41-bit fixed point relative to the
+    largest |h| of their cell-matrix row and the largest |x| of their column (rounding error
+    2^-42 of those), and the digit products of order >= 6 are dropped (below 5 2^-42 of their
+    product), so each cell term is off by at most 2^-36.7 (max|h| of the row)(max|x| of the
+    column); summed over the n_c terms of a row and assembled.  Plus 2^-44 |H~||X| for the
+    FP64 nonlocal part and the final roundings."""
+    B = X.shape[1]
+    rowmax = np.abs(oh.cell_matrices()).max(axis=2)
+    colmax = np.abs(X).max(axis=0)
+    nc = om.nodes_per_cell
+    Yc = (nc * rowmax)[:, :, None] * colmax[None, None, :]
+    return 2.0 ** -36 * (om.QT @ Yc.reshape(-1, B)) + 2.0 ** -44 * abs_bound(om, oh, X)
+
+
+@pytest.mark.parametrize("ncol", [1, 33, 64, 100, 200])
+def test_slices_apply_is_fp64_accurate(dg, pair, ncol):
+    """DFTFE_FP64_SLICES (W = H~X of the mixed passes): exact digit products on the tensor
+    cores, one and two 128-column blocks, one and two 64-column items per cell, ragged."""
+    om, oh, mesh, ham = pair
+    X0 = synth.random_block(700 + ncol, om.ndofs, ncol)
+    X = torch.from_numpy(X0).cuda()
+    Y = torch.full_like(X, float("nan"))
+    dg.dftfe_ham_apply(ham, X, Y, dg.DFTFE_FP64_SLICES)
+    y = Y.cpu().numpy()
+    err = np.abs(y - oh.apply(X0))
+    bound = slices_bound(om, oh, X0)
+    assert np.all(np.isfinite(y))
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_slices_apply_column_scales_and_zero_column(dg, pair):
+    """Each column has its own exponent: columns scaled by 1e-200 .. 1e200 keep the same
+    relative bound, and an all-zero column gives exact zeros; the result is bitwise
+    repeatable (exact accumulation, colour-ordered FP64 adds)."""
+    om, oh, mesh, ham = pair
+    scales = np.array([1.0, 1e-200, 1e200, 0.0, 2.0 ** -20, 3.0e7])
+    X0 = synth.random_block(710, om.ndofs, scales.size) * scales[None, :]
+    X = torch.from_numpy(X0).cuda()
+    Y = torch.full_like(X, float("nan"))
+    dg.dftfe_ham_apply(ham, X, Y, dg.DFTFE_FP64_SLICES)
+    y = Y.cpu().numpy()
+    err = np.abs(y - oh.apply(X0))
+    assert np.all(err <= slices_bound(om, oh, X0))
+    assert np.all(y[:, 3] == 0.0)
+    Y2 = torch.full_like(X, float("nan"))
+    dg.dftfe_ham_apply(ham, X, Y2, dg.DFTFE_FP64_SLICES)
+    assert torch.equal(Y, Y2)
+
+
+@pytest.mark.parametrize("p,n,L", [(4, (8, 8, 8), 10.0), (5, (7, 7, 7), 10.0), (6, (6, 6, 6), 9.0),
+                                   (7, (4, 4, 5), 9.0)])
+def test_slices_apply_many_cells_per_cta(dg, p, n, L):
+    """More (cell, 64-column) items than SMs, for one to four 128-row M-tiles (p = 4 .. 7),
+    128 + 72 columns: the exact-slice apply within its bound."""
+    c = small_case(4, n=n, p=p, L=L, nl=True)
+    om, oh = oracle_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    mesh, ham = gpu_system(c["L"], c["n"], c["p"], c["centres"], c["depth"], c["width"], c["vquad"], c["proj"])
+    try:
+        X0 = synth.random_block(600 + p, om.ndofs, 200)
+        X = torch.from_numpy(X0).cuda()
+        Y = torch.full_like(X, float("nan"))
+        dg.dftfe_ham_apply(ham, X, Y, dg.DFTFE_FP64_SLICES)
+        err = np.abs(Y.cpu().numpy() - oh.apply(X0))
+        bound = slices_bound(om, oh, X0)
+        assert np.all(err <= bound), float((err / bound).max())
+    finally:
+        dg.dftfe_ham_destroy(ham)
+        dg.dftfe_mesh_destroy(mesh)
+
+
 @pytest.mark.parametrize("p,n,L", [(4, (8, 8, 8), 10.0), (5, (8, 8, 8), 10.0), (6, (6, 6, 6), 9.0)])
 def test_mixed_apply_many_cells_per_cta(dg, p, n, L):
     """More cells than SMs (each CTA of the persistent cell kernel walks several cells, so
