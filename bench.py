@@ -42,7 +42,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk/SM x 2.
 # launch of this workload processes N_c / 8 cells (FP64, one colour) or all N_c cells
 # (split precision), so traffic scales with the cells.  A kernel that changed since its
 # capture has no entry here (traffic null).
-DRAM_BYTES_PER_CELL = {"cell_gemm_fp64": (124.1e6 + 10.2e6) / 64}
+DRAM_BYTES_PER_CELL = {"cell_gemm_fp64": (124.1e6 + 10.2e6) / 64,
+                       # k_cell_tf32p<true>, one 128-column launch over 1,728 cells (p = 6)
+                       "cell_gemm_tf32x3": (1038.675e6 + 270.679e6) / 1728}
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -508,8 +510,9 @@ def scf_step(dg, dev, stream, steps=4, tol=1e-5):
     SCF-like sequences: sixteen independent systems (3^3-5^3 cells, p = 4-6, 16-40 states,
     3 Gaussian wells each, no projectors) whose atoms move 0.05 bohr per step with the potential
     mixed 0.3 old / 0.7 new.  From a common start (every system converged at its first
-    potential in FP64, untimed) each form must bring the largest residual of the lowest 3/4 of
-    every system's states to tol at each of the next `steps` potentials:
+    potential in FP64, untimed) each form must bring the largest generalised residual
+    ||H psi - eps M psi|| / ||psi|| (degree.Judge) of the lowest 3/4 of every system's states to
+    tol at each of the next `steps` potentials:
       fp64_one_by_one_standard   FP64 passes, one system at a time, Lanczos bound + degree 40
       tf32x3_one_by_one_standard TF32x3 passes, one system at a time, standard rule
       tf32x3_batched_standard    TF32x3 batched passes (one persistent cell launch per step)
@@ -591,7 +594,8 @@ def scf_step(dg, dev, stream, steps=4, tol=1e-5):
         one_by_one(dg.DFTFE_MIXED_TF32X3, None)               # warm-up of the split-precision workspaces
         out = {"workload": "16 systems, 3^3-5^3 cells, p 4-6, 16-40 states, 3 wells each; SCF-like sequence of "
                            f"{steps} potentials (atoms move 0.05 bohr per step, mixing 0.3/0.7)",
-               "tolerance": tol, "residual": "largest of the lowest 3/4 of every system's states, at every potential",
+               "tolerance": tol, "residual": "generalised ||H psi - eps M psi|| / ||psi|| from an FP64-accurate H~X, largest of "
+                           "the lowest 3/4 of every system's states, at every potential (check inside the timed region)",
                "training": {"sequences": len(systems), "samples": len(F), "loss_first_last": [loss[0], loss[-1]],
                             "target_degrees": {str(d): degs.count(d) for d in sorted(set(degs))}},
                "fp64_one_by_one_standard": one_by_one(dg.DFTFE_FP64, None),
@@ -667,7 +671,9 @@ def rooflines(fam, wl, precision):
         flops = 3 * 2.0 * Nc * nc * nc * B                         # three split products
         tb, tt = byt / (hbm_peak * 1e9), flops / (tensor_peak[p] * 1e12)
         tensor_bound = tt >= tb
-        r = {"kernel": f"k_cell_mixed<{p}> (gather + tcgen05 split cell products, FP32 TMEM accumulation)",
+        kname = ("k_cell_tf32p (FP32 plane split on chip, A from TMEM" if p == "tf32x3"
+                 else "k_cell_mixed<bf16x3> (pre-split tiles") + ", tcgen05, FP32 TMEM accumulation)"
+        r = {"kernel": kname,
              "bound": "tensor" if tensor_bound else "hbm",
              "achieved": flops / t / 1e12 if tensor_bound else byt / t / 1e9,
              "peak": tensor_peak[p] if tensor_bound else hbm_peak,

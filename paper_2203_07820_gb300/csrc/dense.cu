@@ -1064,7 +1064,12 @@ __global__ void k_lz_bound(const double* d, const double* Z, const double* beta,
   }
   out3[0] = d[imin];
   out3[1] = d[imax];
-  out3[2] = d[imax] + fabs(beta[k - 1]) * fabs(Z[(int64_t)(k - 1) * k + imax]);
+  // upper-bound estimator of Zhou and Saad: the largest Ritz value plus the norm of the last
+  // Lanczos residual |beta_k|.  (theta_max + |beta_k| |s_k|, the residual of that Ritz pair
+  // alone, undershoots when the top of the spectrum is clustered: measured on a periodic
+  // 27-cell p = 4 box, 30.21 against lambda_max = 30.54.)
+  (void)Z;
+  out3[2] = d[imax] + fabs(beta[k - 1]);
 }
 
 void lanczos(dftfe_ham h, int k, const double* v0, uint64_t seed, double* out3, bool cplx) {

@@ -66,7 +66,10 @@ def test_lanczos_bounds_bracket_spectrum():
     gersh = np.max(np.diag(Hd) + np.sum(np.abs(Hd), axis=1) - np.abs(np.diag(Hd)))
     assert b <= gersh
     assert tmin >= lam[0] - 1e-10 and tmax <= lam[-1] + 1e-10
-    assert b - lam[-1] < 0.1 * (lam[-1] - lam[0])
+    # b - lambda_max <= |beta_k| <= (lambda_max - lambda_min) / 2: every Lanczos coefficient
+    # beta_j = v_{j+1}^T (H - c) v_j (v_{j+1} orthogonal to v_j) is at most ||H - c|| with c
+    # the middle of the spectrum
+    assert b - lam[-1] <= 0.5 * (lam[-1] - lam[0]) + 1e-9
 
 
 def test_cholgs_orthonormal_and_span():
