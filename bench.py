@@ -164,7 +164,8 @@ def barrier(tdist, device):
 class OracleSample:
     """The FP64 oracle, as it stands, on a bounded sample of a workload, scaled to one pass.
 
-    The sample is a periodic box of 8^3 cells with the workload's cell size and degree
+    The sample is a periodic box of 16^3 cells (about 10 s of oracle work on 16 cores for
+    p = 6, 128 and 256 columns) with the workload's cell size and degree
     (so every cell matrix has the workload's shape), one well of the workload's depth and
     width with its four projectors (the workload's atom density), and seeded random
     blocks.  Timed through the oracle's own code path: `Hamiltonian.apply` (gather, cell
@@ -181,7 +182,7 @@ class OracleSample:
         self.wl = wl
         t0 = time.perf_counter()
         h = wl.L / wl.ncell
-        ncs = 8
+        ncs = 16
         Ls = ncs * h
         m = oracle.PeriodicMesh(Ls, ncs, wl.degree)
         ham = oracle.Hamiltonian(m)
@@ -191,7 +192,7 @@ class OracleSample:
             rowptr, node, chi = synth.projector_csr(m.node_xyz(), centre, wl.proj_width, wl.proj_cutoff, Ls)
             ham.set_nonlocal(wl.couplings[:4], rowptr, node, chi)
         ham.cell_matrices()                              # set-up, outside the pass
-        self.m, self.ham = m, ham
+        self.m, self.ham, self.ncs = m, ham, ncs
         self.ns = min(wl.nstates, 256)
         self.X = synth.random_block(wl.seed, m.ndofs, wl.block)
         self.Xs = synth.random_block(wl.seed + 1, m.ndofs, self.ns)
@@ -226,7 +227,7 @@ class OracleSample:
         work = 3 * t_apply + t_chol + t_rr + t_eig
         return {"value": value, "unit": "s/pass", "cores": os.cpu_count(), "kind": "oracle", "extrapolated": True,
                 "sample_s": work,
-                "sample": (f"oracle Hamiltonian.apply (gather, cell GEMMs, assembly, nonlocal) on an 8^3-cell "
+                "sample": (f"oracle Hamiltonian.apply (gather, cell GEMMs, assembly, nonlocal) on a {self.ncs}^3-cell "
                            f"box of the workload's cell shape ({m.ndofs} DoFs, 1 atom) x {B} columns "
                            f"({t_apply:.2f} s, median of 3), cholgs ({t_chol:.2f} s) and rayleigh_ritz ({t_rr:.2f} s, "
                            f"eigh {t_eig:.2f} s) on {ns} columns; scaled to {Nc} cells x {N} columns x "
