@@ -131,6 +131,19 @@ dftfe_status dftfe_mesh_destroy(dftfe_mesh mesh);
  * ham runs.  The mesh must outlive the ham. */
 dftfe_status dftfe_ham_create(dftfe_mesh mesh, void* stream, dftfe_ham* out);
 
+/* A second ham over src's mesh, on src's stream, that uses src's local operator: the cell
+ * matrices H~^c that dftfe_ham_set_potential(src, ...) forms and every form the library
+ * derives from them (the FP32 plane of the split products, the digit rows of the exact-slice
+ * products, the float pairs), built once on first use and read by both.  The local term
+ * -1/2 lap + V_loc is the same at every Bloch k-point of a system (Sec. 2.1: only the k terms
+ * and the projector phases depend on k), so the k-point hams of one system made this way
+ * hold one copy of it instead of one each.  The new ham has its own nonlocal term, k-point,
+ * workspace, graphs and autotuner.  dftfe_ham_set_potential on it returns DFTFE_ERR_STATE
+ * (set the potential on src; the change is seen by every ham that shares it), as does
+ * dftfe_ham_destroy(src) while a ham made from it exists.  src must own its operator (not be
+ * made by this call), and the current device must be src's (DFTFE_ERR_ARG otherwise). */
+dftfe_status dftfe_ham_create_shared(dftfe_ham src, dftfe_ham* out);
+
 /* Set the local potential (a2; Sec. 4.2, Eq. quadLocal / Eq. gemmLoc):
  * v_quad is DEVICE memory, ncells x quad_per_cell FP64 values V(x_q).  Forms
  * V^c for all cells with one packed-symmetric GEMM K = P V, adds the stiffness
@@ -169,9 +182,23 @@ dftfe_status dftfe_ham_apply(dftfe_ham ham, const double* X, int64_t ldx,
  * pass over the mesh for each column count (real columns: 2 ncol for the _z calls) times
  * every launch shape of the FP64 cell kernel -- 64, 128, ... rows of a cell per CTA, and the
  * built-in heuristic -- on the caller's block into a scratch output and keeps the fastest
- * for this ham (that first call synchronises the stream).  Every shape gives bit-identical
- * results.  enable = 0 restores the heuristic; either call forgets earlier choices. */
+ * for this ham (that first call synchronises the stream).  Likewise the first TF32x3
+ * cell-product launch of the split-precision filter (Sec. 4.3's cell products on the tensor
+ * cores) times every launch shape of that kernel -- the split A operand staged in tensor
+ * memory (where the accumulators leave room: at most three 128-row M-tiles, p <= 6) or in a
+ * shared-memory ring, and the cells dealt to the persistent CTAs round-robin or in contiguous
+ * ranges -- on the launch's own operands and keeps the fastest (queried with
+ * dftfe_autotune_query_mixed).  Tuning is skipped while the stream is being captured.  Every
+ * shape gives bit-identical results.  enable = 0 restores the defaults; either call forgets
+ * earlier choices. */
 dftfe_status dftfe_ham_autotune(dftfe_ham ham, int enable);
+
+/* The tuned TF32x3 cell-kernel shape of this ham's mesh: HOST atmem (1 = A operand in tensor
+ * memory, 0 = in shared memory, -1 = not tuned yet), deal (0 = round-robin, 1 = contiguous
+ * ranges, -1 = not tuned), best_ms and default_ms (one launch over all cells in the chosen and
+ * in the default shape -- tensor memory where it fits, round-robin; may be NULL). */
+dftfe_status dftfe_autotune_query_mixed(dftfe_ham ham, int* atmem, int* deal, double* best_ms,
+                                        double* default_ms);
 
 /* The tuned shape for ncol real columns: HOST rows_per_cta (0 = the heuristic won, -1 = not
  * tuned yet), best_ms and heuristic_ms (one cell-product pass over the mesh; may be NULL). */
@@ -423,7 +450,10 @@ typedef struct {
  * keeps pointers to them (destroy the batch first).  Potentials may change between passes. */
 dftfe_status dftfe_batch_create(const dftfe_ham* hams, int nsys, dftfe_batch* out);
 
-/* One pass for every system; items[i] belongs to hams[i].  prec is DFTFE_FP64 (shared FP64
+/* One pass for every system; items[i] belongs to hams[i].  The systems' pass tails (CholGS,
+ * Rayleigh-Ritz, residuals) run one after another and share one workspace that the batch owns
+ * (sized by the largest system, freed by dftfe_batch_destroy), so a batch of many k-point
+ * items holds one set of tail buffers instead of one per item.  prec is DFTFE_FP64 (shared FP64
  * launches as above) or DFTFE_MIXED_TF32X3: the split-precision filter of Sec. 4.3's cell
  * products on the tensor cores, where per Chebyshev step ONE persistent cell-product launch
  * per FE degree covers every cell of every system still filtering (a work list of
@@ -446,6 +476,25 @@ dftfe_status dftfe_batch_use_graphs(dftfe_batch batch, int enable);
 
 /* HOST counts of graph launches and instantiations of the batch since dftfe_batch_use_graphs. */
 dftfe_status dftfe_batch_graph_query(dftfe_batch batch, int64_t* replays, int64_t* instantiations);
+
+/* Autotuner of the batched split-precision filter.  With enable = 1, every distinct
+ * cell-product launch of a DFTFE_MIXED_TF32X3 batched pass (one FE degree's systems at one
+ * Chebyshev step: keyed by nodes per cell, work items, systems and distinct cell-matrix
+ * planes) is timed on its first appearance in every shape -- A operand in tensor memory or
+ * shared memory, round-robin or contiguous dealing, and the (system, cell) work list
+ * system-major or interleaved cell by cell across the systems, which lets the k-point hams of
+ * one system that share a local operator (dftfe_ham_create_shared) read each cell's FP32 tiles
+ * at about the same time, once from HBM -- and the fastest is used from then on.  Results are
+ * bit-identical to untuned passes.  Synchronises the stream; either call forgets earlier
+ * choices and makes the next graphed pass run directly. */
+dftfe_status dftfe_batch_autotune(dftfe_batch batch, int enable);
+
+/* The index-th tuned launch (in key order): HOST nodes per cell, work items, atmem, deal,
+ * order (0 = system-major, 1 = interleaved), best_ms and default_ms (may be NULL); every
+ * output -1 (0 for the times) when index is past the last. */
+dftfe_status dftfe_batch_autotune_query(dftfe_batch batch, int index, int* nodes_per_cell, int* work_items,
+                                        int* atmem, int* deal, int* order, double* best_ms,
+                                        double* default_ms);
 
 /* ------------------------------------------ learned degree / bounds proposer */
 /* The network that proposes the Chebyshev degree and the unwanted-interval bounds of the

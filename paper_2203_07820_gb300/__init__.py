@@ -45,6 +45,9 @@ DFTFE_MIXED_TF32X3 = 2
 DFTFE_FP64_FLOAT_PAIRS = 3
 DFTFE_FP64_SLICES = 4
 
+DFTFE_OK, DFTFE_ERR_ARG, DFTFE_ERR_OOM, DFTFE_ERR_CUDA = 0, 1, 2, 3
+DFTFE_ERR_NOT_SPD, DFTFE_ERR_NOCONV, DFTFE_ERR_TIMEOUT, DFTFE_ERR_STATE = 4, 5, 6, 7
+
 STATUS = {0: "DFTFE_OK", 1: "DFTFE_ERR_ARG", 2: "DFTFE_ERR_OOM", 3: "DFTFE_ERR_CUDA",
           4: "DFTFE_ERR_NOT_SPD", 5: "DFTFE_ERR_NOCONV", 6: "DFTFE_ERR_TIMEOUT",
           7: "DFTFE_ERR_STATE"}
@@ -80,6 +83,7 @@ _SIGS = {
     "dftfe_mesh_coords": [_vp, _vp, _vp],
     "dftfe_mesh_destroy": [_vp],
     "dftfe_ham_create": [_vp, _vp, C.POINTER(_vp)],
+    "dftfe_ham_create_shared": [_vp, C.POINTER(_vp)],
     "dftfe_ham_set_potential": [_vp, _vp],
     "dftfe_ham_set_nonlocal": [_vp, _int, _vp, _vp, _vp, _vp],
     "dftfe_ham_destroy": [_vp],
@@ -109,6 +113,10 @@ _SIGS = {
     "dftfe_graph_query": [_vp, C.POINTER(_i64), C.POINTER(_i64)],
     "dftfe_ham_autotune": [_vp, _int],
     "dftfe_autotune_query": [_vp, _int, C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
+    "dftfe_autotune_query_mixed": [_vp, C.POINTER(_int), C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
+    "dftfe_batch_autotune": [_vp, _int],
+    "dftfe_batch_autotune_query": [_vp, _int, C.POINTER(_int), C.POINTER(_int), C.POINTER(_int), C.POINTER(_int),
+                                   C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
     "dftfe_ham_set_kpoint": [_vp, _vp, _vp],
     "dftfe_mesh_kpoint_stencil": [_vp, _vp, _vp],
     "dftfe_ham_apply_z": [_vp, _vp, _i64, _vp, _i64, _int, _int],
@@ -207,6 +215,12 @@ def dftfe_ham_create(mesh, stream=None):
     return out
 
 
+def dftfe_ham_create_shared(src):
+    out = _vp()
+    _check(_lib.dftfe_ham_create_shared(src, C.byref(out)))
+    return out
+
+
 def dftfe_ham_set_potential(ham, v_quad):
     p, _ = _dev(v_quad.reshape(-1), "v_quad")
     _check(_lib.dftfe_ham_set_potential(ham, p))
@@ -259,6 +273,13 @@ def dftfe_autotune_query(ham, ncol):
     r, b, hm = _int(), _dbl(), _dbl()
     _check(_lib.dftfe_autotune_query(ham, int(ncol), C.byref(r), C.byref(b), C.byref(hm)))
     return r.value, b.value, hm.value
+
+
+def dftfe_autotune_query_mixed(ham):
+    """(atmem, deal, best_ms, default_ms) of the tuned TF32x3 cell-kernel shape; -1 = not tuned."""
+    a, d, b, dm = _int(), _int(), _dbl(), _dbl()
+    _check(_lib.dftfe_autotune_query_mixed(ham, C.byref(a), C.byref(d), C.byref(b), C.byref(dm)))
+    return a.value, d.value, b.value, dm.value
 
 
 # ------------------------------------------------------------ ChFSI steps
@@ -432,6 +453,24 @@ def dftfe_batch_graph_query(batch):
     r, n = _i64(), _i64()
     _check(_lib.dftfe_batch_graph_query(batch, C.byref(r), C.byref(n)))
     return r.value, n.value
+
+
+def dftfe_batch_autotune(batch, enable=True):
+    _check(_lib.dftfe_batch_autotune(batch, 1 if enable else 0))
+
+
+def dftfe_batch_autotune_query(batch):
+    """Every tuned launch of the batch: a list of dicts (nodes_per_cell, work_items, atmem,
+    deal, order, best_ms, default_ms)."""
+    out = []
+    while True:
+        v = [_int() for _ in range(5)]
+        b, dm = _dbl(), _dbl()
+        _check(_lib.dftfe_batch_autotune_query(batch, len(out), *[C.byref(x) for x in v], C.byref(b), C.byref(dm)))
+        if v[0].value < 0:
+            return out
+        out.append(dict(nodes_per_cell=v[0].value, work_items=v[1].value, atmem=v[2].value, deal=v[3].value,
+                        order=v[4].value, best_ms=b.value, default_ms=dm.value))
 
 
 def dftfe_batch_chfsi_pass(batch, Xs, blocks, degrees, bounds, evals, resids, prec=DFTFE_FP64):

@@ -160,7 +160,7 @@ extern "C" dftfe_status dftfe_lanczos(dftfe_ham h, int k, const double* v0, uint
   ABI_BEGIN
   DFTFE_REQUIRE(h && out3, "null argument");
   DFTFE_REQUIRE(k >= 1 && k <= 200, "k must be in 1..200");
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   lanczos(h, k, v0, seed, out3);
   ABI_END
 }
@@ -170,7 +170,7 @@ extern "C" dftfe_status dftfe_spectrum_bounds(dftfe_ham h, int k, uint64_t seed,
   ABI_BEGIN
   DFTFE_REQUIRE(h && out, "null argument");
   DFTFE_REQUIRE(k >= 1 && k <= 200 && nstates >= 1, "bad k / nstates");
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   double r[3];
   lanczos(h, k, nullptr, seed, r);
   const double frac = std::max(4.0 * nstates / (double)h->mesh->M, 0.05);
@@ -197,7 +197,7 @@ extern "C" dftfe_status dftfe_rayleigh_ritz(dftfe_ham h, double* X, int64_t ld, 
   DFTFE_REQUIRE(ncol >= 1 && ncol <= 2048 && ld >= ncol, "bad ncol / ld");
   DFTFE_REQUIRE(!HX || ldhx >= ncol, "bad ldhx");
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3, "unknown precision");
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   double* W = HX;
   int64_t ldw = ldhx;
   if (!W) {
@@ -229,7 +229,7 @@ extern "C" dftfe_status dftfe_chfsi_pass(dftfe_ham h, double* X, int64_t ld, int
   DFTFE_REQUIRE(std::isnan(inout->a0) || inout->a0 < inout->a, "need a0 < a for the scaled filter");
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
                 "unknown precision");
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   if (h->use_graphs) {
     chfsi_pass_graphed(h, X, ld, ncol, block, degree, inout, evals, resid, prec);
     return DFTFE_OK;

@@ -53,6 +53,13 @@ struct dftfe_batch_s {
   // descriptors of the batched split-precision filter (device buffer and its host staging)
   dftfe::DevBuf mixed_desc;
   std::vector<uint8_t> mixed_host;
+  // autotuner of the split-precision cell-product launches (dftfe_batch_autotune)
+  bool autotune = false;
+  std::map<std::string, dftfe::MixedShape> tuned;
+  // workspace of the per-system pass tails (CholGS, Rayleigh-Ritz, residuals), which run one
+  // system after another on the batch's stream: shared by every ham of the batch during its
+  // tail, sized by the largest, freed with the batch
+  std::map<std::string, dftfe::DevBuf> tail_ws;
   // CUDA graph of the filter phase (dftfe_batch_use_graphs)
   bool use_graphs = false;
   std::map<std::string, dftfe::GraphSlot> graphs;
@@ -189,7 +196,7 @@ static void batch_filter(dftfe_batch bt, dftfe_batch_item* items) {
         while (out == r.cur[s] || out == prev[s]) ++out;
         double alpha, s1, s2;
         cheb_coef(items[s].bounds, k, sigma[s], alpha, s1, s2);
-        d.Hc = h->d_Hc;
+        d.Hc = loc(h)->d_Hc;
         d.map = h->d_map;
         d.X = r.buf[s][r.cur[s]];
         d.ldx = r.lds[s][r.cur[s]];
@@ -298,7 +305,8 @@ static void batch_filter_mixed(dftfe_batch bt, dftfe_batch_item* items, int* err
       plan[j].push_back(MixedBlock{bt->hams[s], items[s].X + (int64_t)cw * j * items[s].block, cw * items[s].ld,
                                    cw * nb, items[s].degree, items[s].bounds, items[s].kpoint != 0});
     }
-  auto enqueue = plan_mixed_batch(plan, bt->stream, err, bt->mixed_desc, bt->mixed_host);
+  auto enqueue = plan_mixed_batch(plan, bt->stream, err, bt->mixed_desc, bt->mixed_host,
+                                  bt->autotune ? &bt->tuned : nullptr);
   if (!bt->use_graphs) {
     enqueue();
     return;
@@ -392,6 +400,7 @@ extern "C" dftfe_status dftfe_batch_destroy(dftfe_batch b) {
   for (auto& kv : b->graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  for (auto& kv : b->tail_ws) kv.second.release();
   delete b;
   ABI_END
 }
@@ -413,7 +422,7 @@ extern "C" dftfe_status dftfe_batch_chfsi_pass(dftfe_batch b, dftfe_batch_item* 
     DFTFE_REQUIRE(it.ncol <= h->mesh->M, "more columns than DoFs");
     DFTFE_REQUIRE(it.bounds.b > it.bounds.a, "need b > a");
     DFTFE_REQUIRE(std::isnan(it.bounds.a0) || it.bounds.a0 < it.bounds.a, "need a0 < a for the scaled filter");
-    if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+    if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   }
   {
     ProfScope ps(b->hams[0], "batch_filter");
@@ -429,13 +438,55 @@ extern "C" dftfe_status dftfe_batch_chfsi_pass(dftfe_batch b, dftfe_batch_item* 
       if (herr) throw Error(DFTFE_ERR_TIMEOUT, "batched mixed cell kernel: a bounded wait timed out");
     }
   }
-  for (int s = 0; s < ns; ++s)
+  for (int s = 0; s < ns; ++s) {
+    dftfe_ham h = b->hams[s];
+    struct TailWs {         // the batch's shared tail workspace while this system's tail runs
+      dftfe_ham h;
+      TailWs(dftfe_ham h_, std::map<std::string, DevBuf>* w) : h(h_) { h->tail_ws = w; }
+      ~TailWs() { h->tail_ws = nullptr; }
+    } guard(h, &b->tail_ws);
     if (items[s].kpoint)
-      chfsi_pass_tail_z(b->hams[s], items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
+      chfsi_pass_tail_z(h, items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
                         items[s].resid, prec);
     else
-      chfsi_pass_tail(b->hams[s], items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
+      chfsi_pass_tail(h, items[s].X, items[s].ld, items[s].ncol, &items[s].bounds, items[s].evals,
                       items[s].resid, prec);
+  }
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_batch_autotune(dftfe_batch b, int enable) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(b, "null batch");
+  DFTFE_REQUIRE(enable == 0 || enable == 1, "enable must be 0 or 1");
+  DFTFE_CHECK_CUDA(cudaStreamSynchronize(b->stream));
+  b->autotune = enable == 1;
+  b->tuned.clear();
+  for (auto& kv : b->graphs) kv.second.warm = false;   // cached graphs hold the old shapes
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_batch_autotune_query(dftfe_batch b, int index, int* nodes_per_cell, int* work_items,
+                                                   int* atmem, int* deal, int* order, double* best_ms,
+                                                   double* default_ms) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(b && nodes_per_cell && work_items && atmem && deal && order, "null argument");
+  DFTFE_REQUIRE(index >= 0, "index must be >= 0");
+  if (index >= (int)b->tuned.size()) {
+    *nodes_per_cell = *work_items = *atmem = *deal = *order = -1;
+    if (best_ms) *best_ms = 0.0;
+    if (default_ms) *default_ms = 0.0;
+    return DFTFE_OK;
+  }
+  auto it = b->tuned.begin();
+  std::advance(it, index);
+  *nodes_per_cell = std::atoi(it->first.c_str());
+  *work_items = std::atoi(it->first.c_str() + it->first.find('/') + 1);
+  *atmem = it->second.atmem;
+  *deal = it->second.deal;
+  *order = it->second.order;
+  if (best_ms) *best_ms = it->second.best_ms;
+  if (default_ms) *default_ms = it->second.default_ms;
   ABI_END
 }
 

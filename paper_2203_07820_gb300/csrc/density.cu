@@ -200,7 +200,7 @@ extern "C" dftfe_status dftfe_rayleigh_ritz_split(dftfe_ham h, const double* X, 
   DFTFE_REQUIRE(nfr >= 1 && nfr <= ncol && nfr <= 512 && ldfr >= nfr, "bad nfr / ldfr");
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
                 "unknown precision");
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   auto* m = h->mesh;
   const int N = ncol;
   const bool mixed = prec != DFTFE_FP64;

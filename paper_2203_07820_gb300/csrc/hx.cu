@@ -183,11 +183,11 @@ static void local_part_rows(dftfe_ham h, const double* X, int64_t ldx, double* Z
     ProfScope ps(h, "cell_gemm_fp64");
     if (ncol <= 1) {
       size_t sh = (size_t)nc * 1 * sizeof(double) + nc * sizeof(int32_t);
-      DFTFE_LAUNCH(k_cell_fp64_narrow<1>, (unsigned)n, 256, sh, h->stream, h->d_Hc, h->d_map, cells,
+      DFTFE_LAUNCH(k_cell_fp64_narrow<1>, (unsigned)n, 256, sh, h->stream, loc(h)->d_Hc, h->d_map, cells,
                    nc, X, ldx, Z, ldz, ncol, alpha);
     } else if (ncol <= 4) {
       size_t sh = (size_t)nc * 4 * sizeof(double) + nc * sizeof(int32_t);
-      DFTFE_LAUNCH(k_cell_fp64_narrow<4>, (unsigned)n, 256, sh, h->stream, h->d_Hc, h->d_map, cells,
+      DFTFE_LAUNCH(k_cell_fp64_narrow<4>, (unsigned)n, 256, sh, h->stream, loc(h)->d_Hc, h->d_map, cells,
                    nc, X, ldx, Z, ldz, ncol, alpha);
     } else {
       size_t sh = (size_t)nc * 32 * sizeof(double) + nc * sizeof(int32_t);
@@ -195,7 +195,7 @@ static void local_part_rows(dftfe_ham h, const double* X, int64_t ldx, double* Z
       const int splits = fp64_row_splits(h, n * tiles, nc);
       const int rows = rows_per_cta > 0 ? rows_per_cta : ((nc + splits - 1) / splits + 63) / 64 * 64;
       dim3 grid((unsigned)n, (unsigned)tiles, (unsigned)((nc + rows - 1) / rows));
-      DFTFE_LAUNCH(k_cell_fp64_wide, grid, 256, sh, h->stream, h->d_Hc, h->d_map, cells, nc, X, ldx, Z,
+      DFTFE_LAUNCH(k_cell_fp64_wide, grid, 256, sh, h->stream, loc(h)->d_Hc, h->d_map, cells, nc, X, ldx, Z,
                    ldz, ncol, alpha, rows);
     }
   }
@@ -266,7 +266,7 @@ void nonlocal_add_fp64(dftfe_ham h, const double* X, int64_t ldx, double* Z, int
 
 void apply_combo(dftfe_ham h, const double* X, int64_t ldx, const double* Xprev, int64_t ldp,
                  double* Z, int64_t ldz, int ncol, double alpha, double s1, double s2) {
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential before applying H");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential before applying H");
   auto* m = h->mesh;
   if (ncol <= 0) return;
   set_smem_attrs();
@@ -344,7 +344,7 @@ extern "C" dftfe_status dftfe_ham_apply(dftfe_ham h, const double* X, int64_t ld
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3 ||
                     prec == DFTFE_FP64_FLOAT_PAIRS || prec == DFTFE_FP64_SLICES,
                 "unknown precision");
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   if (prec == DFTFE_FP64_SLICES && !slices_applicable(h))
     throw Error(DFTFE_ERR_ARG, "exact-slice products need at most 682 nodes per cell (degree <= 7)");
   if (prec == DFTFE_FP64) apply_combo(h, X, ldx, nullptr, 0, Y, ldy, ncol, 1.0, 0.0, 0.0);
@@ -361,6 +361,8 @@ extern "C" dftfe_status dftfe_ham_autotune(dftfe_ham h, int enable) {
   DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
   h->autotune = enable == 1;
   h->tuned_fp64.clear();
+  h->tuned_mixed_done = false;
+  h->tuned_mixed = MixedShape{};
   // cached graphs hold the old launch shapes: the next pass of each runs directly again
   for (auto& kv : h->graphs) kv.second.warm = false;
   ABI_END
@@ -392,8 +394,20 @@ extern "C" dftfe_status dftfe_chebyshev_filter(dftfe_ham h, double* X, int64_t l
   DFTFE_REQUIRE(std::isnan(bounds->a0) || bounds->a0 < bounds->a, "need a0 < a for the scaled filter");
   DFTFE_REQUIRE(prec == DFTFE_FP64 || prec == DFTFE_MIXED_BF16X3 || prec == DFTFE_MIXED_TF32X3,
                 "unknown precision");
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   if (prec == DFTFE_FP64) chebyshev_filter(h, X, ld, ncol, degree, *bounds);
   else chebyshev_filter_mixed(h, X, ld, ncol, degree, *bounds, prec == DFTFE_MIXED_TF32X3);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_autotune_query_mixed(dftfe_ham h, int* atmem, int* deal, double* best_ms,
+                                                   double* default_ms) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(h && atmem && deal, "null argument");
+  const bool done = h->tuned_mixed_done;
+  *atmem = done ? h->tuned_mixed.atmem : -1;
+  *deal = done ? h->tuned_mixed.deal : -1;
+  if (best_ms) *best_ms = done ? h->tuned_mixed.best_ms : 0.0;
+  if (default_ms) *default_ms = done ? h->tuned_mixed.default_ms : 0.0;
   ABI_END
 }

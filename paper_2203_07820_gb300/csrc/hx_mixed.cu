@@ -461,11 +461,13 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
 
 // Work item g of a launch: cell g of `single` (work == NULL), or the (system, cell) pair
 // work[g] of the systems `items` (all of one degree: nc, nkc, nmt are the launch's).  Items
-// are dealt round-robin over the persistent grid.
+// are dealt to the persistent grid round-robin (deal = 0: CTA b takes b, b + grid, ...) or in
+// contiguous ranges (deal = 1: CTA b takes the b-th of grid near-equal ranges), a launch shape
+// the autotuner picks; every item is computed the same way either way.
 template <bool ATMEM>
 __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single, const mp::Item* __restrict__ items,
                                                                 const int2* __restrict__ work, int nwork, int nc,
-                                                                int nkc, int nmt, int* err) {
+                                                                int nkc, int nmt, int deal, int* err) {
   using namespace mp;
   using tc::mbar_arrive;
   using tc::mbar_init;
@@ -476,8 +478,10 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   using tc::tc_commit;
   constexpr int kLand = Cfg<ATMEM>::kLand, kStagesB = Cfg<ATMEM>::kStagesB;
   // the CTA's i-th work item: its system's operands and its cell
+  const int q_deal = nwork / (int)gridDim.x, r_deal = nwork % (int)gridDim.x;
+  const int64_t first = deal ? (int64_t)blockIdx.x * q_deal + min((int)blockIdx.x, r_deal) : 0;
   auto item_of = [&](int64_t i, int64_t& cell) -> Item {
-    const int64_t g = blockIdx.x + i * gridDim.x;
+    const int64_t g = deal ? first + i : blockIdx.x + i * gridDim.x;
     if (!work) {
       cell = g;
       return single;
@@ -520,7 +524,8 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh->tmem;
-  const int my_cells = nwork > (int)blockIdx.x ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int my_cells = deal ? q_deal + ((int)blockIdx.x < r_deal ? 1 : 0)
+                            : (nwork > (int)blockIdx.x ? (nwork - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
   const int rows8 = ((nc - 128 * (nmt - 1)) + 7) / 8 * 8;   // rows of the last M-tile, in atoms
   const int64_t kcb = kc_block_bytes(nmt, rows8);
 
@@ -785,15 +790,77 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
 }
 
-// the A-in-TMEM form when the accumulators leave room for it (at most three M-tiles)
+// one launch in the given shape (the A-in-TMEM form needs at most three M-tiles beside the A
+// slots; the default shape is that form where it fits, with round-robin dealing)
 static void launch_cell_tf32p(cudaStream_t s, unsigned grid, const mp::Item& one, const mp::Item* items,
-                              const int2* work, int nwork, int nc, int nkc, int nmt, int* err) {
-  if (nmt <= 3)
+                              const int2* work, int nwork, int nc, int nkc, int nmt, int* err,
+                              const MixedShape& shape = MixedShape{}) {
+  if (nmt <= 3 && shape.atmem)
     DFTFE_LAUNCH(k_cell_tf32p<true>, grid, mp::kThreads, mp::smem_bytes<true>(), s, one, items, work, nwork, nc, nkc,
-                 nmt, err);
+                 nmt, shape.deal, err);
   else
     DFTFE_LAUNCH(k_cell_tf32p<false>, grid, mp::kThreads, mp::smem_bytes<false>(), s, one, items, work, nwork, nc,
-                 nkc, nmt, err);
+                 nkc, nmt, shape.deal, err);
+}
+
+static bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  DFTFE_CHECK_CUDA(cudaStreamIsCapturing(s, &st));
+  return st != cudaStreamCaptureStatusNone;
+}
+
+// The autotuner of the TF32x3 cell-product launch: every candidate shape (A operand in tensor
+// memory where it fits, or in shared memory; round-robin or contiguous dealing; with
+// work_alt, the interleaved work list too) runs once untimed and three times timed (CUDA
+// events on the launch stream) on the launch's own operands, and the fastest is kept.  The
+// launches only write the per-cell products, which the real launch that follows rewrites, so
+// tuning changes no result.  The first candidate is the default shape.
+static MixedShape tune_cell_tf32p(cudaStream_t s, int sm, const mp::Item& one, const mp::Item* items, const int2* work,
+                                  const int2* work_alt, int nwork, int nc, int nkc, int nmt, int* err) {
+  std::vector<MixedShape> cands;
+  for (int order = 0; order < (work_alt ? 2 : 1); ++order)
+    for (int atmem = (nmt <= 3 ? 1 : 0); atmem >= 0; --atmem)
+      for (int deal = 0; deal < 2; ++deal) {
+        MixedShape c;
+        c.atmem = atmem;
+        c.deal = deal;
+        c.order = order;
+        cands.push_back(c);
+      }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DFTFE_CHECK_CUDA(cudaEventCreate(&e0));
+  DFTFE_CHECK_CUDA(cudaEventCreate(&e1));
+  const unsigned grid = (unsigned)std::min(nwork, sm);
+  MixedShape best = cands[0];
+  double tbest = 1e300, tdef = 0.0;
+  try {
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+      const MixedShape& c = cands[ci];
+      const int2* w = c.order ? work_alt : work;
+      launch_cell_tf32p(s, grid, one, items, w, nwork, nc, nkc, nmt, err, c);
+      DFTFE_CHECK_CUDA(cudaEventRecord(e0, s));
+      for (int r = 0; r < 3; ++r) launch_cell_tf32p(s, grid, one, items, w, nwork, nc, nkc, nmt, err, c);
+      DFTFE_CHECK_CUDA(cudaEventRecord(e1, s));
+      DFTFE_CHECK_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      DFTFE_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      const double t = ms / 3.0;
+      if (ci == 0) tdef = t;
+      if (t < tbest) {
+        tbest = t;
+        best = c;
+      }
+    }
+  } catch (...) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  best.best_ms = tbest;
+  best.default_ms = tdef;
+  return best;
 }
 
 static void set_tf32p_attrs() {
@@ -890,28 +957,29 @@ static uint8_t* mixed_tiles(dftfe_ham h, bool tf32, int* nkc_out, int* nmt_out) 
   *nmt_out = nmt;
   if (nmt > mx::kMaxMTiles) throw Error(DFTFE_ERR_ARG, "mixed precision supports at most 512 nodes per cell (p <= 7)");
   const int fmt = tf32 ? 1 : 0;
+  dftfe_ham o = loc(h);                 // the owner of the cell matrices and their split forms
   if (tf32) {
     // TF32x3: one FP32 plane, split in shared memory by the kernel
     const int rows8 = ((m->nc - 128 * (nmt - 1)) + 7) / 8 * 8;
     const size_t bytes = (size_t)m->Nc * nkc * (size_t)mp::kc_block_bytes(nmt, rows8);
-    uint8_t* A = (uint8_t*)ws_get(h, "mixed_plane_tf32", bytes);
-    if (h->mixed_version[fmt] != h->potential_version) {
-      DFTFE_LAUNCH(k_plane_cells, h->sm_count * 16, 256, 0, h->stream, h->d_Hc, (float*)A, m->Nc, m->nc, nkc, nmt,
+    uint8_t* A = (uint8_t*)ws_get(o, "mixed_plane_tf32", bytes);
+    if (o->mixed_version[fmt] != o->potential_version) {
+      DFTFE_LAUNCH(k_plane_cells, h->sm_count * 16, 256, 0, h->stream, o->d_Hc, (float*)A, m->Nc, m->nc, nkc, nmt,
                    rows8);
-      h->mixed_version[fmt] = h->potential_version;
+      o->mixed_version[fmt] = o->potential_version;
     }
     return A;
   }
   const char* name = "mixed_tiles_bf16";
   const size_t bytes = (size_t)m->Nc * nkc * nmt * 2 * mx::kTile;
-  uint8_t* A = (uint8_t*)ws_get(h, name, bytes);
-  if (h->mixed_version[fmt] != h->potential_version) {
+  uint8_t* A = (uint8_t*)ws_get(o, name, bytes);
+  if (o->mixed_version[fmt] != o->potential_version) {
     const int grid = h->sm_count * 16;
     if (tf32)
-      DFTFE_LAUNCH(k_split_cells<true>, grid, 256, 0, h->stream, h->d_Hc, A, m->Nc, m->nc, nkc, nmt);
+      DFTFE_LAUNCH(k_split_cells<true>, grid, 256, 0, h->stream, o->d_Hc, A, m->Nc, m->nc, nkc, nmt);
     else
-      DFTFE_LAUNCH(k_split_cells<false>, grid, 256, 0, h->stream, h->d_Hc, A, m->Nc, m->nc, nkc, nmt);
-    h->mixed_version[fmt] = h->potential_version;
+      DFTFE_LAUNCH(k_split_cells<false>, grid, 256, 0, h->stream, o->d_Hc, A, m->Nc, m->nc, nkc, nmt);
+    o->mixed_version[fmt] = o->potential_version;
   }
   return A;
 }
@@ -1026,7 +1094,13 @@ static void apply_combo_mixed(dftfe_ham h, bool tf32, const uint8_t* A, int nkc,
       ProfScope ps(h, tf32 ? "cell_gemm_tf32x3" : "cell_gemm_bf16x3");
       if (tf32) {
         const mp::Item one{A, h->d_map, X, Yc, ldx, col0, ncol};
-        launch_cell_tf32p(h->stream, grid, one, nullptr, nullptr, (int)m->Nc, m->nc, nkc, nmt, err);
+        if (h->autotune && !h->tuned_mixed_done && !capturing(h->stream)) {
+          h->tuned_mixed = tune_cell_tf32p(h->stream, h->sm_count, one, nullptr, nullptr, nullptr, (int)m->Nc, m->nc,
+                                           nkc, nmt, err);
+          h->tuned_mixed_done = true;
+        }
+        launch_cell_tf32p(h->stream, grid, one, nullptr, nullptr, (int)m->Nc, m->nc, nkc, nmt, err,
+                          h->autotune && h->tuned_mixed_done ? h->tuned_mixed : MixedShape{});
       } else
         DFTFE_LAUNCH(k_cell_mixed<false>, grid, mx::kThreads, sh, h->stream, A, h->d_map, (int)m->Nc, m->nc,
                      nkc, nmt, X, ldx, Yc, col0, ncol, err);
@@ -1125,8 +1199,9 @@ struct MixedRoundPlan {
   };
   struct CellLaunch {
     int k, tile, nc, nkc, nmt;
-    size_t item_off, work_off;
-    int nwork;
+    size_t item_off, work_off, work_off_alt;   // system-major and interleaved work lists
+    int nwork, nitems;
+    MixedShape shape;
   };
   std::vector<MixedBlock> blk;
   std::vector<Sys> sy;
@@ -1213,6 +1288,7 @@ static void plan_mixed_round(MixedRoundPlan& R, std::vector<mp::Item>& items, st
   // launch descriptors: per (step, tile, degree group) the items of the systems still
   // filtering, and one work list per distinct set of systems
   std::map<std::vector<int>, std::pair<size_t, int>> lists;
+  std::map<std::vector<int>, size_t> lists_alt;
   std::vector<CellLaunch>& launches = R.launches;
   launches.clear();
   std::vector<int> ncs;
@@ -1226,7 +1302,8 @@ static void plan_mixed_round(MixedRoundPlan& R, std::vector<mp::Item>& items, st
         for (int s = 0; s < ns; ++s)
           if ((int)steps[s].size() >= k && blk[s].h->mesh->nc == nc && blk[s].ncol > 128 * t) act.push_back(s);
         if (act.empty()) continue;
-        CellLaunch L{k, t, nc, sy[act[0]].nkc, sy[act[0]].nmt, items.size() - R.item_base, 0, 0};
+        CellLaunch L{k, t, nc, sy[act[0]].nkc, sy[act[0]].nmt, items.size() - R.item_base, 0, 0, 0,
+                     (int)act.size(), MixedShape{}};
         for (int s : act) {
           const StepSys& st = steps[s][k - 1];
           items.push_back(mp::Item{sy[s].A, blk[s].h->d_map, sy[s].buf[st.cur], sy[s].Yc, sy[s].ld32, 128 * t,
@@ -1240,8 +1317,17 @@ static void plan_mixed_round(MixedRoundPlan& R, std::vector<mp::Item>& items, st
             for (int64_t cidx = 0; cidx < Nc; ++cidx) work.push_back(make_int2(li, (int)cidx));
           }
           it = lists.emplace(act, std::make_pair(off, (int)(work.size() - R.work_base - off))).first;
+          // the same pairs interleaved: cell 0 of every system, then cell 1, ...
+          const size_t off_alt = work.size() - R.work_base;
+          int64_t ncmax = 0;
+          for (int s : act) ncmax = std::max<int64_t>(ncmax, blk[s].h->mesh->Nc);
+          for (int64_t cidx = 0; cidx < ncmax; ++cidx)
+            for (int li = 0; li < (int)act.size(); ++li)
+              if (cidx < blk[act[li]].h->mesh->Nc) work.push_back(make_int2(li, (int)cidx));
+          lists_alt.emplace(act, off_alt);
         }
         L.work_off = it->second.first;
+        L.work_off_alt = lists_alt.at(act);
         L.nwork = it->second.second;
         launches.push_back(L);
       }
@@ -1292,7 +1378,8 @@ static void enqueue_mixed_round(const MixedRoundPlan& R, cudaStream_t stream, in
         ProfScope ps(blk[0].h, "batch_cell_tf32x3");
         const mp::Item none{};
         launch_cell_tf32p(stream, (unsigned)std::min(L.nwork, sm), none, d_items + R.item_base + L.item_off,
-                          d_work + R.work_base + L.work_off, L.nwork, L.nc, L.nkc, L.nmt, err);
+                          d_work + R.work_base + (L.shape.order ? L.work_off_alt : L.work_off), L.nwork, L.nc, L.nkc,
+                          L.nmt, err, L.shape);
       }
       for (int s = 0; s < ns; ++s) {
         if ((int)steps[s].size() < k || blk[s].ncol <= 128 * t) continue;
@@ -1301,6 +1388,7 @@ static void enqueue_mixed_round(const MixedRoundPlan& R, cudaStream_t stream, in
         const StepSys& st = steps[s][k - 1];
         float* const* b3 = sy[s].buf;
         const int64_t l = sy[s].ld32;
+        ProfScope ps(h, "batch_assemble32");
         DFTFE_LAUNCH(k_assemble32, nblk((m->M + 7) / 8 * 256), 256, 0, stream, b3[st.out], l, b3[st.cur], l,
                      st.prev >= 0 ? b3[st.prev] : nullptr, l, sy[s].Yc, sy[s].nptr, sy[s].nslot,
                      P[s] ? h->d_nptr_all : nullptr, h->d_sproj, h->d_sval, P[s], ldP[s], m->M, 128 * t, blk[s].ncol,
@@ -1322,7 +1410,8 @@ static void enqueue_mixed_round(const MixedRoundPlan& R, cudaStream_t stream, in
 }
 
 std::function<void()> plan_mixed_batch(const std::vector<std::vector<MixedBlock>>& rounds, cudaStream_t stream,
-                                       int* err, DevBuf& desc, std::vector<uint8_t>& host_desc) {
+                                       int* err, DevBuf& desc, std::vector<uint8_t>& host_desc,
+                                       std::map<std::string, MixedShape>* tuned) {
   if (!g_mixed_attr) {
     set_tf32p_attrs();
     DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_mixed<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mixed_smem()));
@@ -1349,6 +1438,31 @@ std::function<void()> plan_mixed_batch(const std::vector<std::vector<MixedBlock>
   DFTFE_CHECK_CUDA(cudaMemcpyAsync(ddesc, host_desc.data(), host_desc.size(), cudaMemcpyHostToDevice, stream));
   const mp::Item* d_items = reinterpret_cast<const mp::Item*>(ddesc);
   const int2* d_work = reinterpret_cast<const int2*>(ddesc + woff);
+  // launch shapes: the tuned shape of each distinct launch (FE degree, systems, work items),
+  // timed on its first appearance when the batch tunes, else the default shape
+  if (tuned) {
+    const int sm = rounds.empty() || rounds[0].empty() ? 1 : rounds[0][0].h->sm_count;
+    for (MixedRoundPlan& R : *plans)
+      for (auto& L : R.launches) {
+        // key: FE degree (nodes per cell), work items, systems and distinct cell-matrix planes
+        std::vector<const uint8_t*> planes;
+        for (int q = 0; q < L.nitems; ++q) planes.push_back(items[R.item_base + L.item_off + q].A);
+        std::sort(planes.begin(), planes.end());
+        const size_t nplanes = (size_t)(std::unique(planes.begin(), planes.end()) - planes.begin());
+        const std::string key = std::to_string(L.nc) + "/" + std::to_string(L.nwork) + "/" +
+                                std::to_string(L.nitems) + "/" + std::to_string(nplanes);
+        auto it = tuned->find(key);
+        if (it == tuned->end()) {
+          if (capturing(stream)) continue;
+          const mp::Item none{};
+          MixedShape sh = tune_cell_tf32p(stream, sm, none, d_items + R.item_base + L.item_off,
+                                          d_work + R.work_base + L.work_off, d_work + R.work_base + L.work_off_alt,
+                                          L.nwork, L.nc, L.nkc, L.nmt, err);
+          it = tuned->emplace(key, sh).first;
+        }
+        L.shape = it->second;
+      }
+  }
   return [plans, stream, err, d_items, d_work]() {
     for (const MixedRoundPlan& R : *plans) enqueue_mixed_round(R, stream, err, d_items, d_work);
   };
@@ -1654,10 +1768,11 @@ static bool apply_df_tiled(dftfe_ham h, const double* X, int64_t ldx, double* Y,
   }
   const int RP = 32 * TM;
   const size_t n2 = (size_t)m->Nc * nc * RP;
-  float2* Hk = (float2*)ws_get(h, "cells_df_k", sizeof(float2) * n2);
-  if (h->df_version != h->potential_version) {
-    DFTFE_LAUNCH(k_split_df_k, nblk2((int64_t)n2), 256, 0, h->stream, h->d_Hc, Hk, (int64_t)m->Nc, nc, RP);
-    h->df_version = h->potential_version;
+  dftfe_ham o = loc(h);
+  float2* Hk = (float2*)ws_get(o, "cells_df_k", sizeof(float2) * n2);
+  if (o->df_version != o->potential_version) {
+    DFTFE_LAUNCH(k_split_df_k, nblk2((int64_t)n2), 256, 0, h->stream, o->d_Hc, Hk, (int64_t)m->Nc, nc, RP);
+    o->df_version = o->potential_version;
   }
   int* err = tc_err_flag(h, (int*)ws_get(h, "df_err", sizeof(int)));
   if (!h->deferred) DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));
@@ -1693,10 +1808,11 @@ void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy,
     attr = true;
   }
   const size_t n2 = (size_t)m->Nc * nc * nc;
-  float2* Hdf = (float2*)ws_get(h, "cells_df", sizeof(float2) * n2);
-  if (h->df_version != h->potential_version) {
-    DFTFE_LAUNCH(k_split_df, nblk2((int64_t)n2), 256, 0, h->stream, h->d_Hc, Hdf, (int64_t)n2);
-    h->df_version = h->potential_version;
+  dftfe_ham o = loc(h);
+  float2* Hdf = (float2*)ws_get(o, "cells_df", sizeof(float2) * n2);
+  if (o->df_version != o->potential_version) {
+    DFTFE_LAUNCH(k_split_df, nblk2((int64_t)n2), 256, 0, h->stream, o->d_Hc, Hdf, (int64_t)n2);
+    o->df_version = o->potential_version;
   }
   // zero output and the FP64 nonlocal part, then the cell products colour by colour
   df_init(h, X, ldx, Y, ldy, ncol, with_nl);

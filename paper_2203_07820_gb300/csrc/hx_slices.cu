@@ -538,12 +538,13 @@ bool apply_slices(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t 
     attr = true;
   }
   const int64_t cell_bytes = (int64_t)nks * ((nmt - 1) * 128 + rows8) * kRowBytes;
-  uint8_t* A = (uint8_t*)ws_get(h, "cells_slices", (size_t)(m->Nc * cell_bytes));
-  int32_t* eA = (int32_t*)ws_get(h, "cells_slices_e", sizeof(int32_t) * (size_t)m->Nc * nmt * 128);
-  if (h->slices_version != h->potential_version) {
-    DFTFE_LAUNCH(k_cell_digits, nblk_oz(m->Nc * nmt * 128, 128), 128, 0, h->stream, h->d_Hc, m->Nc, nc, nmt, rows8,
+  dftfe_ham o = loc(h);                 // the owner of the cell matrices and their digit rows
+  uint8_t* A = (uint8_t*)ws_get(o, "cells_slices", (size_t)(m->Nc * cell_bytes));
+  int32_t* eA = (int32_t*)ws_get(o, "cells_slices_e", sizeof(int32_t) * (size_t)m->Nc * nmt * 128);
+  if (o->slices_version != o->potential_version) {
+    DFTFE_LAUNCH(k_cell_digits, nblk_oz(m->Nc * nmt * 128, 128), 128, 0, h->stream, o->d_Hc, m->Nc, nc, nmt, rows8,
                  nks, A, eA);
-    h->slices_version = h->potential_version;
+    o->slices_version = o->potential_version;
   }
   int* err = tc_err_flag(h, (int*)ws_get(h, "slices_err", sizeof(int)));
   if (!h->deferred) DFTFE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), h->stream));

@@ -99,6 +99,19 @@ struct TunedShape {
   double heuristic_ms = 0.0;
 };
 
+// A launch shape of the TF32x3 cell-product kernel, as the autotuner picks it: the split A
+// operand staged in tensor memory (atmem = 1, at most three 128-row M-tiles) or in a
+// shared-memory ring (0); work items dealt to the persistent CTAs round-robin (deal = 0) or
+// in contiguous ranges (1); in a batched launch, the work list system-major (order = 0) or
+// interleaved cell by cell across the systems (1, so the k-point items that share one FP32
+// plane read each cell's tiles at about the same time).  Every shape computes every cell
+// product the same way.  best_ms / default_ms: the timed launch in this shape and in the
+// default one (0 when not tuned).
+struct MixedShape {
+  int atmem = 1, deal = 0, order = 0;
+  double best_ms = 0.0, default_ms = 0.0;
+};
+
 // A CUDA graph of one enqueued region (graph.cu), re-captured on every call and applied to the
 // cached executable by cudaGraphExecUpdate (new bounds change only kernel arguments).
 struct GraphSlot {
@@ -171,6 +184,8 @@ struct dftfe_ham_s {
   // autotuner (dftfe_ham_autotune): FP64 cell-kernel shape per real column count
   bool autotune = false;
   std::map<int, dftfe::TunedShape> tuned_fp64;
+  bool tuned_mixed_done = false;       // the TF32x3 cell-kernel shape of this mesh (one per ham)
+  dftfe::MixedShape tuned_mixed;
   // bounded device waits (dftfe_ham_set_wait_test): spin limit of the eigensolver's grid
   // barrier (0 = the built-in limit of about a second) and arrivals withheld from it (a test
   // makes the wait run out with 1)
@@ -184,6 +199,14 @@ struct dftfe_ham_s {
   bool deferred = false;
   int* d_pass = nullptr;
   void* h_pass = nullptr;
+  // a ham made by dftfe_ham_create_shared uses the local operator of local_src (its cell
+  // matrices and every form derived from them, built on first use into local_src's
+  // workspace); `sharers` counts the hams that use this one's
+  dftfe_ham_s* local_src = nullptr;
+  int sharers = 0;
+  // while a batched pass runs this ham's tail: the batch's shared tail workspace, which the
+  // tail's buffers (names in ws_get's list) come from instead of `ws`
+  std::map<std::string, dftfe::DevBuf>* tail_ws = nullptr;
   // workspace
   std::map<std::string, dftfe::DevBuf> ws;
   // profiling
@@ -194,6 +217,10 @@ struct dftfe_ham_s {
 namespace dftfe {
 
 void* ws_get(dftfe_ham h, const char* name, size_t bytes);
+
+// the ham that owns h's local operator (h itself unless it was made by
+// dftfe_ham_create_shared)
+inline dftfe_ham loc(dftfe_ham h) { return h->local_src ? h->local_src : h; }
 
 // the device status words of a deferred pass that a rotation of X or W checks (NULL: none)
 inline const int* rot_guard(dftfe_ham h) { return h->deferred ? h->d_pass : nullptr; }
@@ -242,8 +269,11 @@ struct MixedBlock {
 // step, tile and degree group over all systems' cells.  Plans every round (workspaces, host
 // descriptors uploaded into desc, staged through host_desc) and returns the closure that
 // enqueues all launches on `stream`; err is zeroed and read by the caller.
+// tuned: the batch's launch shapes by launch key, filled by timing the first appearance of a
+// key (NULL: default shapes, no tuning)
 std::function<void()> plan_mixed_batch(const std::vector<std::vector<MixedBlock>>& rounds, cudaStream_t stream,
-                                       int* err, DevBuf& desc, std::vector<uint8_t>& host_desc);
+                                       int* err, DevBuf& desc, std::vector<uint8_t>& host_desc,
+                                       std::map<std::string, MixedShape>* tuned = nullptr);
 // with_nl = false: the local part only (real view of a complex block)
 void apply_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int64_t ldy, int ncol, bool with_nl = true);
 // hx_slices.cu: Y = H~X from exact bf16 digit products on the tensor cores (FP64-accurate;

@@ -97,35 +97,83 @@ __global__ void __launch_bounds__(256) k_kin_init(double2* Z, int64_t ldz,
   Z[i * ldz + c] = z;
 }
 
-// P[a][col] = h_a sum_{e in supp a} conj(C~^k_e) X[node_e][col]; one CTA per (projector, 32 cols)
-__global__ void __launch_bounds__(256) k_nl_coef_z(const double2* __restrict__ X, int64_t ldx, int ncol,
-                                                   const int64_t* __restrict__ prow,
-                                                   const int32_t* __restrict__ pnode,
-                                                   const double2* __restrict__ pval,
-                                                   const double* __restrict__ hcoup, double2* __restrict__ P) {
-  __shared__ double2 red[8][32];
-  const int a = blockIdx.x;
+// The same coefficients split over each projector's support, so that a long support does not
+// run as one latency-bound chain of dependent loads per warp: CTA (a, s) sums split s of
+// projector a's entries (warp w every 8th entry of the split, lane l complex column
+// 32 blockIdx.y + l) into part[a S + s][col]; k_nl_coefz_reduce adds the S splits in order and
+// scales by h_a.  C is float2 (the complex64 filter) or double2.
+constexpr int kNlzSplits = 8;
+template <typename C>
+__global__ void __launch_bounds__(256) k_nl_coefz_part(const C* __restrict__ X, int64_t ldx, int ncol,
+                                                       const int64_t* __restrict__ prow,
+                                                       const int32_t* __restrict__ pnode, const C* __restrict__ pval,
+                                                       C* __restrict__ part) {
+  using R = decltype(C::x);
+  __shared__ C red[8][32];
+  const int a = blockIdx.x / kNlzSplits, sidx = blockIdx.x % kNlzSplits;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.y * 32 + lane;
-  double sr = 0.0, si = 0.0;
-  if (col < ncol)
-    for (int64_t e = prow[a] + warp; e < prow[a + 1]; e += 8) {
-      const double2 cv = pval[e];
-      const double2 xv = X[(int64_t)pnode[e] * ldx + col];
+  const int64_t e0 = prow[a], e1 = prow[a + 1];
+  const int64_t len = (e1 - e0 + kNlzSplits - 1) / kNlzSplits;
+  const int64_t s0 = e0 + sidx * len, s1 = min(e1, s0 + len);
+  R sr = 0, si = 0;
+  if (col < ncol) {
+#pragma unroll 4
+    for (int64_t e = s0 + warp; e < s1; e += 8) {
+      const C cv = pval[e];
+      const C xv = X[(int64_t)pnode[e] * ldx + col];
       sr = fma(cv.x, xv.x, fma(cv.y, xv.y, sr));
       si = fma(cv.x, xv.y, fma(-cv.y, xv.x, si));
     }
-  red[warp][lane] = make_double2(sr, si);
+  }
+  C v;
+  v.x = sr;
+  v.y = si;
+  red[warp][lane] = v;
   __syncthreads();
   if (warp == 0 && col < ncol) {
-    double tr = 0.0, ti = 0.0;
+    R tr = 0, ti = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
       tr += red[w][lane].x;
       ti += red[w][lane].y;
     }
-    P[(int64_t)a * ncol + col] = make_double2(hcoup[a] * tr, hcoup[a] * ti);
+    C o;
+    o.x = tr;
+    o.y = ti;
+    part[(int64_t)blockIdx.x * ncol + col] = o;
   }
+}
+
+template <typename C>
+__global__ void k_nl_coefz_reduce(const C* __restrict__ part, const double* __restrict__ hcoup, int nproj, int ncol,
+                                  C* __restrict__ P) {
+  using R = decltype(C::x);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nproj * ncol) return;
+  const int a = (int)(t / ncol), col = (int)(t % ncol);
+  R sr = 0, si = 0;
+  for (int k = 0; k < kNlzSplits; ++k) {
+    const C v = part[((int64_t)a * kNlzSplits + k) * ncol + col];
+    sr += v.x;
+    si += v.y;
+  }
+  const R hv = (R)hcoup[a];
+  C o;
+  o.x = hv * sr;
+  o.y = hv * si;
+  P[t] = o;
+}
+
+// P = h (C~^kH X) for ncol complex columns through the split kernels above
+template <typename C>
+static void nl_coef_z_split(dftfe_ham h, const C* X, int64_t ldx, int ncol, const C* pval, C* P) {
+  C* part = (C*)ws_get(h, sizeof(C) == 8 ? "nl_coefz32_part" : "nl_coefz_part",
+                       sizeof(C) * (size_t)h->nproj * kNlzSplits * ncol);
+  dim3 g1((unsigned)(h->nproj * kNlzSplits), (unsigned)((ncol + 31) / 32));
+  DFTFE_LAUNCH(k_nl_coefz_part<C>, g1, 256, 0, h->stream, X, ldx, ncol, h->d_prow, h->d_pnode, pval, part);
+  DFTFE_LAUNCH(k_nl_coefz_reduce<C>, nblk((int64_t)h->nproj * ncol), 256, 0, h->stream, part, h->d_h, h->nproj,
+               ncol, P);
 }
 
 // Z[node][col] += alpha sum_{t in node's projectors} C~^k_t P[proj_t][col]; one warp per node
@@ -157,64 +205,58 @@ __global__ void __launch_bounds__(256) k_kin_add32(float2* __restrict__ Z, int64
                                                    const float2* __restrict__ X, int64_t ldx, int64_t M, int ncol,
                                                    float alpha, const float* __restrict__ tab, int p, int64_t g0,
                                                    int64_t g1, int kbits) {
+  // one warp per node (its mesh position computed once, in 32-bit arithmetic: M < 2^31);
+  // lane l takes complex columns 64 blockIdx.y + 2l and + 1 (one 16-byte load per
+  // neighbour row); the neighbours are summed axis by axis in increasing offset, per column
   extern __shared__ float tsf[];
   const int W = 2 * p + 1;
   for (int t = threadIdx.x; t < 3 * p * W; t += blockDim.x) tsf[t] = tab[t];
   __syncthreads();
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= M * ncol) return;
-  const int64_t i = t / ncol;
-  const int c = (int)(t - i * ncol);
-  const int64_t pos[3] = {i % g0, (i / g0) % g1, i / (g0 * g1)};
-  const int64_t ext[3] = {g0, g1, M / (g0 * g1)};
-  const int64_t stride[3] = {1, g0, g0 * g1};
-  float sr = 0.f, si = 0.f;
+  const unsigned i = blockIdx.x * 8u + (threadIdx.x >> 5);
+  const int c = blockIdx.y * 64 + 2 * (threadIdx.x & 31);
+  if ((int64_t)i >= M || c >= ncol) return;
+  const bool two = c + 1 < ncol;
+  const unsigned G0 = (unsigned)g0, G1 = (unsigned)g1, G2 = (unsigned)M / (G0 * G1);
+  const unsigned iy_all = i / G0;
+  const unsigned pos[3] = {i - iy_all * G0, iy_all % G1, iy_all / G1};
+  const unsigned ext[3] = {G0, G1, G2};
+  const unsigned stride[3] = {1u, G0, G0 * G1};
+  float sr0 = 0.f, si0 = 0.f, sr1 = 0.f, si1 = 0.f;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (!(kbits & (1 << d))) continue;
-    const int a = (int)(pos[d] % p);
-    const float* T = tsf + ((size_t)d * p + a) * W + p;
+    const int a = (int)(pos[d] % (unsigned)p);
+    const float* T = tsf + (d * p + a) * W + p;
     for (int o = a == 0 ? -p : -a; o <= p - a; ++o) {
-      int64_t j = pos[d] + o;
-      j += j < 0 ? ext[d] : (j >= ext[d] ? -ext[d] : 0);
-      const float2 v = X[(i + (j - pos[d]) * stride[d]) * ldx + c];
-      sr = fmaf(T[o], v.x, sr);
-      si = fmaf(T[o], v.y, si);
+      int j = (int)pos[d] + o;
+      j += j < 0 ? (int)ext[d] : (j >= (int)ext[d] ? -(int)ext[d] : 0);
+      const unsigned row = i + (unsigned)(j - (int)pos[d]) * stride[d];
+      const float2* src = X + (int64_t)row * ldx + c;
+      const float t = T[o];
+      if (two) {
+        const float4 v = *reinterpret_cast<const float4*>(src);
+        sr0 = fmaf(t, v.x, sr0);
+        si0 = fmaf(t, v.y, si0);
+        sr1 = fmaf(t, v.z, sr1);
+        si1 = fmaf(t, v.w, si1);
+      } else {
+        const float2 v = *src;
+        sr0 = fmaf(t, v.x, sr0);
+        si0 = fmaf(t, v.y, si0);
+      }
     }
   }
-  float2* z = Z + i * ldz + c;
-  z->x = fmaf(alpha, si, z->x);
-  z->y = fmaf(-alpha, sr, z->y);
-}
-
-__global__ void __launch_bounds__(256) k_nl_coef32_z(const float2* __restrict__ X, int64_t ldx, int ncol,
-                                                     const int64_t* __restrict__ prow,
-                                                     const int32_t* __restrict__ pnode,
-                                                     const float2* __restrict__ pval,
-                                                     const double* __restrict__ hcoup, float2* __restrict__ P) {
-  __shared__ float2 red[8][32];
-  const int a = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col = blockIdx.y * 32 + lane;
-  float sr = 0.f, si = 0.f;
-  if (col < ncol)
-    for (int64_t e = prow[a] + warp; e < prow[a + 1]; e += 8) {
-      const float2 cv = pval[e];
-      const float2 xv = X[(int64_t)pnode[e] * ldx + col];
-      sr = fmaf(cv.x, xv.x, fmaf(cv.y, xv.y, sr));
-      si = fmaf(cv.x, xv.y, fmaf(-cv.y, xv.x, si));
-    }
-  red[warp][lane] = make_float2(sr, si);
-  __syncthreads();
-  if (warp == 0 && col < ncol) {
-    float tr = 0.f, ti = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) {
-      tr += red[w][lane].x;
-      ti += red[w][lane].y;
-    }
-    const float hv = (float)hcoup[a];
-    P[(int64_t)a * ncol + col] = make_float2(hv * tr, hv * ti);
+  float2* z = Z + (int64_t)i * ldz + c;
+  if (two) {
+    float4 zv = *reinterpret_cast<float4*>(z);
+    zv.x = fmaf(alpha, si0, zv.x);
+    zv.y = fmaf(-alpha, sr0, zv.y);
+    zv.z = fmaf(alpha, si1, zv.z);
+    zv.w = fmaf(-alpha, sr1, zv.w);
+    *reinterpret_cast<float4*>(z) = zv;
+  } else {
+    z->x = fmaf(alpha, si0, z->x);
+    z->y = fmaf(-alpha, sr0, z->y);
   }
 }
 
@@ -347,7 +389,7 @@ static int kbits_of(dftfe_ham h) {
 }
 
 void require_kpoint(dftfe_ham h) {
-  if (!h->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
+  if (!loc(h)->has_potential) throw Error(DFTFE_ERR_STATE, "set the potential first");
   if (!h->has_kpoint) throw Error(DFTFE_ERR_STATE, "set the k-point first (dftfe_ham_set_kpoint)");
   if (h->nproj > 0 && !h->kpoint_nl)
     throw Error(DFTFE_ERR_STATE, "the projectors changed: call dftfe_ham_set_kpoint again");
@@ -368,9 +410,7 @@ void kpoint_init_terms(dftfe_ham h, const double* X, int64_t ldx, const double* 
   if (h->nproj > 0) {
     ProfScope ps(h, "nl_z");
     double2* P = (double2*)ws_get(h, "nl_coef_z", sizeof(double2) * h->nproj * (size_t)ncol);
-    dim3 g1((unsigned)h->nproj, (unsigned)((ncol + 31) / 32));
-    DFTFE_LAUNCH(k_nl_coef_z, g1, 256, 0, h->stream, (const double2*)X, ldx, ncol, h->d_prow, h->d_pnode,
-                 (const double2*)h->d_pval_z, h->d_h, P);
+    nl_coef_z_split(h, (const double2*)X, ldx, ncol, (const double2*)h->d_pval_z, P);
     dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
     DFTFE_LAUNCH(k_nl_add_z, g2, 256, 0, h->stream, (double2*)Z, ldz, ncol, h->d_snode, h->d_srow, h->d_sproj,
                  (const double2*)h->d_sval_z, P, h->nsup, alpha);
@@ -393,15 +433,16 @@ void kpoint_add32(dftfe_ham h, const float* X, int64_t ldx, float* Z, int64_t ld
   {
     ProfScope ps(h, "kin_k32");
     const size_t sh = sizeof(float) * 3 * p * (2 * p + 1);
-    DFTFE_LAUNCH(k_kin_add32, nblk(m->M * ncolz), 256, sh, h->stream, (float2*)Z, ldz / 2, (const float2*)X, ldx / 2,
+    // 8 nodes per CTA, 64 complex columns per blockIdx.y; the complex row strides ldx / 2 and
+    // ldz / 2 are multiples of 2, so the two-column accesses are 16-byte aligned
+    dim3 grid((unsigned)((m->M + 7) / 8), (unsigned)((ncolz + 63) / 64));
+    DFTFE_LAUNCH(k_kin_add32, grid, 256, sh, h->stream, (float2*)Z, ldz / 2, (const float2*)X, ldx / 2,
                  m->M, ncolz, alpha, h->d_ktab32, p, m->g[0], m->g[1], kbits_of(h));
   }
   if (h->nproj > 0) {
     ProfScope ps(h, "nl_z32");
     float2* P = (float2*)ws_get(h, "nl_coef32_z", sizeof(float2) * h->nproj * (size_t)ncolz);
-    dim3 g1((unsigned)h->nproj, (unsigned)((ncolz + 31) / 32));
-    DFTFE_LAUNCH(k_nl_coef32_z, g1, 256, 0, h->stream, (const float2*)X, ldx / 2, ncolz, h->d_prow, h->d_pnode,
-                 (const float2*)h->d_pval_z32, h->d_h, P);
+    nl_coef_z_split(h, (const float2*)X, ldx / 2, ncolz, (const float2*)h->d_pval_z32, P);
     dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncolz + 31) / 32));
     DFTFE_LAUNCH(k_nl_add32_z, g2, 256, 0, h->stream, (float2*)Z, ldz / 2, ncolz, h->d_snode, h->d_srow, h->d_sproj,
                  (const float2*)h->d_sval_z32, P, h->nsup, alpha);
@@ -429,9 +470,7 @@ static void apply_z_df(dftfe_ham h, const double* X, int64_t ldx, double* Y, int
   if (h->nproj > 0) {
     ProfScope ps(h, "nl_z");
     double2* P = (double2*)ws_get(h, "nl_coef_z", sizeof(double2) * h->nproj * (size_t)ncol);
-    dim3 g1((unsigned)h->nproj, (unsigned)((ncol + 31) / 32));
-    DFTFE_LAUNCH(k_nl_coef_z, g1, 256, 0, h->stream, (const double2*)X, ldx, ncol, h->d_prow, h->d_pnode,
-                 (const double2*)h->d_pval_z, h->d_h, P);
+    nl_coef_z_split(h, (const double2*)X, ldx, ncol, (const double2*)h->d_pval_z, P);
     dim3 g2((unsigned)((h->nsup + 7) / 8), (unsigned)((ncol + 31) / 32));
     DFTFE_LAUNCH(k_nl_add_z, g2, 256, 0, h->stream, (double2*)Y, ldy, ncol, h->d_snode, h->d_srow, h->d_sproj,
                  (const double2*)h->d_sval_z, P, h->nsup, 1.0);

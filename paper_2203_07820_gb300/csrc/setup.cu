@@ -43,8 +43,20 @@ void DevBuf::release() {
   bytes = 0;
 }
 
+// buffers that live only inside one pass tail (CholGS, Rayleigh-Ritz, residuals): in a batched
+// pass they come from the batch's shared tail workspace
+static bool tail_buffer(const char* name) {
+  static const char* const names[] = {"S", "Zinv", "gram_part", "Hhat", "Q", "W", "chol_d0", "chol_linv",
+                                      "eig_V", "eigz_V", "eig_vec", "eig_perm", "resid_part", "coldot_part",
+                                      "gram32_part", "rotmix_Zf", "rotmix_zd", "Hz", "Qz", "rot_tc_tiles",
+                                      "rot_tc_zd", "rot_tc_out", "gram_tc_part", "slices_x", "slices_xe"};
+  for (const char* n : names)
+    if (std::strcmp(n, name) == 0) return true;
+  return false;
+}
+
 void* ws_get(dftfe_ham h, const char* name, size_t bytes) {
-  DevBuf& b = h->ws[name];
+  DevBuf& b = (h->tail_ws && tail_buffer(name)) ? (*h->tail_ws)[name] : h->ws[name];
   if (bytes > b.bytes && b.ptr) DFTFE_CHECK_CUDA(cudaStreamSynchronize(h->stream));
   return b.get(bytes);
 }
@@ -306,12 +318,13 @@ extern "C" dftfe_status dftfe_mesh_destroy(dftfe_mesh m) {
 }
 
 // ----------------------------------------------------------------- ABI: ham
-extern "C" dftfe_status dftfe_ham_create(dftfe_mesh m, void* stream, dftfe_ham* out) {
-  ABI_BEGIN
-  DFTFE_REQUIRE(m && out, "null argument");
+// A ham over mesh m on `stream`; with src, one that uses src's local operator (no cell
+// matrices or packed basis products of its own).
+static dftfe_ham create_ham(dftfe_mesh m, void* stream, dftfe_ham src) {
   auto* h = new dftfe_ham_s();
   try {
     h->mesh = m;
+    h->local_src = src;
     h->stream = (cudaStream_t)stream;
     DFTFE_CHECK_CUDA(cudaGetDevice(&h->device));
     DFTFE_CHECK_CUDA(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
@@ -407,25 +420,48 @@ extern "C" dftfe_status dftfe_ham_create(dftfe_mesh m, void* stream, dftfe_ham* 
         }
       }
       h->d_Nq = dev_upload(Nq, s);
-      double* d_Lq = dev_upload(m->Lq, s);
-      DFTFE_CHECK_CUDA(cudaMalloc(&h->d_P, sizeof(double) * Msym * m->nq));
-      DFTFE_LAUNCH(k_products, nblk(Msym * m->nq), 256, 0, s, h->d_P, h->d_pairs, d_Lq, Msym,
-                   m->nq1, n1);
-      DFTFE_CHECK_CUDA(cudaStreamSynchronize(s));
-      cudaFree(d_Lq);
+      if (!src) {
+        double* d_Lq = dev_upload(m->Lq, s);
+        DFTFE_CHECK_CUDA(cudaMalloc(&h->d_P, sizeof(double) * Msym * m->nq));
+        DFTFE_LAUNCH(k_products, nblk(Msym * m->nq), 256, 0, s, h->d_P, h->d_pairs, d_Lq, Msym,
+                     m->nq1, n1);
+        DFTFE_CHECK_CUDA(cudaStreamSynchronize(s));
+        cudaFree(d_Lq);
+      }
     }
-    DFTFE_CHECK_CUDA(cudaMalloc(&h->d_Hc, sizeof(double) * m->Nc * (int64_t)nc * nc));
+    if (!src) DFTFE_CHECK_CUDA(cudaMalloc(&h->d_Hc, sizeof(double) * m->Nc * (int64_t)nc * nc));
   } catch (...) {
+    h->local_src = nullptr;
     dftfe_ham_destroy(h);
     throw;
   }
-  *out = h;
+  if (src) src->sharers++;
+  return h;
+}
+
+extern "C" dftfe_status dftfe_ham_create(dftfe_mesh m, void* stream, dftfe_ham* out) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(m && out, "null argument");
+  *out = create_ham(m, stream, nullptr);
+  ABI_END
+}
+
+extern "C" dftfe_status dftfe_ham_create_shared(dftfe_ham src, dftfe_ham* out) {
+  ABI_BEGIN
+  DFTFE_REQUIRE(src && out, "null argument");
+  DFTFE_REQUIRE(!src->local_src, "src must own its local operator (not itself made by dftfe_ham_create_shared)");
+  int dev = -1;
+  DFTFE_CHECK_CUDA(cudaGetDevice(&dev));
+  DFTFE_REQUIRE(dev == src->device, "the current device must be src's");
+  *out = create_ham(src->mesh, (void*)src->stream, src);
   ABI_END
 }
 
 extern "C" dftfe_status dftfe_ham_set_potential(dftfe_ham h, const double* v_quad) {
   ABI_BEGIN
   DFTFE_REQUIRE(h && v_quad, "null argument");
+  if (h->local_src)
+    throw Error(DFTFE_ERR_STATE, "this ham uses another ham's local operator: set the potential on that ham");
   auto* m = h->mesh;
   const int64_t Msym = (int64_t)m->nc * (m->nc + 1) / 2;
   dim3 grid((unsigned)((Msym + PV_BM - 1) / PV_BM), (unsigned)((m->Nc + PV_BN - 1) / PV_BN));
@@ -513,7 +549,10 @@ extern "C" dftfe_status dftfe_ham_set_nonlocal(dftfe_ham h, int nproj, const dou
 extern "C" dftfe_status dftfe_ham_destroy(dftfe_ham h) {
   ABI_BEGIN
   if (!h) return DFTFE_OK;
-  if (h->stream || true) cudaStreamSynchronize(h->stream);
+  if (h->sharers > 0)
+    throw Error(DFTFE_ERR_STATE, "hams made by dftfe_ham_create_shared still use this ham: destroy them first");
+  if (h->local_src) h->local_src->sharers--;
+  cudaStreamSynchronize(h->stream);
   free_graphs(h);
   if (h->h_pass) cudaFreeHost(h->h_pass);
   free_nonlocal(h);
@@ -543,9 +582,9 @@ extern "C" dftfe_status dftfe_ham_export(dftfe_ham h, double* mass, int32_t* cel
                                      cudaMemcpyDeviceToDevice, s));
   if (cell_mats) {
     DFTFE_REQUIRE(c0 >= 0 && count >= 0 && c0 + count <= m->Nc, "cell range out of bounds");
-    DFTFE_REQUIRE(h->has_potential, "no potential set");
+    DFTFE_REQUIRE(loc(h)->has_potential, "no potential set");
     const int64_t n2 = (int64_t)m->nc * m->nc;
-    DFTFE_CHECK_CUDA(cudaMemcpyAsync(cell_mats, h->d_Hc + c0 * n2, sizeof(double) * count * n2,
+    DFTFE_CHECK_CUDA(cudaMemcpyAsync(cell_mats, loc(h)->d_Hc + c0 * n2, sizeof(double) * count * n2,
                                      cudaMemcpyDeviceToDevice, s));
   }
   ABI_END

@@ -499,8 +499,23 @@ bool gram_lower_tc(dftfe_ham h, const double* A, int64_t lda, const double* B, i
   }
   const int NB = (N + 127) / 128;
   const int npairs = NB * (NB + 1) / 2;
-  const int64_t want = std::max<int64_t>(1, (2LL * h->sm_count + npairs - 1) / npairs);
-  const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(want, (M + 1023) / 1024));
+  // row splits: at least two CTAs per SM in all, and (one CTA per SM at a time) a split
+  // count whose CTAs fill their last wave: the count in [want, 8 want] with the least idle
+  // SM slots in the last wave, per CTA-wave of work (36 blocks at N = 1,024 take 38 splits,
+  // 9 full waves, where 9 splits left 0.87 of the third wave idle)
+  const int64_t sm = std::max(1, h->sm_count);
+  const int64_t want = std::max<int64_t>(1, (2 * sm + npairs - 1) / npairs);
+  int64_t pick = want;
+  double best = 1e300;
+  for (int64_t c = want; c <= 8 * want; ++c) {
+    const int64_t ctas = c * npairs, waves = (ctas + sm - 1) / sm;
+    const double t = (double)waves / (double)c;          // time ~ waves x rows per split
+    if (t < best * (1.0 - 1e-9)) {
+      best = t;
+      pick = c;
+    }
+  }
+  const int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(pick, (M + 1023) / 1024));
   const int64_t rows = ((M + nsplit - 1) / nsplit + 31) / 32 * 32;
   const int64_t ns = (M + rows - 1) / rows;
   float* part = (float*)ws_get(h, "gram_tc_part", sizeof(float) * (size_t)ns * N * N);

@@ -241,3 +241,35 @@ def atom_walk(seed, centres, steps, step_len=0.05):
             nxt[a] += step_len * np.array([r * math.cos(phi), r * math.sin(phi), z])
         pos.append(nxt)
     return pos
+
+
+# (cells per axis, FE degree, states, atoms, Chebyshev degree) of the sixteen systems of the
+# batched k-point workload: meshes of 8^3 to 20^3 cells, p = 4 to 6, 64 to 768 states,
+# 8 to 48 atoms, degrees 20 to 40 (the larger state counts on the smaller meshes, so that
+# every system's 8 k-points fit on one device together)
+KPOINT_BATCH = [(8, 6, 768, 8, 40), (8, 5, 512, 10, 36), (8, 4, 640, 12, 32), (9, 6, 384, 14, 40),
+                (10, 6, 192, 16, 36), (10, 5, 320, 12, 32), (10, 4, 448, 18, 28), (11, 5, 160, 20, 30),
+                (12, 4, 256, 22, 26), (12, 5, 96, 24, 28), (13, 4, 160, 28, 24), (14, 4, 128, 32, 22),
+                (15, 4, 96, 36, 22), (16, 4, 80, 40, 20), (18, 4, 64, 44, 20), (20, 4, 64, 48, 20)]
+# cell edge by FE degree: about 0.21 bohr between nodes at every degree
+KPOINT_BATCH_CELL = {4: 0.85, 5: 1.05, 6: 1.25}
+
+
+def kpoint_batch(seed=0, systems=None):
+    """The batched k-point workload: one Workload per system (atoms of depth 3 Ha and width
+    0.8 bohr at centres uniform in the box, 4 projectors per atom of width 1 bohr and cutoff
+    2.5 bohr with couplings U[0.5, 2] Ha, complex block 64) with its 8 k-points, the 2 x 2 x 2
+    Monkhorst-Pack grid (2 pi / L)(+-1/4, +-1/4, +-1/4) in bohr^-1.  Returns a list of
+    (Workload, kpoints)."""
+    out = []
+    for i, (n, p, N, natoms, deg) in enumerate(KPOINT_BATCH if systems is None else systems):
+        s = Stream(seed * 1000 + i)
+        L = n * KPOINT_BATCH_CELL[p]
+        centres = [[L * s.uniform() for _ in range(3)] for _ in range(natoms)]
+        couplings = np.array([0.5 + 1.5 * s.uniform() for _ in range(4 * natoms)])
+        wl = Workload(f"kbatch{i}-{n}c-p{p}-N{N}", L, n, p, 3.0, 0.8, centres, N, 64, deg, 1, seed * 1000 + i,
+                      proj_width=1.0, proj_cutoff=2.5, couplings=couplings)
+        g = 2.0 * math.pi / L
+        kpts = [(g * a / 4.0, g * b / 4.0, g * c / 4.0) for a in (-1, 1) for b in (-1, 1) for c in (-1, 1)]
+        out.append((wl, kpts))
+    return out

@@ -100,3 +100,35 @@ def test_projector_disp_matches_the_csr_entries():
             g = np.exp(-r2 / (2 * w * w))
             ref = g / n_s if j == 0 else (d[:, j - 1] / w) * g / n_p
             assert np.allclose(chi[e0:e1], ref, rtol=1e-14, atol=1e-300)
+
+
+def test_kpoint_batch_recipe_spans_the_stated_ranges():
+    """The batched k-point workload: sixteen systems of 8^3-20^3 cells, p = 4-6, 64-768 states,
+    8-48 atoms with 4 projectors each, Chebyshev degrees 20-40; every system carries the 8
+    points of the 2 x 2 x 2 Monkhorst-Pack grid (2 pi / L)(+-1/4, +-1/4, +-1/4), all inside
+    the first Brillouin zone, distinct and summing to zero; atoms inside the box; seeds give
+    distinct systems and repeat exactly."""
+    import math
+    out = synth.kpoint_batch(0)
+    assert len(out) == 16
+    cells = [wl.ncell for wl, _ in out]
+    ps = [wl.degree for wl, _ in out]
+    states = [wl.nstates for wl, _ in out]
+    atoms = [len(wl.centres) for wl, _ in out]
+    degs = [wl.cheb_degree for wl, _ in out]
+    assert (min(cells), max(cells)) == (8, 20) and set(ps) == {4, 5, 6}
+    assert (min(states), max(states)) == (64, 768) and (min(atoms), max(atoms)) == (8, 48)
+    assert (min(degs), max(degs)) == (20, 40)
+    for wl, kpts in out:
+        assert wl.couplings.size == 4 * len(wl.centres)
+        assert np.all((wl.centres >= 0.0) & (wl.centres < wl.L))
+        assert np.all((wl.couplings >= 0.5) & (wl.couplings <= 2.0))
+        assert wl.proj_cutoff < wl.L / 2          # minimum image is the only image
+        k = np.array(kpts)
+        assert k.shape == (8, 3) and len({tuple(v) for v in k}) == 8
+        assert np.allclose(np.abs(k), 0.5 * math.pi / wl.L)
+        assert np.allclose(k.sum(axis=0), 0.0)
+    again = synth.kpoint_batch(0)
+    assert all(np.array_equal(a.centres, b.centres) for (a, _), (b, _) in zip(out, again))
+    other = synth.kpoint_batch(1)
+    assert not np.array_equal(out[0][0].centres, other[0][0].centres)
