@@ -185,8 +185,8 @@ dftfe_status dftfe_ham_apply(dftfe_ham ham, const double* X, int64_t ldx,
  * for this ham (that first call synchronises the stream).  Likewise the first TF32x3
  * cell-product launch of the split-precision filter (Sec. 4.3's cell products on the tensor
  * cores) times every launch shape of that kernel -- the split A operand staged in tensor
- * memory (where the accumulators leave room: at most three 128-row M-tiles, p <= 6) or in a
- * shared-memory ring, and the cells dealt to the persistent CTAs round-robin or in contiguous
+ * memory (where the accumulators leave room: at most three 128-row M-tiles, p <= 6; with 6 or
+ * 8 landing slots for the cell-matrix tiles) or in a shared-memory ring, and the cells dealt to the persistent CTAs round-robin or in contiguous
  * ranges -- on the launch's own operands and keeps the fastest (queried with
  * dftfe_autotune_query_mixed).  Tuning is skipped while the stream is being captured.  Every
  * shape gives bit-identical results.  enable = 0 restores the defaults; either call forgets
@@ -194,10 +194,12 @@ dftfe_status dftfe_ham_apply(dftfe_ham ham, const double* X, int64_t ldx,
 dftfe_status dftfe_ham_autotune(dftfe_ham ham, int enable);
 
 /* The tuned TF32x3 cell-kernel shape of this ham's mesh: HOST atmem (1 = A operand in tensor
- * memory, 0 = in shared memory, -1 = not tuned yet), deal (0 = round-robin, 1 = contiguous
- * ranges, -1 = not tuned), best_ms and default_ms (one launch over all cells in the chosen and
- * in the default shape -- tensor memory where it fits, round-robin; may be NULL). */
-dftfe_status dftfe_autotune_query_mixed(dftfe_ham ham, int* atmem, int* deal, double* best_ms,
+ * memory, 0 = in shared memory, -1 = not tuned yet), deep (with atmem: 0 = 6 landing slots for
+ * the cell-matrix tiles and 4 stages for the gathered X, 1 = 8 and 3 in the same shared
+ * memory), deal (0 = round-robin, 1 = contiguous ranges), best_ms and default_ms (one launch
+ * over all cells in the chosen and in the default shape -- tensor memory where it fits, 6 and
+ * 4, round-robin; may be NULL).  Every output -1 before tuning. */
+dftfe_status dftfe_autotune_query_mixed(dftfe_ham ham, int* atmem, int* deep, int* deal, double* best_ms,
                                         double* default_ms);
 
 /* The tuned shape for ncol real columns: HOST rows_per_cta (0 = the heuristic won, -1 = not
@@ -489,11 +491,11 @@ dftfe_status dftfe_batch_graph_query(dftfe_batch batch, int64_t* replays, int64_
  * choices and makes the next graphed pass run directly. */
 dftfe_status dftfe_batch_autotune(dftfe_batch batch, int enable);
 
-/* The index-th tuned launch (in key order): HOST nodes per cell, work items, atmem, deal,
- * order (0 = system-major, 1 = interleaved), best_ms and default_ms (may be NULL); every
- * output -1 (0 for the times) when index is past the last. */
+/* The index-th tuned launch (in key order): HOST nodes per cell, work items, atmem, deep, deal
+ * (as dftfe_autotune_query_mixed), order (0 = system-major, 1 = interleaved), best_ms and
+ * default_ms (may be NULL); every output -1 (0 for the times) when index is past the last. */
 dftfe_status dftfe_batch_autotune_query(dftfe_batch batch, int index, int* nodes_per_cell, int* work_items,
-                                        int* atmem, int* deal, int* order, double* best_ms,
+                                        int* atmem, int* deep, int* deal, int* order, double* best_ms,
                                         double* default_ms);
 
 /* ------------------------------------------ learned degree / bounds proposer */

@@ -113,10 +113,11 @@ _SIGS = {
     "dftfe_graph_query": [_vp, C.POINTER(_i64), C.POINTER(_i64)],
     "dftfe_ham_autotune": [_vp, _int],
     "dftfe_autotune_query": [_vp, _int, C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
-    "dftfe_autotune_query_mixed": [_vp, C.POINTER(_int), C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
+    "dftfe_autotune_query_mixed": [_vp, C.POINTER(_int), C.POINTER(_int), C.POINTER(_int), C.POINTER(_dbl),
+                                   C.POINTER(_dbl)],
     "dftfe_batch_autotune": [_vp, _int],
     "dftfe_batch_autotune_query": [_vp, _int, C.POINTER(_int), C.POINTER(_int), C.POINTER(_int), C.POINTER(_int),
-                                   C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
+                                   C.POINTER(_int), C.POINTER(_int), C.POINTER(_dbl), C.POINTER(_dbl)],
     "dftfe_ham_set_kpoint": [_vp, _vp, _vp],
     "dftfe_mesh_kpoint_stencil": [_vp, _vp, _vp],
     "dftfe_ham_apply_z": [_vp, _vp, _i64, _vp, _i64, _int, _int],
@@ -276,10 +277,10 @@ def dftfe_autotune_query(ham, ncol):
 
 
 def dftfe_autotune_query_mixed(ham):
-    """(atmem, deal, best_ms, default_ms) of the tuned TF32x3 cell-kernel shape; -1 = not tuned."""
-    a, d, b, dm = _int(), _int(), _dbl(), _dbl()
-    _check(_lib.dftfe_autotune_query_mixed(ham, C.byref(a), C.byref(d), C.byref(b), C.byref(dm)))
-    return a.value, d.value, b.value, dm.value
+    """(atmem, deep, deal, best_ms, default_ms) of the tuned TF32x3 cell-kernel shape; -1 = not tuned."""
+    a, dp, d, b, dm = _int(), _int(), _int(), _dbl(), _dbl()
+    _check(_lib.dftfe_autotune_query_mixed(ham, C.byref(a), C.byref(dp), C.byref(d), C.byref(b), C.byref(dm)))
+    return a.value, dp.value, d.value, b.value, dm.value
 
 
 # ------------------------------------------------------------ ChFSI steps
@@ -461,16 +462,16 @@ def dftfe_batch_autotune(batch, enable=True):
 
 def dftfe_batch_autotune_query(batch):
     """Every tuned launch of the batch: a list of dicts (nodes_per_cell, work_items, atmem,
-    deal, order, best_ms, default_ms)."""
+    deep, deal, order, best_ms, default_ms)."""
     out = []
     while True:
-        v = [_int() for _ in range(5)]
+        v = [_int() for _ in range(6)]
         b, dm = _dbl(), _dbl()
         _check(_lib.dftfe_batch_autotune_query(batch, len(out), *[C.byref(x) for x in v], C.byref(b), C.byref(dm)))
         if v[0].value < 0:
             return out
-        out.append(dict(nodes_per_cell=v[0].value, work_items=v[1].value, atmem=v[2].value, deal=v[3].value,
-                        order=v[4].value, best_ms=b.value, default_ms=dm.value))
+        out.append(dict(nodes_per_cell=v[0].value, work_items=v[1].value, atmem=v[2].value, deep=v[3].value,
+                        deal=v[4].value, order=v[5].value, best_ms=b.value, default_ms=dm.value))
 
 
 def dftfe_batch_chfsi_pass(batch, Xs, blocks, degrees, bounds, evals, resids, prec=DFTFE_FP64):

@@ -467,13 +467,13 @@ extern "C" dftfe_status dftfe_batch_autotune(dftfe_batch b, int enable) {
 }
 
 extern "C" dftfe_status dftfe_batch_autotune_query(dftfe_batch b, int index, int* nodes_per_cell, int* work_items,
-                                                   int* atmem, int* deal, int* order, double* best_ms,
+                                                   int* atmem, int* deep, int* deal, int* order, double* best_ms,
                                                    double* default_ms) {
   ABI_BEGIN
-  DFTFE_REQUIRE(b && nodes_per_cell && work_items && atmem && deal && order, "null argument");
+  DFTFE_REQUIRE(b && nodes_per_cell && work_items && atmem && deep && deal && order, "null argument");
   DFTFE_REQUIRE(index >= 0, "index must be >= 0");
   if (index >= (int)b->tuned.size()) {
-    *nodes_per_cell = *work_items = *atmem = *deal = *order = -1;
+    *nodes_per_cell = *work_items = *atmem = *deep = *deal = *order = -1;
     if (best_ms) *best_ms = 0.0;
     if (default_ms) *default_ms = 0.0;
     return DFTFE_OK;
@@ -483,6 +483,7 @@ extern "C" dftfe_status dftfe_batch_autotune_query(dftfe_batch b, int index, int
   *nodes_per_cell = std::atoi(it->first.c_str());
   *work_items = std::atoi(it->first.c_str() + it->first.find('/') + 1);
   *atmem = it->second.atmem;
+  *deep = it->second.deep;
   *deal = it->second.deal;
   *order = it->second.order;
   if (best_ms) *best_ms = it->second.best_ms;

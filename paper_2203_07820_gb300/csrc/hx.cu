@@ -400,12 +400,13 @@ extern "C" dftfe_status dftfe_chebyshev_filter(dftfe_ham h, double* X, int64_t l
   ABI_END
 }
 
-extern "C" dftfe_status dftfe_autotune_query_mixed(dftfe_ham h, int* atmem, int* deal, double* best_ms,
+extern "C" dftfe_status dftfe_autotune_query_mixed(dftfe_ham h, int* atmem, int* deep, int* deal, double* best_ms,
                                                    double* default_ms) {
   ABI_BEGIN
-  DFTFE_REQUIRE(h && atmem && deal, "null argument");
+  DFTFE_REQUIRE(h && atmem && deep && deal, "null argument");
   const bool done = h->tuned_mixed_done;
   *atmem = done ? h->tuned_mixed.atmem : -1;
+  *deep = done ? h->tuned_mixed.deep : -1;
   *deal = done ? h->tuned_mixed.deal : -1;
   if (best_ms) *best_ms = done ? h->tuned_mixed.best_ms : 0.0;
   if (default_ms) *default_ms = done ? h->tuned_mixed.default_ms : 0.0;

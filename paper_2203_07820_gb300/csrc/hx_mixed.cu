@@ -381,23 +381,29 @@ constexpr int kStage = 2 * kTile;                  // hi | lo
 constexpr int kMaxMTiles = 4;
 constexpr int kConv = 2;
 constexpr uint32_t kAcolBase = 384;                // first TMEM column of the A slots (TMEM form)
-template <bool ATMEM> struct Cfg {
-  static constexpr int kLand = ATMEM ? 6 : 4;      // landing ring slots (FP32 tiles)
-  static constexpr int kStagesB = ATMEM ? 4 : 3;   // B ring stages
+// DEEP: the same shared memory as 8 landing slots and 3 B stages instead of 6 and 4 (more of
+// the A stream in flight, less lookahead for the X gathers); a launch shape the tuner times
+template <bool ATMEM, bool DEEP = false> struct Cfg {
+  static constexpr int kLand = ATMEM ? (DEEP ? 8 : 6) : 4;      // landing ring slots (FP32 tiles)
+  static constexpr int kStagesB = ATMEM ? (DEEP ? 3 : 4) : 3;   // B ring stages
   static constexpr int kConvSmem = ATMEM ? 0 : kConv;
 };
-template <bool ATMEM> struct Shared {
-  uint64_t land_full[Cfg<ATMEM>::kLand], land_empty[Cfg<ATMEM>::kLand];
+template <bool ATMEM, bool DEEP = false> struct Shared {
+  uint64_t land_full[Cfg<ATMEM, DEEP>::kLand], land_empty[Cfg<ATMEM, DEEP>::kLand];
   uint64_t conv_full[kConv], conv_empty[kConv];
-  uint64_t b_full[Cfg<ATMEM>::kStagesB], b_empty[Cfg<ATMEM>::kStagesB];
+  uint64_t b_full[Cfg<ATMEM, DEEP>::kStagesB], b_empty[Cfg<ATMEM, DEEP>::kStagesB];
   uint64_t acc_full, acc_empty[kMaxMTiles], drain;
   uint32_t tmem;
   int abort;
 };
-template <bool ATMEM> constexpr size_t smem_bytes() {
-  return 1024 + (size_t)Cfg<ATMEM>::kLand * kTile + (size_t)Cfg<ATMEM>::kConvSmem * kStage +
-         (size_t)Cfg<ATMEM>::kStagesB * kStage + sizeof(Shared<ATMEM>);
+template <bool ATMEM, bool DEEP = false> constexpr size_t smem_bytes() {
+  using C = Cfg<ATMEM, DEEP>;
+  return 1024 + (size_t)C::kLand * kTile + (size_t)C::kConvSmem * kStage + (size_t)C::kStagesB * kStage +
+         sizeof(Shared<ATMEM, DEEP>);
 }
+static_assert(smem_bytes<true, true>() <= 227 * 1024 && smem_bytes<true, false>() <= 227 * 1024 &&
+                  smem_bytes<false, false>() <= 227 * 1024,
+              "TF32x3 cell kernel: shared memory above the 227 KB per CTA");
 __host__ __device__ inline int64_t kc_block_bytes(int nmt, int rows8) {
   return (int64_t)(nmt - 1) * kTile + (int64_t)rows8 * 128;
 }
@@ -464,7 +470,7 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
 // are dealt to the persistent grid round-robin (deal = 0: CTA b takes b, b + grid, ...) or in
 // contiguous ranges (deal = 1: CTA b takes the b-th of grid near-equal ranges), a launch shape
 // the autotuner picks; every item is computed the same way either way.
-template <bool ATMEM>
+template <bool ATMEM, bool DEEP>
 __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single, const mp::Item* __restrict__ items,
                                                                 const int2* __restrict__ work, int nwork, int nc,
                                                                 int nkc, int nmt, int deal, int* err) {
@@ -476,7 +482,7 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   using tc::smem_u32;
   using tc::sw128;
   using tc::tc_commit;
-  constexpr int kLand = Cfg<ATMEM>::kLand, kStagesB = Cfg<ATMEM>::kStagesB;
+  constexpr int kLand = Cfg<ATMEM, DEEP>::kLand, kStagesB = Cfg<ATMEM, DEEP>::kStagesB;
   // the CTA's i-th work item: its system's operands and its cell
   const int q_deal = nwork / (int)gridDim.x, r_deal = nwork % (int)gridDim.x;
   const int64_t first = deal ? (int64_t)blockIdx.x * q_deal + min((int)blockIdx.x, r_deal) : 0;
@@ -494,8 +500,8 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sL = base;                                        // landing ring: kLand x 16 KB FP32
   uint8_t* sC = sL + kLand * kTile;                          // shared-memory hi/lo ring (not ATMEM)
-  uint8_t* sB = sC + Cfg<ATMEM>::kConvSmem * kStage;         // B ring: kStagesB x (hi | lo)
-  Shared<ATMEM>* sh = (Shared<ATMEM>*)(sB + kStagesB * kStage);
+  uint8_t* sB = sC + Cfg<ATMEM, DEEP>::kConvSmem * kStage;   // B ring: kStagesB x (hi | lo)
+  Shared<ATMEM, DEEP>* sh = (Shared<ATMEM, DEEP>*)(sB + kStagesB * kStage);
   volatile int* abort = &sh->abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -795,12 +801,15 @@ __global__ void __launch_bounds__(mp::kThreads, 1) k_cell_tf32p(mp::Item single,
 static void launch_cell_tf32p(cudaStream_t s, unsigned grid, const mp::Item& one, const mp::Item* items,
                               const int2* work, int nwork, int nc, int nkc, int nmt, int* err,
                               const MixedShape& shape = MixedShape{}) {
-  if (nmt <= 3 && shape.atmem)
-    DFTFE_LAUNCH(k_cell_tf32p<true>, grid, mp::kThreads, mp::smem_bytes<true>(), s, one, items, work, nwork, nc, nkc,
-                 nmt, shape.deal, err);
+  if (nmt <= 3 && shape.atmem && shape.deep)
+    DFTFE_LAUNCH((k_cell_tf32p<true, true>), grid, mp::kThreads, (mp::smem_bytes<true, true>()), s, one, items, work,
+                 nwork, nc, nkc, nmt, shape.deal, err);
+  else if (nmt <= 3 && shape.atmem)
+    DFTFE_LAUNCH((k_cell_tf32p<true, false>), grid, mp::kThreads, (mp::smem_bytes<true, false>()), s, one, items,
+                 work, nwork, nc, nkc, nmt, shape.deal, err);
   else
-    DFTFE_LAUNCH(k_cell_tf32p<false>, grid, mp::kThreads, mp::smem_bytes<false>(), s, one, items, work, nwork, nc,
-                 nkc, nmt, shape.deal, err);
+    DFTFE_LAUNCH((k_cell_tf32p<false, false>), grid, mp::kThreads, (mp::smem_bytes<false, false>()), s, one, items,
+                 work, nwork, nc, nkc, nmt, shape.deal, err);
 }
 
 static bool capturing(cudaStream_t s) {
@@ -820,13 +829,15 @@ static MixedShape tune_cell_tf32p(cudaStream_t s, int sm, const mp::Item& one, c
   std::vector<MixedShape> cands;
   for (int order = 0; order < (work_alt ? 2 : 1); ++order)
     for (int atmem = (nmt <= 3 ? 1 : 0); atmem >= 0; --atmem)
-      for (int deal = 0; deal < 2; ++deal) {
-        MixedShape c;
-        c.atmem = atmem;
-        c.deal = deal;
-        c.order = order;
-        cands.push_back(c);
-      }
+      for (int deep = 0; deep < (atmem ? 2 : 1); ++deep)
+        for (int deal = 0; deal < 2; ++deal) {
+          MixedShape c;
+          c.atmem = atmem;
+          c.deep = deep;
+          c.deal = deal;
+          c.order = order;
+          cands.push_back(c);
+        }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   DFTFE_CHECK_CUDA(cudaEventCreate(&e0));
   DFTFE_CHECK_CUDA(cudaEventCreate(&e1));
@@ -864,10 +875,12 @@ static MixedShape tune_cell_tf32p(cudaStream_t s, int sm, const mp::Item& one, c
 }
 
 static void set_tf32p_attrs() {
-  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)mp::smem_bytes<true>()));
-  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)mp::smem_bytes<false>()));
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)mp::smem_bytes<true, false>()));
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)mp::smem_bytes<true, true>()));
+  DFTFE_CHECK_CUDA(cudaFuncSetAttribute(k_cell_tf32p<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)mp::smem_bytes<false, false>()));
 }
 
 // ------------------------------------------------------------ FP32 helpers

@@ -101,14 +101,15 @@ struct TunedShape {
 
 // A launch shape of the TF32x3 cell-product kernel, as the autotuner picks it: the split A
 // operand staged in tensor memory (atmem = 1, at most three 128-row M-tiles) or in a
-// shared-memory ring (0); work items dealt to the persistent CTAs round-robin (deal = 0) or
+// shared-memory ring (0); with atmem, 6 landing slots for the FP32 plane and 4 stages for the
+// gathered X (deep = 0) or 8 and 3 (deep = 1); work items dealt to the persistent CTAs round-robin (deal = 0) or
 // in contiguous ranges (1); in a batched launch, the work list system-major (order = 0) or
 // interleaved cell by cell across the systems (1, so the k-point items that share one FP32
 // plane read each cell's tiles at about the same time).  Every shape computes every cell
 // product the same way.  best_ms / default_ms: the timed launch in this shape and in the
 // default one (0 when not tuned).
 struct MixedShape {
-  int atmem = 1, deal = 0, order = 0;
+  int atmem = 1, deep = 0, deal = 0, order = 0;
   double best_ms = 0.0, default_ms = 0.0;
 };
 

@@ -147,8 +147,8 @@ def test_tuned_tf32x3_passes_are_bit_identical(dg):
             dg.dftfe_chfsi_pass(made[1][1], X2, N, 12, b2, e2, r2, dg.DFTFE_MIXED_TF32X3)
             torch.cuda.synchronize()
             assert torch.equal(X1, X2) and torch.equal(e1, e2)
-        atmem, deal, best, default = dg.dftfe_autotune_query_mixed(made[1][1])
-        assert atmem in (0, 1) and deal in (0, 1) and 0.0 < best <= default
+        atmem, deep, deal, best, default = dg.dftfe_autotune_query_mixed(made[1][1])
+        assert atmem in (0, 1) and deep in (0, 1) and deal in (0, 1) and 0.0 < best <= default
     finally:
         for mesh, ham in made:
             dg.dftfe_ham_destroy(ham)
