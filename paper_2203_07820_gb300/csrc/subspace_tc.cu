@@ -56,14 +56,6 @@ __device__ __forceinline__ void slices3(float f, uint32_t& s1, uint32_t& s2, uin
   s3 = tc::tf32_rn(r1 - __uint_as_float(s2));
 }
 
-// L2 prefetch of the FP64 row segment [c0, c1] of row `row` (c1 >= c0, in bounds): its first,
-// middle and last lines (a 32-double segment spans at most three 128-byte lines)
-__device__ __forceinline__ void prefetch_seg(const double* row, int c0, int c1) {
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(row + c0));
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(row + min(c0 + 16, c1)));
-  asm volatile("prefetch.global.L2 [%0];" :: "l"(row + c1));
-}
-
 // the six slice products of one 32-deep chunk into accumulator d (fresh)
 __device__ __forceinline__ void chunk_mma(uint32_t d, uint32_t a0, uint32_t b0) {
   const uint32_t id = tc::idesc(2u, 128, 128);
@@ -217,21 +209,12 @@ __global__ void __launch_bounds__(st::kThreads, 1) k_rot_tc(const double* __rest
         raw[rr] = (m < M && k < N) ? X[m * ld + k] : 0.0;
       }
     };
-    // lane l prefetches into L2 its row 32 w + l of chunk kc: the register loads of that chunk,
-    // two chunks later, then wait on L2 rather than on HBM
-    auto prefetch_a = [&](int kc) {
-      const int64_t m = m0 + 32 * w + lane;
-      const int c0 = 32 * kc;
-      if (m < M && c0 < N) prefetch_seg(X + m * ld, c0, min(c0 + 31, N - 1));
-    };
     if (nkc > 0) load_a(0);
-    if (nkc > 1) prefetch_a(1);
     for (int kc = 0; kc < nkc && !*abort; ++kc) {
       const int s = kc % kStages;
       float v[32];
 #pragma unroll
       for (int rr = 0; rr < 32; ++rr) v[rr] = narrow_f64(raw[rr]);
-      if (kc + 2 < nkc) prefetch_a(kc + 2);
       if (kc + 1 < nkc) load_a(kc + 1);
       if (!mbar_wait(&sh->empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
       uint8_t* tile = base + s * kStage;
@@ -387,24 +370,13 @@ __global__ void __launch_bounds__(st::kThreads, 1) k_gram_tc(const double* __res
         raw[kk] = (c < N && m < k1) ? src[m * ldm + c] : 0.0;
       }
     };
-    // lane l prefetches into L2 the row 32 kc + l of unit u (its 32 columns of this warp): the
-    // register loads of that unit, a few units later, then wait on L2 rather than on HBM
-    auto prefetch_u = [&](int u) {
-      const int kc = u >> 1;
-      const bool isA = (u & 1) == 0;
-      const int64_t m = k0 + 32 * kc + lane;
-      const int c0 = 128 * (isA ? bi : bj) + 32 * w;
-      if (m < k1 && c0 < N) prefetch_seg((isA ? A : B) + m * (isA ? lda : ldb), c0, min(c0 + 31, N - 1));
-    };
     if (total > 0) load(0);
-    for (int u = 1; u < min(total, 3); ++u) prefetch_u(u);
     for (int u = 0; u < total && !*abort; ++u) {
       const int kc = u >> 1, s = kc % kStages;
       const bool isA = (u & 1) == 0;
       float v[32];
 #pragma unroll
       for (int kk = 0; kk < 32; ++kk) v[kk] = narrow_f64(raw[kk]);
-      if (u + 3 < total) prefetch_u(u + 3);
       if (u + 1 < total) load(u + 1);
       if (isA && !mbar_wait(&sh->empty[s], ((kc / kStages) & 1) ^ 1, abort, err)) break;
       uint8_t* tile = base + s * kStage + (isA ? 0 : kOperand);
