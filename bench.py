@@ -59,6 +59,11 @@ def workload(name, seed):
         # same per-cell shape, 15 bohr box, 12^3 cells (216 per colour), 8 atoms: about
         # 4.5 GB on the device in a mixed pass (for ncu captures)
         return synth.lattice_atoms(seed, ncell=12, L=15.0, nside=2, nstates=128, block=128, passes=1)
+    if name == "profile1024":
+        # the subspace shape of the 32^3-cell workload (1,024 states, block 128) on the 8^3-cell
+        # box: 110,592 DoFs, X 0.9 GB (> L2), about 3 GB on the device (for ncu captures of the
+        # Gram and rotation kernels)
+        return synth.lattice_atoms(seed, ncell=8, L=10.0, nside=1, nstates=1024, block=128, passes=1)
     if name == "scale":
         # 24^3 cells, 2,985,984 DoFs, 512 states
         return synth.lattice_atoms(seed)
@@ -1209,7 +1214,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="scale32", choices=["scale32", "scale", "small", "profile", "profile12"])
+    ap.add_argument("--workload", default="scale32", choices=["scale32", "scale", "small", "profile", "profile12", "profile1024"])
     ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")

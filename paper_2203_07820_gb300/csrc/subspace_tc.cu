@@ -48,12 +48,14 @@ struct Bars {
 
 constexpr size_t smem_bytes() { return 1024 + kStages * (size_t)kStage + sizeof(Bars); }
 
-// the three TF32 slices of an FP32 value (exact)
+// the three TF32 slices of an FP32 value (exact); each rounding by the two-integer-operation
+// form of cvt.rna.tf32.f32 (identical for every finite input), which keeps the conversion off
+// the instruction the producers would otherwise issue three times per value
 __device__ __forceinline__ void slices3(float f, uint32_t& s1, uint32_t& s2, uint32_t& s3) {
-  s1 = tc::tf32_rn(f);
+  s1 = tc::tf32_rn_bits(__float_as_uint(f));
   const float r1 = f - __uint_as_float(s1);
-  s2 = tc::tf32_rn(r1);
-  s3 = tc::tf32_rn(r1 - __uint_as_float(s2));
+  s2 = tc::tf32_rn_bits(__float_as_uint(r1));
+  s3 = tc::tf32_rn_bits(__float_as_uint(r1 - __uint_as_float(s2)));
 }
 
 // the six slice products of one 32-deep chunk into accumulator d (fresh)
