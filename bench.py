@@ -637,8 +637,8 @@ def ttr_step(dg, dev, stream, tol=1e-5, max_passes=30):
 
 
 def scf_step(dg, dev, stream, steps=4, tol=1e-5):
-    """The benchmark spec's combined form against the plain FP64 form, in time to residual on
-    SCF-like sequences: sixteen independent systems (3^3-5^3 cells, p = 4-6, 16-40 states,
+    """The combined form (split precision, batched, learned degree) against the plain FP64 form,
+    in time to residual on SCF-like sequences: sixteen independent systems (3^3-5^3 cells, p = 4-6, 16-40 states,
     3 Gaussian wells each, no projectors) whose atoms move 0.05 bohr per step with the potential
     mixed 0.3 old / 0.7 new.  From a common start (every system converged at its first
     potential in FP64, untimed) each form must bring the largest generalised residual
@@ -775,8 +775,8 @@ def query_families(dg, ham, steps):
 
 
 def rooflines(fam, wl, precision):
-    """Per kernel family: algorithmic work per launch (SURVEY 8(d) units) over the measured
-    launch time, against the measured peaks."""
+    """Per kernel family: algorithmic work per launch (flops, or bytes the method must move)
+    over the measured launch time, against the measured peaks."""
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     bf16_sust = peaks.get("bf16_tflops_sustained", 1700.0)

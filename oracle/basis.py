@@ -3,7 +3,7 @@
 The paper's basis is C0 Lagrange polynomials on Gauss-Lobatto-Legendre (GLL)
 nodes (Sec. 2.3, Eq. fem), with GLL quadrature making the mass matrix diagonal
 (text after Eq. hep).  The local-potential term uses an n_q-point rule per cell
-(Eq. quadLocal); the paper does not fix n_q, and this build reads it as a
+(Eq. quadLocal); the paper does not fix n_q, and it is read here as a
 Gauss-Legendre rule with p+1 points per axis.
 """
 import numpy as np

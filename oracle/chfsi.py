@@ -3,7 +3,7 @@
 Filter (Eq. chebyfilter): Psi_f = T_m(Hbar) Psi_in with Hbar = (H~ - c)/e mapping
 the unwanted interval [a, b] to [-1, 1], e = (b-a)/2, c = (b+a)/2, evaluated by the
 three-term recurrence T_{k+1} = 2 x T_k - T_{k-1}.  The paper fixes neither c1, c2
-nor a scaling; this build offers the unscaled recurrence and the scaled one of
+nor a scaling; the oracle offers the unscaled recurrence and the scaled one of
 Zhou & Saad (2007, the paper's ref. saad2006), which keeps the vectors O(1):
   sigma_1 = e/(a0 - c),  X_1 = sigma_1 (H~ - c) X_0 / e,
   sigma_{k+1} = 1/(2/sigma_1 - sigma_k),

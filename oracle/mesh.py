@@ -1,6 +1,6 @@
 """Periodic hexahedral spectral-element mesh (oracle, FP64).
 
-Numbering (the paper is silent; this build's convention):
+Numbering (the paper is silent; the convention used here and by the library):
   global node (ix, iy, iz), ix in [0, nx*p), index = ix + gx*(iy + gy*iz), gx = nx*p;
   cell (cx, cy, cz) index = cx + nx*(cy + ny*cz);
   cell-local node (a, b, c) -> a + (p+1)*(b + (p+1)*c), global ix = (cx*p + a) mod gx;
