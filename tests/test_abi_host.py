@@ -141,6 +141,15 @@ def test_null_arguments_rejected_by_the_kpoint_graph_and_tuning_calls(dg):
     assert lib.dftfe_autotune_query(None, 8, None, None, None) == 1
     assert lib.dftfe_batch_use_graphs(None, 1) == 1
     assert lib.dftfe_batch_graph_query(None, None, None) == 1
+    # the shared local operator and the split-precision tuner
+    out = C.c_void_p()
+    assert lib.dftfe_ham_create_shared(None, C.byref(out)) == 1 and out.value is None
+    i = [C.c_int(7) for _ in range(6)]
+    t = [C.c_double(7.0) for _ in range(2)]
+    assert lib.dftfe_autotune_query_mixed(None, *[C.byref(x) for x in i[:3]], *[C.byref(x) for x in t]) == 1
+    assert lib.dftfe_batch_autotune(None, 1) == 1
+    assert lib.dftfe_batch_autotune_query(None, 0, *[C.byref(x) for x in i], *[C.byref(x) for x in t]) == 1
+    assert all(x.value == 7 for x in i) and all(x.value == 7.0 for x in t)     # outputs untouched
     mesh = dg.dftfe_mesh_create(6.0, 2, 3)
     try:
         assert lib.dftfe_mesh_kpoint_stencil(mesh, None, None) == 1
